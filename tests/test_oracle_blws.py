@@ -1,0 +1,162 @@
+"""Pins for the oracle's block Lanczos with warm start: Theorem 1, the
+invariants of Algorithm 2, the b = 1 reduction to Algorithm 1, exactness
+under an exact warm start (Section 3), and exactness once the Krylov space is
+the whole space."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.blws import augmented, apply_augmented, block_lanczos, assemble_T
+from oracle.lanczos import lanczos_alg1, tridiag
+from paper_1012_0365_gb300 import synthetic as syn
+
+
+@pytest.mark.parametrize("m,n", [(3, 5), (5, 3), (4, 4)])
+def test_theorem1_spectrum_and_vectors(m, n):
+    # Theorem 1: eig(W~) = {+sigma_i} U {-sigma_i} U {0 x |m-n|},
+    # eigenvectors (u_i; +-v_i)/sqrt(2).
+    W = syn.gaussian_block(m, n, seed=m * 10 + n)
+    U, s, Vt = np.linalg.svd(W)
+    lam, Z = np.linalg.eigh(augmented(W))
+    want = np.sort(np.concatenate([s, -s, np.zeros(abs(m - n))]))
+    np.testing.assert_allclose(lam, want, atol=1e-12)
+    p = min(m, n)
+    for i in range(p):
+        top = Z[:, np.argmin(np.abs(lam - s[i]))]
+        ref = np.concatenate([U[:, i], Vt[i]]) / np.sqrt(2)
+        assert abs(abs(top @ ref) - 1) < 1e-10
+        bot = Z[:, np.argmin(np.abs(lam + s[i]))]
+        ref = np.concatenate([U[:, i], -Vt[i]]) / np.sqrt(2)
+        assert abs(abs(bot @ ref) - 1) < 1e-10
+
+
+def test_apply_augmented_skips_zero_blocks_exactly():
+    W = syn.gaussian_block(7, 4, seed=5)
+    X = syn.gaussian_block(11, 3, seed=6)
+    np.testing.assert_allclose(apply_augmented(W, X), augmented(W) @ X, atol=1e-13)
+
+
+@pytest.mark.parametrize("k,b", [(2, 3), (3, 4), (4, 2)])
+def test_alg2_invariants(k, b):
+    # Q_k orthonormal, T_k symmetric and W~ Q_k = Q_k T_k + R_k E_k^T (Eq. 12).
+    W = syn.gaussian_block(20, 16, seed=k * 7 + b)
+    op = lambda X: apply_augmented(W, X)
+    X1, _ = np.linalg.qr(syn.gaussian_block(36, b, seed=b))
+    Xs, Ms, Bs, Rk = block_lanczos(op, X1, k)
+    Q = np.hstack(Xs)
+    T = assemble_T(Ms, Bs)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(k * b), atol=1e-12)
+    np.testing.assert_allclose(T, T.T, atol=0)
+    lhs = op(Q)
+    rhs = Q @ T
+    rhs[:, (k - 1) * b:] += Rk
+    np.testing.assert_allclose(lhs, rhs, atol=1e-11 * np.abs(lhs).max())
+    # B_l is upper triangular (the R factor of the QR of R_l)
+    for B in Bs:
+        np.testing.assert_allclose(np.tril(B, -1), 0, atol=0)
+
+
+def test_alg1_full_krylov_reproduces_spectrum():
+    # Algorithm 1 with k = size: T_k is similar to W, so eig(T_k) = eig(W).
+    A = syn.gaussian_block(6, 6, seed=11)
+    W = A + A.T
+    q1 = syn.gaussian_block(6, 1, seed=12)[:, 0]
+    q1 /= np.linalg.norm(q1)
+    Q, alpha, beta = lanczos_alg1(W, q1, 6)
+    np.testing.assert_allclose(np.linalg.eigvalsh(tridiag(alpha, beta)),
+                               np.linalg.eigvalsh(W), atol=1e-9)
+    np.testing.assert_allclose(Q.T @ W @ Q, tridiag(alpha, beta), atol=1e-9)
+
+
+def test_block_b1_reduces_to_alg1():
+    # Algorithm 2 with one column per block is Algorithm 1 (Section 4).
+    W = syn.gaussian_block(9, 8, seed=13)
+    Wt = augmented(W)
+    q1 = syn.gaussian_block(17, 1, seed=14)
+    q1 /= np.linalg.norm(q1)
+    k = 5
+    Q1, alpha, beta = lanczos_alg1(Wt, q1[:, 0], k)
+    Xs, Ms, Bs, _ = block_lanczos(lambda X: apply_augmented(W, X), q1, k)
+    np.testing.assert_allclose([M[0, 0] for M in Ms], alpha, atol=1e-10)
+    np.testing.assert_allclose([abs(B[0, 0]) for B in Bs], beta, atol=1e-10)
+    for l in range(k):
+        assert abs(abs(Xs[l][:, 0] @ Q1[:, l]) - 1) < 1e-9
+
+
+def _known_svd(m, n, s, seed):
+    p = len(s)
+    U = syn.orthonormal(m, p, seed=seed)
+    V = syn.orthonormal(n, p, seed=seed + 1)
+    return U, V, (U * s) @ V.T
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_exact_warm_start_is_exact(k):
+    # Section 3/4: a start block spanning a paired top singular subspace is
+    # invariant under W~, R_1 = 0 (deflated), and BLWS returns T_eps(W) exactly.
+    s = np.array([10.0, 8.0, 6.0, 4.0, 2.0, 1.0, 0.5])
+    U, V, W = _known_svd(12, 9, s, seed=20)
+    r = 4
+    out = oracle.blws_svt_ref(W, 3.0, U[:, :r], V[:, :r], k, r)
+    A, c = oracle.svt_full(W, 3.0)
+    np.testing.assert_allclose(out["A"], A, atol=1e-12 * np.abs(A).max())
+    np.testing.assert_allclose(out["sigma"], s[:r], atol=1e-12)
+    assert out["c"] == c == 4
+
+
+def test_whole_space_krylov_is_exact():
+    # k*b >= m + n: the Krylov space is everything, Ritz pairs are exact.
+    W = syn.gaussian_block(5, 4, seed=30)
+    U0 = syn.gaussian_block(5, 3, seed=31)
+    V0 = syn.gaussian_block(4, 3, seed=32)
+    eps = 0.7
+    out = oracle.blws_svt_ref(W, eps, U0, V0, k=3, r=4)
+    A, c = oracle.svt_full(W, eps)
+    np.testing.assert_allclose(out["sigma"], np.linalg.svd(W, compute_uv=False), atol=1e-10)
+    np.testing.assert_allclose(out["A"], A, atol=1e-10)
+    assert out["c"] == c
+
+
+def test_cold_start_whole_space_is_exact():
+    W = syn.gaussian_block(6, 5, seed=40)
+    G = syn.gaussian_block(11, 4, seed=41)
+    out = oracle.cold_svt_ref(W, 0.5, G, k=3, r=5)
+    A, c = oracle.svt_full(W, 0.5)
+    np.testing.assert_allclose(out["A"], A, atol=1e-10)
+
+
+def test_warm_start_error_shrinks_with_perturbation():
+    # Section 4.1: W_i close to W_{i-1} makes a few steps accurate.  BLWS
+    # started from W's top subspace and applied to W + d G has an error that
+    # falls in proportion to d, and each extra block step divides it by about
+    # the gap ratio sigma_7 / sigma_6 = 0.2 (Discussion, Section 6).
+    s = np.concatenate([np.linspace(20, 10, 6), np.linspace(2, 0.1, 14)])
+    U, V, W = _known_svd(40, 30, s, seed=50)
+    G = syn.gaussian_block(40, 30, seed=51)
+    errs = {2: [], 3: []}
+    for d in (1e-2, 1e-3, 1e-4, 1e-5):
+        Wd = W + d * G
+        A, _ = oracle.svt_full(Wd, 5.0)
+        for k in (2, 3):
+            out = oracle.blws_svt_ref(Wd, 5.0, U[:, :6], V[:, :6], k=k, r=6)
+            errs[k].append(np.linalg.norm(out["A"] - A) / np.linalg.norm(A))
+    for k in (2, 3):
+        ratios = np.array(errs[k][:-1]) / np.array(errs[k][1:])
+        assert np.all((ratios > 8) & (ratios < 12)), ratios
+    assert all(e3 < 0.3 * e2 for e2, e3 in zip(errs[2], errs[3]))
+    assert errs[3][-1] < 1e-6
+
+
+def test_mixed_start_beats_one_sided_start():
+    # Section 4.1: the mixed start (U;V)/sqrt2 gives higher precision than the
+    # standard (U;0) start for the same number of steps.
+    s = np.concatenate([np.linspace(20, 10, 5), np.linspace(3, 0.1, 25)])
+    U, V, W = _known_svd(50, 40, s, seed=60)
+    G = syn.gaussian_block(50, 40, seed=61)
+    Wd = W + 0.3 * G
+    A, _ = oracle.svt_full(Wd, 5.0)
+    mixed = oracle.blws_svt_ref(Wd, 5.0, U[:, :5], V[:, :5], k=2, r=5)
+    one_sided = oracle.blws_svt_ref(Wd, 5.0, U[:, :5] * np.sqrt(2), 0 * V[:, :5], k=2, r=5)
+    e_mixed = np.linalg.norm(mixed["A"] - A)
+    e_one = np.linalg.norm(one_sided["A"] - A)
+    assert e_mixed < e_one
