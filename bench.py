@@ -1,0 +1,318 @@
+"""Benchmark of the BLWS path: Robust PCA solves/s and latency on one GPU.
+
+One step = one complete Robust PCA solve (inexact ALM, every SVT by BLWS:
+start block, block Lanczos products, block coefficients, residuals,
+CholeskyQR2, T_k eigen-solve, Ritz lift, threshold and count, fused epilogue)
+on the 2000 x 2000, rank-100, 10%-corrupted synthetic workload (seeded), run
+to tol 1e-7.  The timed region holds only device work on inputs already in
+HBM; L2 is flushed (a 512 MB write) between steps, outside the timed events.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(full-SVD inexact ALM) on the host cores instead, on a bounded sample.
+Under torchrun (N > 1) every rank solves its own instances (replicas: the
+solves are independent) and rank 0 reports the aggregate.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (m, n, rank, corrupted fraction)
+    "rpca_2000x2000_r100": (2000, 2000, 100, 0.10),
+    "rpca_20000x200_r5": (20000, 200, 5, 0.10),
+    "rpca_200x200_r10": (200, 200, 10, 0.05),
+}
+DEFAULT = "rpca_2000x2000_r100"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9  # SMs x DFMA/clk x flops x max clock
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_sample(D, iters_full, budget_s=20.0):
+    """Time the FP64 oracle (full-SVD inexact ALM) for a bounded number of
+    iterations and scale to one full solve (same iteration count)."""
+    import oracle
+    # ||D||_2 set-up plus as many iterations as fit the budget (at least 2)
+    t0 = time.perf_counter()
+    n_it = 0
+    setup = None
+    while True:
+        n_it += 1
+        t1 = time.perf_counter()
+        out = oracle.rpca_ialm_full(D, tol=0.0, max_iter=n_it)
+        dt = time.perf_counter() - t1
+        if setup is None:
+            setup = dt  # one iteration + set-up
+        if dt > budget_s / 3 or n_it >= 3:
+            break
+    per_iter = max((dt - setup) / max(n_it - 1, 1), 1e-9) if n_it > 1 else dt
+    est = setup + per_iter * (iters_full - 1)
+    return {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d of %d inexact-ALM iterations (full LAPACK SVD each) on the same "
+                      "workload, scaled to the full iteration count; %.1f s of CPU work"
+                      % (n_it, iters_full, time.perf_counter() - t0)}
+
+
+def run_reference(args, ws, rank):
+    """--impl reference: the FP64 CPU oracle on the host cores."""
+    from paper_1012_0365_gb300 import synthetic as syn
+    import oracle
+    if rank != 0:
+        return None
+    m, n, r, f = WORKLOADS[args.workload]
+    D, L0, _ = syn.rpca_problem(m, n, r, f, seed=0)
+    # one full solve's iteration count is fixed by the workload (the GPU path
+    # needs the same count within one): measure it on a short oracle run is too
+    # slow at full size, so take it from the planted problem's known behaviour
+    iters_full = args.ref_iters
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.rpca_ialm_full(D, tol=0.0, max_iter=args.ref_sample_iters)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt / args.ref_sample_iters * iters_full)
+    value = 1.0 / float(np.mean(times))
+    return {"metric": "rpca_solves_per_s", "value": value, "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "corrupt": f,
+                       "tol": args.tol},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                             "unit": "solves/s",
+                             "sample": "each step: %d inexact-ALM iterations with full LAPACK "
+                                       "SVD, scaled to %d iterations per solve"
+                                       % (args.ref_sample_iters, iters_full)},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="blws", choices=["blws", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--tol", type=float, default=1e-7)
+    ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-iters", type=int, default=25)
+    ap.add_argument("--ref-sample-iters", type=int, default=2)
+    args = ap.parse_args()
+    ws, rank = dist_env()
+
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+        if out is not None:
+            print(json.dumps(out))
+        return
+
+    import torch
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    m, n, r, f = WORKLOADS[args.workload]
+    D, L0, S0 = syn.rpca_problem(m, n, r, f, seed=rank)
+    Dh = torch.from_numpy(D.T.copy()).pin_memory()  # column-major host copy
+    Dg = blws.empty_colmajor(m, n)
+    Dg.t().copy_(Dh)
+    A = blws.empty_colmajor(m, n)
+    E = blws.empty_colmajor(m, n)
+    Ah = torch.empty((n, m), dtype=torch.float64).pin_memory()
+    Eh = torch.empty((n, m), dtype=torch.float64).pin_memory()
+    ctx = blws.Context(k=args.k, device=local_rank)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve():
+        return ctx.rpca_solve(Dg, tol=args.tol, A=A, E=E)
+
+    for _ in range(args.warmup):
+        _, _, info = solve()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM) ----
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms = []
+    launches0 = ctx.launches
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        _, _, info = solve()
+        ev1.record(stream)
+        ev1.synchronize()
+        step_ms.append(ev0.elapsed_time(ev1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = ctx.launches - launches0
+    clocks = sampler.stop()
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * args.steps / (total_ms / 1e3)
+    relerr = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
+
+    # ---- end to end through the public API with host buffers ----
+    e2e_ms = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Dg.t().copy_(Dh, non_blocking=True)
+        _, _, _ = solve()
+        Ah.copy_(A.t(), non_blocking=True)
+        Eh.copy_(E.t(), non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_val = ws / (float(np.mean(e2e_ms)) / 1e3)
+
+    # ---- roofline of the dominant kernel: the block product with W~ ----
+    b = max(info["rank"] + 1, 1)
+    X = blws.colmajor(torch.randn(m + n, b, dtype=torch.float64, device="cuda"))
+    P = blws.empty_colmajor(m + n, b)
+    for _ in range(3):
+        ctx.apply(Dg, X, P)
+    reps = 10
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        ctx.apply(Dg, X, P)
+    ev1.record(stream)
+    ev1.synchronize()
+    apply_ms = ev0.elapsed_time(ev1) / reps
+    flops = 4.0 * m * n * b
+    achieved = flops / (apply_ms / 1e3) / 1e12
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_oracle_sample(D, info["iters"])
+    lat = np.array(step_ms)
+    out = {
+        "metric": "rpca_solves_per_s",
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "corrupt": f,
+                   "tol": args.tol, "k": args.k, "l2": "flushed between steps (512 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "solve": {"iters": info["iters"], "rank": info["rank"], "nnzE": info["nnzE"],
+                  "residual": info["residual"], "relerr_vs_planted": relerr},
+        "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * n * 8,
+                "d2h_bytes_per_step": 2 * m * n * 8},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "gemm_f64 (block product with the augmented matrix, b=%d)" % b,
+                     "bound": "alu", "achieved": achieved * 1e3, "peak": FP64_PEAK_GFLOPS,
+                     "unit": "GFLOP/s", "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
+                     "traffic": None, "peak_source": "FP64 152 SMs x 2 DFMA/clk x 2.07 GHz"},
+        "clocks": clocks,
+        "wall_s": t_wall,
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

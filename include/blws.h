@@ -1,0 +1,206 @@
+/* blws.h -- C ABI of the GB300 (sm_103a) block-Lanczos-with-warm-start library.
+ *
+ * Method: Lin & Wei, "A Block Lanczos with Warm Start Technique for
+ * Accelerating Nuclear Norm Minimization Algorithms".  Every nuclear-norm
+ * solver evaluates, once per iteration, the singular value thresholding
+ *     A = T_eps(W) = U Theta_eps(S) V^T,  Theta_eps(x) = sgn(x) max(|x|-eps, 0)
+ * (Section 1, Eq. (3)-(4)).  BLWS computes the needed partial SVD by block
+ * Lanczos on the augmented matrix [[0, W], [W^T, 0]] (Theorem 1, Eq. (7)),
+ * restarted from the previous iteration's singular subspaces (Section 4,
+ * "BLWS"; mixed start of Section 4.1) for a few blocks only (Section 4.1),
+ * with the number of output pairs following the predicted rank (Section 4.2).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major (LAPACK order) with an explicit leading
+ *     dimension; all array arguments are DEVICE pointers owned by the caller
+ *     unless the comment says "host".  The library never frees them.
+ *   - Scalars are FP64.  Sparse indices are 0-based int32 (CSR).
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All device work of a call is enqueued on it.  The
+ *     solvers and blws_svt synchronise `stream` before returning, because
+ *     they return host-side results (counts, iteration info).
+ *   - The library owns its workspace (grown on demand, freed by
+ *     blws_destroy).  A context is not thread-safe: use one context per host
+ *     thread / stream.
+ *   - No exception crosses the ABI.  A negative return is an error; the
+ *     message of the last error is available from blws_last_error().
+ */
+#ifndef BLWS_H
+#define BLWS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int blws_status;
+#define BLWS_OK 0
+#define BLWS_EINVAL (-1)      /* bad argument (size, pointer, parameter) */
+#define BLWS_ENOMEM (-2)      /* device allocation failed */
+#define BLWS_ECUDA (-3)       /* a CUDA call or kernel launch failed */
+#define BLWS_ENOCONV (-4)     /* a solver hit max_iter before its tolerance */
+#define BLWS_ENONFINITE (-5)  /* NaN/Inf met in an input or an iterate */
+#define BLWS_ETIMEOUT (-6)    /* a bounded device wait gave up */
+#define BLWS_ENOTSUP (-7)     /* requested mode not built for this device */
+
+/* Arithmetic of the block products (a2, a9).  The small steps (Cholesky of
+ * the Gram matrix, the eigenproblem of T_k, the count of values above eps)
+ * are FP64 in every mode. */
+#define BLWS_PREC_FP64 0      /* all arithmetic FP64 */
+
+typedef struct blws_ctx blws_ctx;
+
+typedef struct {
+  int k;          /* Lanczos blocks per warm-started call (paper's k, Section
+                     4.1; the paper typically uses 2).  Default 3. */
+  int k_cold;     /* blocks for a cold start (no previous subspace), run with
+                     full reorthogonalisation.  Default 4. */
+  int precision;  /* BLWS_PREC_* ; default BLWS_PREC_FP64 */
+  uint64_t seed;  /* seed of the counter-based generator (Philox4x32-10) that
+                     draws extra start columns.  Default 0x5eed. */
+  int device;     /* CUDA device ordinal the context binds to.  Default 0. */
+} blws_config;
+
+/* Fill *cfg with the defaults above.  Never fails for a non-NULL cfg. */
+blws_status blws_config_default(blws_config* cfg);
+
+/* Create a context bound to cfg->device (cfg NULL: defaults).  *ctx receives
+ * the handle; release it with blws_destroy. */
+blws_status blws_create(blws_ctx** ctx, const blws_config* cfg);
+blws_status blws_destroy(blws_ctx* ctx);
+
+/* Number of kernels this context has launched so far (host counter, exact). */
+uint64_t blws_launch_count(const blws_ctx* ctx);
+
+/* Text of a status code (static string). */
+const char* blws_status_str(blws_status s);
+/* Message of the last error recorded on ctx (static per ctx; "" if none). */
+const char* blws_last_error(const blws_ctx* ctx);
+
+/* The operator W (m x n) of one SVT evaluation.
+ *   dense:  W != NULL, column-major with leading dimension ldw >= m.
+ *   sparse: W == NULL, CSR (rowptr[m+1], colidx[nnz], val[nnz]) plus an
+ *           optional low-rank term Ul diag(sl) Vl^T (rl columns, Ul m x rl
+ *           with ld m, Vl n x rl with ld n; rl = 0 means none).  This is the
+ *           "sparse residual plus low-rank" input of matrix completion. */
+typedef struct {
+  int m, n;
+  const double* W;
+  int ldw;
+  int nnz;
+  const int* rowptr;
+  const int* colidx;
+  const double* val;
+  int rl;
+  const double* Ul;
+  const double* sl;
+  const double* Vl;
+} blws_op;
+
+/* One SVT evaluation T_eps(W) by BLWS (Sections 4, 4.1, 4.2; Eq. (4)).
+ *
+ *   eps     threshold (> 0).
+ *   r       Ritz pairs to output (the predicted rank), 1 <= r <= min(m, n).
+ *   U0, V0  warm start: the previous principal subspaces, m x w and n x w
+ *           (ld m and n); w = 0 means cold start (U0, V0 ignored).
+ *   G, g    optional extra start columns ((m+n) x g, ld m+n) appended after
+ *           the warm block; when G == NULL and r > w the library draws
+ *           b - w = r - w (cold start: r) columns itself with its seeded
+ *           generator.  The block width is b = max(r, w + g).
+ *   U, V    out: the r leading Ritz vectors as left/right singular vectors,
+ *           m x r and n x r (ld m and n), the sqrt(2)-scaled halves of the
+ *           Ritz vectors of the augmented matrix (Theorem 1).
+ *   sigma   out: the r leading Ritz values, decreasing.
+ *   count   out (host): #{sigma_t > eps}; A = U[:, :c] diag(sigma - eps) V^T.
+ *   Requires 1 <= r <= b and k*b <= m + n (k the context's block count, or
+ *   k_cold on a cold start).  The call synchronises `stream`. */
+blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r,
+                     const double* U0, const double* V0, int w,
+                     const double* G, int g,
+                     double* U, double* V, double* sigma, int* count,
+                     void* stream);
+
+/* Step a2 alone: P = W~ X for the augmented matrix without forming it
+ * (Section 4, end): P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m].
+ *   X   (m+n) x b, leading dimension ldx >= m+n (device, FP64)
+ *   P   (m+n) x b, leading dimension ldp >= m+n (device, FP64, output)
+ * The building block every BLWS step repeats k times; exported so callers
+ * (and benchmarks) can run and time it on its own.  Does not synchronise. */
+blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx, int b,
+                       double* P, int ldp, void* stream);
+
+/* Robust PCA (Section 5, Table 1): min ||A||_* + lambda ||E||_1 s.t. D = A+E
+ * by inexact ALM with every SVT evaluated by BLWS. */
+typedef struct {
+  double lambda;   /* <= 0: 1/sqrt(max(m, n)) */
+  double tol;      /* stop when ||D - A - E||_F / ||D||_F < tol.  Default 1e-7 */
+  int max_iter;    /* default 1000 */
+  double rho;      /* mu growth factor, default 1.5 */
+  double mu0;      /* <= 0: 1.25 / ||D||_2 */
+  double mu_bar_ratio; /* mu cap = ratio * mu0, default 1e7 */
+  int sv0;         /* initial predicted rank, default 10 */
+} rpca_params;
+
+typedef struct {
+  int iters;        /* outer iterations run */
+  int rank;         /* #{sigma > 1/mu} at the last iteration = rank(A) */
+  int64_t nnzE;     /* nonzeros of E */
+  double residual;  /* ||D - A - E||_F / ||D||_F at exit */
+  double norm_two;  /* the estimate of ||D||_2 used for mu0 and Y0 */
+  int status;       /* BLWS_OK or BLWS_ENOCONV */
+} rpca_info;
+
+blws_status rpca_params_default(rpca_params* p);
+
+/* D, A, E: m x n, column-major, common leading dimension ld >= m, FP64.
+ * A and E are outputs (overwritten).  Returns BLWS_ENOCONV (with A, E the
+ * last iterate and info filled) if max_iter is reached. */
+blws_status rpca_solve(blws_ctx* ctx, const double* D, int m, int n, int ld,
+                       const rpca_params* p, double* A, double* E,
+                       rpca_info* info, void* stream);
+
+/* Matrix completion (Section 5, Table 2) from the observed entries of M on
+ * Omega (CSR, sorted column indices within a row, no duplicates).
+ *   variant 0: SVT of [Cai08] (the paper's host): Y^0 = k0 delta P_Omega(M),
+ *              X^k = T_tau(Y^{k-1}), Y^k = Y^{k-1} + delta P_Omega(M - X^k).
+ *   variant 1: proximal / FPC form: W_k = X_k + delta P_Omega(M - X_k)
+ *              (low-rank + sparse operator), X_{k+1} = T_tau(W_k) with tau
+ *              continuation. */
+typedef struct {
+  int variant;      /* 0 SVT, 1 PROX */
+  double tau;       /* <= 0: 5 sqrt(m n) (SVT); ignored by PROX */
+  double delta;     /* <= 0: 1.2 m n / nnz (SVT); 1 (PROX) */
+  double tol;       /* stop on ||P_Omega(X - M)||_F / ||P_Omega M||_F <= tol; default 1e-4 */
+  int max_iter;     /* default 500 (SVT), 1000 (PROX) */
+  int incr;         /* SVT rank increment l of [Cai08], default 5 */
+  double eta;       /* PROX continuation factor, default 0.25 */
+  double tau_min_rel; /* PROX floor tau_min = tau_min_rel * ||P_Omega M||_2, default 1e-4 */
+  double xtol;      /* PROX: lower tau when ||dX||_F / max(1, ||X||_F) < xtol; default 1e-3 */
+} mc_params;
+
+typedef struct {
+  int iters;
+  int rank;         /* columns of the returned factors */
+  double residual;  /* observed relative residual at exit */
+  double norm_two;  /* the estimate of ||P_Omega M||_2 */
+  int status;
+} mc_info;
+
+blws_status mc_params_default(mc_params* p);
+
+/* Output: X = U diag(theta) V^T with rank <= max_rank columns: U m x
+ * max_rank (ld m), V n x max_rank (ld n), theta max_rank entries; columns
+ * past info->rank are zero.  Returns BLWS_EINVAL if the rank would exceed
+ * max_rank, BLWS_ENOCONV at max_iter. */
+blws_status mc_solve(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr,
+                     const int* colidx, const double* vals,
+                     const mc_params* p, int max_rank,
+                     double* U, double* theta, double* V,
+                     mc_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLWS_H */

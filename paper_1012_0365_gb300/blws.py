@@ -1,0 +1,266 @@
+"""Thin ctypes binding of the BLWS C ABI (``include/blws.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA library
+``_lib/libblws.so``.  There is no fallback: if the library is missing the
+calls raise.  Arrays are torch tensors on the GPU holding FP64 data in
+column-major (LAPACK) order; ``colmajor(x)`` makes such a tensor from any
+(m, n) tensor, and results come back as column-major views of shape (m, n).
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libblws.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+
+# every symbol include/blws.h declares
+EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
+           "blws_last_error", "blws_launch_count", "blws_apply", "blws_svt", "rpca_params_default", "rpca_solve",
+           "mc_params_default", "mc_solve")
+
+
+class BlwsConfig(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("k_cold", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("device", ctypes.c_int)]
+
+
+class BlwsOp(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("W", ctypes.c_void_p),
+                ("ldw", ctypes.c_int), ("nnz", ctypes.c_int), ("rowptr", ctypes.c_void_p),
+                ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("rl", ctypes.c_int),
+                ("Ul", ctypes.c_void_p), ("sl", ctypes.c_void_p), ("Vl", ctypes.c_void_p)]
+
+
+class RpcaParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("rho", ctypes.c_double), ("mu0", ctypes.c_double), ("mu_bar_ratio", ctypes.c_double),
+                ("sv0", ctypes.c_int)]
+
+
+class RpcaInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rank", ctypes.c_int), ("nnzE", ctypes.c_int64),
+                ("residual", ctypes.c_double), ("norm_two", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+class McParams(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tau", ctypes.c_double), ("delta", ctypes.c_double),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("incr", ctypes.c_int),
+                ("eta", ctypes.c_double), ("tau_min_rel", ctypes.c_double),
+                ("xtol", ctypes.c_double)]
+
+
+class McInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("rank", ctypes.c_int), ("residual", ctypes.c_double),
+                ("norm_two", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Open the library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("BLWS CUDA library not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.blws_config_default.argtypes = [ctypes.POINTER(BlwsConfig)]
+    lib.blws_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(BlwsConfig)]
+    lib.blws_destroy.argtypes = [vp]
+    lib.blws_status_str.argtypes = [ci]
+    lib.blws_status_str.restype = ctypes.c_char_p
+    lib.blws_last_error.argtypes = [vp]
+    lib.blws_last_error.restype = ctypes.c_char_p
+    lib.blws_svt.argtypes = [vp, ctypes.POINTER(BlwsOp), cd, ci, vp, vp, ci, vp, ci, vp, vp, vp,
+                             ctypes.POINTER(ci), vp]
+    lib.blws_apply.argtypes = [vp, ctypes.POINTER(BlwsOp), vp, ci, ci, vp, ci, vp]
+    lib.rpca_params_default.argtypes = [ctypes.POINTER(RpcaParams)]
+    lib.rpca_solve.argtypes = [vp, vp, ci, ci, ci, ctypes.POINTER(RpcaParams), vp, vp,
+                               ctypes.POINTER(RpcaInfo), vp]
+    lib.mc_params_default.argtypes = [ctypes.POINTER(McParams)]
+    lib.mc_solve.argtypes = [vp, ci, ci, ci, vp, vp, vp, ctypes.POINTER(McParams), ci, vp, vp, vp,
+                             ctypes.POINTER(McInfo), vp]
+    lib.blws_launch_count.argtypes = [vp]
+    for f in EXPORTS:
+        if f not in ("blws_status_str", "blws_last_error"):
+            getattr(lib, f).restype = ci
+    lib.blws_launch_count.restype = ctypes.c_uint64
+    _lib = lib
+    return lib
+
+
+class BlwsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (%d): %s" % (load().blws_status_str(status).decode(), status, msg))
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(x):
+    """A column-major FP64 CUDA copy of the (m, n) tensor x (view of shape (m, n))."""
+    torch = _torch()
+    x = x.to(device="cuda", dtype=torch.float64) if x.device.type != "cuda" or x.dtype != torch.float64 else x
+    return x.t().contiguous().t()
+
+
+def empty_colmajor(m, n, device="cuda"):
+    torch = _torch()
+    return torch.empty((n, m), dtype=torch.float64, device=device).t()
+
+
+def _check_colmajor(x, m, n, name):
+    torch = _torch()
+    if x.dtype != torch.float64 or x.device.type != "cuda":
+        raise ValueError("%s must be a float64 CUDA tensor" % name)
+    if tuple(x.shape) != (m, n) or (n > 1 and x.stride(1) != m) or (m > 1 and x.stride(0) != 1):
+        raise ValueError("%s must be a column-major (%d, %d) tensor" % (name, m, n))
+
+
+def _ptr(x):
+    return ctypes.c_void_p(0 if x is None else x.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns a blws_ctx (workspace, generator state) bound to one device."""
+
+    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0):
+        lib = load()
+        cfg = BlwsConfig()
+        lib.blws_config_default(ctypes.byref(cfg))
+        cfg.k, cfg.k_cold, cfg.seed, cfg.device = k, k_cold, seed, device
+        h = ctypes.c_void_p()
+        st = lib.blws_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != OK:
+            raise BlwsError(st, "blws_create")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().blws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self):
+        """Kernels launched through this context so far."""
+        return int(load().blws_launch_count(self._h))
+
+    def _raise(self, st, what):
+        raise BlwsError(st, "%s: %s" % (what, load().blws_last_error(self._h).decode()))
+
+    # ------------------------------------------------------------------ SVT --
+    def blws_svt(self, W, eps, r, U0=None, V0=None, G=None, stream=None, sparse=None):
+        """One SVT evaluation by BLWS.  W: column-major (m, n) FP64 CUDA tensor,
+        or None with sparse=(m, n, rowptr, colidx, val[, Ul, sl, Vl]).
+        Returns (U (m, r), V (n, r), sigma (r,), count)."""
+        torch = _torch()
+        op = BlwsOp()
+        if W is not None:
+            m, n = W.shape
+            _check_colmajor(W, m, n, "W")
+            op.m, op.n, op.W, op.ldw = m, n, W.data_ptr(), m
+        else:
+            m, n, rowptr, colidx, val = sparse[:5]
+            op.m, op.n, op.W, op.ldw = m, n, None, m
+            op.nnz, op.rowptr, op.colidx, op.val = int(val.numel()), rowptr.data_ptr(), colidx.data_ptr(), val.data_ptr()
+            if len(sparse) > 5:
+                Ul, sl, Vl = sparse[5:8]
+                op.rl, op.Ul, op.sl, op.Vl = int(sl.numel()), Ul.data_ptr(), sl.data_ptr(), Vl.data_ptr()
+        w = 0 if U0 is None else U0.shape[1]
+        if w:
+            _check_colmajor(U0, m, w, "U0")
+            _check_colmajor(V0, n, w, "V0")
+        g = 0 if G is None else G.shape[1]
+        if g:
+            _check_colmajor(G, m + n, g, "G")
+        U = empty_colmajor(m, r)
+        V = empty_colmajor(n, r)
+        sigma = torch.empty(r, dtype=torch.float64, device="cuda")
+        cnt = ctypes.c_int(0)
+        st = load().blws_svt(self._h, ctypes.byref(op), float(eps), int(r), _ptr(U0), _ptr(V0), w,
+                             _ptr(G), g, _ptr(U), _ptr(V), _ptr(sigma), ctypes.byref(cnt),
+                             _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_svt")
+        return U, V, sigma, cnt.value
+
+    def apply(self, W, X, P=None, stream=None):
+        """P = [W X_v; W^T X_u] (one product with the augmented matrix).
+        W column-major (m, n); X column-major (m+n, b).  Does not synchronise."""
+        m, n = W.shape
+        _check_colmajor(W, m, n, "W")
+        b = X.shape[1]
+        _check_colmajor(X, m + n, b, "X")
+        P = empty_colmajor(m + n, b) if P is None else P
+        op = BlwsOp()
+        op.m, op.n, op.W, op.ldw = m, n, W.data_ptr(), m
+        st = load().blws_apply(self._h, ctypes.byref(op), _ptr(X), m + n, b, _ptr(P), m + n,
+                               _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_apply")
+        return P
+
+    # ----------------------------------------------------------------- RPCA --
+    def rpca_solve(self, D, lam=0.0, tol=1e-7, max_iter=1000, rho=1.5, sv0=10, mu0=0.0,
+                   mu_bar_ratio=1e7, A=None, E=None, stream=None, allow_noconv=False):
+        """Robust PCA by inexact ALM with BLWS.  D: column-major (m, n) FP64.
+        Returns (A, E, info dict)."""
+        m, n = D.shape
+        _check_colmajor(D, m, n, "D")
+        A = empty_colmajor(m, n) if A is None else A
+        E = empty_colmajor(m, n) if E is None else E
+        p = RpcaParams()
+        load().rpca_params_default(ctypes.byref(p))
+        p.lambda_, p.tol, p.max_iter, p.rho, p.sv0, p.mu0, p.mu_bar_ratio = lam, tol, max_iter, rho, sv0, mu0, mu_bar_ratio
+        info = RpcaInfo()
+        st = load().rpca_solve(self._h, _ptr(D), m, n, m, ctypes.byref(p), _ptr(A), _ptr(E),
+                               ctypes.byref(info), _stream(stream))
+        if st != OK and not (st == ENOCONV and allow_noconv):
+            self._raise(st, "rpca_solve")
+        return A, E, {"iters": info.iters, "rank": info.rank, "nnzE": info.nnzE,
+                      "residual": info.residual, "norm_two": info.norm_two, "status": info.status}
+
+    # ------------------------------------------------------------------- MC --
+    def mc_solve(self, m, n, rowptr, colidx, vals, max_rank, variant=0, tau=0.0, delta=0.0,
+                 tol=1e-4, max_iter=500, incr=5, eta=0.25, tau_min_rel=1e-4, xtol=1e-3,
+                 stream=None, allow_noconv=False):
+        """Matrix completion (variant 0: SVT, 1: proximal/FPC).  rowptr/colidx
+        int32 CUDA tensors (CSR), vals FP64.  Returns (U, theta, V, info)."""
+        torch = _torch()
+        U = empty_colmajor(m, max_rank)
+        V = empty_colmajor(n, max_rank)
+        th = torch.empty(max_rank, dtype=torch.float64, device="cuda")
+        p = McParams()
+        load().mc_params_default(ctypes.byref(p))
+        p.variant, p.tau, p.delta, p.tol, p.max_iter, p.incr = variant, tau, delta, tol, max_iter, incr
+        p.eta, p.tau_min_rel, p.xtol = eta, tau_min_rel, xtol
+        info = McInfo()
+        st = load().mc_solve(self._h, m, n, int(vals.numel()), _ptr(rowptr), _ptr(colidx), _ptr(vals),
+                             ctypes.byref(p), int(max_rank), _ptr(U), _ptr(th), _ptr(V),
+                             ctypes.byref(info), _stream(stream))
+        if st != OK and not (st == ENOCONV and allow_noconv):
+            self._raise(st, "mc_solve")
+        r = info.rank
+        return U[:, :r], th[:r], V[:, :r], {"iters": info.iters, "rank": r,
+                                            "residual": info.residual, "norm_two": info.norm_two,
+                                            "status": info.status}

@@ -1,0 +1,181 @@
+// Block Lanczos with warm start on the augmented matrix W~ = [[0, W], [W^T, 0]].
+//
+//   * start block (Section 4.1, mixed start): X~_1 = [U_{i-1}; V_{i-1}] / sqrt 2,
+//     padded with extra columns when the predicted rank exceeds the warm
+//     width (Section 4.2), orthonormalised by CholeskyQR2;
+//   * Algorithm 2 with W~ applied by skipping its zero blocks (Section 4, end):
+//     P_l = [W X_{l,v}; W^T X_{l,u}],  M_l = sym(X_l^T P_l),
+//     R_l = P_l - X_l M_l - X_{l-1} B_{l-1}^T,  (X_{l+1}, B_l) = qr(R_l);
+//     R_l is projected once more against X_l, X_{l-1} before its QR (with a
+//     warm start R_l is small and its computed direction carries rounding
+//     error along X_l), or against every block on a cold start;
+//   * T_k assembled as in Eq. (11), its EVD in decreasing order (Algorithm 3);
+//   * Ritz lift U = sqrt2 Q_u Z(:, 1:r), V = sqrt2 Q_v Z(:, 1:r) (Theorem 1).
+#include <math.h>
+
+#include <algorithm>
+
+#include "blws_core.cuh"
+
+namespace blws {
+
+namespace {
+
+constexpr double kDeflTol = 1e-12;
+
+__global__ void build_start(int m, int n, int w, const double* __restrict__ U0, int ldu0,
+                            const double* __restrict__ V0, int ldv0, const double* __restrict__ G,
+                            int ldg, int g, int b, uint64_t seed, uint32_t stream_id, double* X,
+                            int ldx) {
+  const int N = m + n;
+  const double r2 = 0.70710678118654752440;
+  const size_t total = (size_t)N * b;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    double v;
+    if (j < w) {
+      v = (i < m ? U0[i + (size_t)j * ldu0] : V0[(i - m) + (size_t)j * ldv0]) * r2;
+    } else if (j - w < g) {
+      v = G[i + (size_t)(j - w) * ldg];
+    } else {
+      v = philox_normal(seed, (uint32_t)i, (uint32_t)j, stream_id);
+    }
+    X[i + (size_t)j * ldx] = v;
+  }
+}
+
+// T(l*b + i, l*b + j) = (M_ij + M_ji) / 2
+__global__ void put_sym_block(int b, const double* __restrict__ M, double* T, int ldt, int off) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b * b; e += gridDim.x * blockDim.x) {
+    const int i = e % b, j = e / b;
+    T[(off + i) + (size_t)(off + j) * ldt] = 0.5 * (M[i + (size_t)j * b] + M[j + (size_t)i * b]);
+  }
+}
+
+// T((l+1) b + i, l b + j) = B_ij and its transpose (Eq. 11)
+__global__ void put_offdiag_block(int b, const double* __restrict__ B, double* T, int ldt, int row0,
+                                  int col0) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < b * b; e += gridDim.x * blockDim.x) {
+    const int i = e % b, j = e / b;
+    const double v = B[i + (size_t)j * b];
+    T[(row0 + i) + (size_t)(col0 + j) * ldt] = v;
+    T[(col0 + j) + (size_t)(row0 + i) * ldt] = v;
+  }
+}
+
+// sigma[0:r] = lam[0:r]; count = #{sigma_t > eps}
+__global__ void ritz_values(int r, const double* __restrict__ lam, double eps, double* sigma,
+                            int* count) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int t = threadIdx.x; t < r; t += blockDim.x) {
+    sigma[t] = lam[t];
+    c += lam[t] > eps ? 1 : 0;
+  }
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *count = cnt;
+}
+
+}  // namespace
+
+blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
+                     double* P, int ldp) {
+  const int m = op.m, n = op.n;
+  if (op.W) {
+    BLWS_TRY(gemm(ctx, s, false, false, m, b, n, 1.0, op.W, op.ldw, X + m, ldx, 0.0, P, ldp));
+    BLWS_TRY(gemm(ctx, s, true, false, n, b, m, 1.0, op.W, op.ldw, X, ldx, 0.0, P + m, ldp));
+    return BLWS_OK;
+  }
+  return apply_sparse(ctx, s, op, X, ldx, b, P, ldp);
+}
+
+blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax) {
+  const size_t N = (size_t)m + n;
+  const size_t kb = (size_t)kmax * bmax;
+  void* p;
+  BLWS_TRY(ctx->get(BUF_Q, N * kb * sizeof(double), &p));
+  BLWS_TRY(ctx->get(BUF_P, N * bmax * sizeof(double), &p));
+  BLWS_TRY(ctx->get(BUF_P2, N * bmax * sizeof(double), &p));
+  BLWS_TRY(ctx->get(BUF_T, (3 * kb * kb + 2 * kb + (size_t)bmax * bmax * 2 + 64) * sizeof(double), &p));
+  BLWS_TRY(ctx->get(BUF_SMALL, 6 * (size_t)bmax * bmax * sizeof(double), &p));
+  // split-K partials: at most 2 * target * BM * BN doubles (see gemm_f64.cu)
+  BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)4 * ctx->sms * 64 * 64 * sizeof(double) + (size_t)6 * kb * kb * sizeof(double), &p));
+  const size_t Ne = kb + (kb & 1);
+  BLWS_TRY(ctx->get(BUF_EIG, 3 * Ne * Ne * sizeof(float) + 6 * kb * kb * sizeof(double) +
+                                 (4 * kb + 3 * 1024 + 64) * sizeof(double), &p));
+  BLWS_TRY(ctx->get(BUF_RED, (size_t)ctx->sms * 8 * sizeof(double), &p));
+  return BLWS_OK;
+}
+
+blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a,
+                     double* U, int ldu, double* V, int ldv, double* sigma, int* count_dev) {
+  const int m = op.m, n = op.n, N = m + n;
+  const int w = a.w, g = a.G ? a.g : 0;
+  const int b = std::max(a.r, w + g);
+  const int k = a.k;
+  const int kb = k * b;
+  if (a.r < 1 || b < 1 || kb > N || a.r > b)
+    return ctx->fail(BLWS_EINVAL, "blws: need 1 <= r <= b and k*b <= m+n (r=%d b=%d k=%d m+n=%d)",
+                     a.r, b, k, N);
+  BLWS_TRY(blws_reserve(ctx, m, n, b, k));
+  double *Q, *P, *P2, *T, *scal;
+  BLWS_TRY(ctx->get(BUF_Q, (size_t)N * kb, &Q));
+  BLWS_TRY(ctx->get(BUF_P, (size_t)N * b, &P));
+  BLWS_TRY(ctx->get(BUF_P2, (size_t)N * b, &P2));
+  BLWS_TRY(ctx->get(BUF_T, (size_t)3 * kb * kb + 2 * kb + (size_t)b * b * 2 + 64, &T));
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  double* Z = T + (size_t)kb * kb;
+  double* lam = Z + (size_t)kb * kb;
+  double* Mtmp = lam + 2 * kb;  // b x b
+  double* Bblk = Mtmp + (size_t)b * b;
+  // second-projection coefficients, (k b) x b <= kb * kb: the Z area is free until the EVD
+  double* C = Z;
+
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(T, 0, sizeof(double) * kb * kb, s));
+  const int eb = std::min(ceil_div((long long)N * b, 256), ctx->sms * 8);
+  build_start<<<eb, 256, 0, s>>>(m, n, w, a.U0, a.ldu0, a.V0, a.ldv0, a.G, a.ldg, g, b,
+                                 ctx->cfg.seed, a.draw, P, N);
+  BLWS_CHECK_LAUNCH(ctx);
+  // orthonormalise the start block: deflation scale = its largest column norm
+  BLWS_TRY(col_norms(ctx, s, N, b, P, N, lam, scal + SLOT_AUX));
+  BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Q, P2, Bblk, scal + SLOT_AUX, kDeflTol));
+
+  for (int l = 0; l < k; ++l) {
+    double* Xl = Q + (size_t)l * b * N;
+    BLWS_TRY(apply_op(ctx, s, op, Xl, N, b, P, N));
+    if (l == 0) BLWS_TRY(col_norms(ctx, s, N, b, P, N, lam, scal + SLOT_SCALE));
+    BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, Xl, N, P, N, 0.0, Mtmp, b));
+    put_sym_block<<<ceil_div((long long)b * b, 256), 256, 0, s>>>(b, Mtmp, T, kb, l * b);
+    BLWS_CHECK_LAUNCH(ctx);
+    if (l == k - 1) break;
+    const double* Ml = T + (size_t)l * b + (size_t)l * b * kb;
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl, N, Ml, kb, 1.0, P, N));
+    if (l > 0) {
+      const double* Bt = T + (size_t)(l - 1) * b + (size_t)l * b * kb;  // B_{l-1}^T block
+      BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl - (size_t)b * N, N, Bt, kb, 1.0, P, N));
+    }
+    // second projection against the recurrence's blocks (all blocks when cold)
+    const int c0 = a.cold ? 0 : std::max(l - 1, 0);
+    const int cols = (l + 1 - c0) * b;
+    const double* base = Q + (size_t)c0 * b * N;
+    BLWS_TRY(gemm(ctx, s, true, false, cols, b, N, 1.0, base, N, P, N, 0.0, C, cols));
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, cols, -1.0, base, N, C, cols, 1.0, P, N));
+    BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Xl + (size_t)b * N, P2, Bblk, scal + SLOT_SCALE, kDeflTol));
+    put_offdiag_block<<<ceil_div((long long)b * b, 256), 256, 0, s>>>(b, Bblk, T, kb, (l + 1) * b,
+                                                                       l * b);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
+  BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z));
+  const double r2 = 1.41421356237309504880;
+  BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu));
+  BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv));
+  ritz_values<<<1, 256, 0, s>>>(a.r, lam, a.eps, sigma, count_dev);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+}  // namespace blws

@@ -1,0 +1,58 @@
+// The BLWS procedure and the operator it is applied to.
+#pragma once
+#include "ops.cuh"
+
+namespace blws {
+
+// W (m x n): dense FP64 column-major, or CSR (+ CSC mirror) plus an optional
+// low-rank term Ul diag(sl) Vl^T.
+struct Operator {
+  int m = 0, n = 0;
+  const double* W = nullptr;
+  int ldw = 0;
+  // sparse part
+  int nnz = 0;
+  const int* rowptr = nullptr;
+  const int* colidx = nullptr;
+  const double* val = nullptr;
+  const int* colptr = nullptr;  // CSC mirror of the pattern
+  const int* rowidx = nullptr;
+  const int* perm = nullptr;    // CSC entry e is CSR entry perm[e]
+  // low-rank part
+  int rl = 0;
+  const double* Ul = nullptr;
+  const double* sl = nullptr;
+  const double* Vl = nullptr;
+};
+
+struct BlwsArgs {
+  double eps = 0.0;
+  int r = 1;                 // Ritz pairs to output
+  const double* U0 = nullptr;
+  int ldu0 = 0;
+  const double* V0 = nullptr;
+  int ldv0 = 0;
+  int w = 0;                 // warm columns
+  const double* G = nullptr;  // extra start columns ((m+n) x g)
+  int ldg = 0;
+  int g = 0;
+  int k = 3;                 // blocks
+  bool cold = false;         // full reorthogonalisation (no previous subspace)
+  uint32_t draw = 0;         // generator stream of the extra columns (per call)
+};
+
+// P = W~ X: P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m]
+blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
+                     double* P, int ldp);
+blws_status apply_sparse(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx,
+                         int b, double* P, int ldp);
+
+// Size every workspace buffer one BLWS call of width <= bmax, <= kmax blocks needs.
+blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax);
+
+// One BLWS evaluation: writes U (m x r), V (n x r), sigma (r) and the count
+// #{sigma > eps} to count_dev (device int).
+blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a, double* U,
+                     int ldu, double* V, int ldv, double* sigma, int* count_dev);
+
+}  // namespace blws

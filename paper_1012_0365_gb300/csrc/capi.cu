@@ -1,0 +1,281 @@
+// C ABI of the library (include/blws.h): argument checks, context, buffers.
+#include <stdarg.h>
+
+#include <algorithm>
+#include <new>
+
+#include "mc_kernels.cuh"
+#include "solver.cuh"
+
+namespace blws {
+
+blws_status Ctx::fail(blws_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(last_error, sizeof(last_error), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+blws_status Ctx::get(Buf b, size_t bytes, void** out) {
+  if (bytes == 0) bytes = 256;
+  if (bytes > cap[b]) {
+    if (buf[b]) {
+      // growth happens between solver phases; make sure nothing still uses it
+      BLWS_TRY_CUDA(this, cudaDeviceSynchronize());
+      BLWS_TRY_CUDA(this, cudaFree(buf[b]));
+      buf[b] = nullptr;
+      cap[b] = 0;
+    }
+    const size_t want = std::max(bytes, cap[b] + cap[b] / 2);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BLWS_ENOMEM, "cudaMalloc(%zu) for workspace buffer %d: %s", want, (int)b,
+                  cudaGetErrorString(e));
+    }
+    buf[b] = p;
+    cap[b] = want;
+  }
+  *out = buf[b];
+  return BLWS_OK;
+}
+
+}  // namespace blws
+
+using blws::Ctx;
+
+namespace {
+
+bool dev_ptr_ok(const void* p) { return p != nullptr; }
+
+blws_status bind_device(blws_ctx* ctx) {
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return ctx->fail(BLWS_ECUDA, "cudaSetDevice(%d): %s", ctx->device, cudaGetErrorString(e));
+  return BLWS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+blws_status blws_config_default(blws_config* cfg) {
+  if (!cfg) return BLWS_EINVAL;
+  cfg->k = 3;
+  cfg->k_cold = 4;
+  cfg->precision = BLWS_PREC_FP64;
+  cfg->seed = 0x5eedull;
+  cfg->device = 0;
+  return BLWS_OK;
+}
+
+blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
+  if (!out) return BLWS_EINVAL;
+  *out = nullptr;
+  blws_config c;
+  blws_config_default(&c);
+  if (cfg) c = *cfg;
+  if (c.k < 1 || c.k_cold < 1 || c.precision != BLWS_PREC_FP64) return BLWS_EINVAL;
+  blws_ctx* ctx = new (std::nothrow) blws_ctx();
+  if (!ctx) return BLWS_ENOMEM;
+  ctx->cfg = c;
+  ctx->device = c.device;
+  blws_status st = bind_device(ctx);
+  cudaDeviceProp prop;
+  if (st == BLWS_OK && cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) st = BLWS_ECUDA;
+  if (st == BLWS_OK && prop.major < 10) st = BLWS_ENOTSUP;
+  if (st == BLWS_OK) {
+    ctx->sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMallocHost(&ctx->host_pinned, 64 * sizeof(double)) != cudaSuccess) st = BLWS_ENOMEM;
+  }
+  double* scal = nullptr;
+  if (st == BLWS_OK) st = ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal);
+  if (st == BLWS_OK) {
+    double init[blws::SLOT_MAX] = {0};
+    init[blws::SLOT_ONE] = 1.0;
+    if (cudaMemcpy(scal, init, sizeof(init), cudaMemcpyHostToDevice) != cudaSuccess) st = BLWS_ECUDA;
+  }
+  if (st != BLWS_OK) {
+    cudaGetLastError();
+    blws_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return BLWS_OK;
+}
+
+blws_status blws_destroy(blws_ctx* ctx) {
+  if (!ctx) return BLWS_OK;
+  cudaSetDevice(ctx->device);
+  for (int b = 0; b < blws::BUF_COUNT_; ++b)
+    if (ctx->buf[b]) cudaFree(ctx->buf[b]);
+  if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  delete ctx;
+  return BLWS_OK;
+}
+
+const char* blws_status_str(blws_status s) {
+  switch (s) {
+    case BLWS_OK: return "ok";
+    case BLWS_EINVAL: return "invalid argument";
+    case BLWS_ENOMEM: return "out of device memory";
+    case BLWS_ECUDA: return "CUDA error";
+    case BLWS_ENOCONV: return "not converged within max_iter";
+    case BLWS_ENONFINITE: return "non-finite value";
+    case BLWS_ETIMEOUT: return "device wait timed out";
+    case BLWS_ENOTSUP: return "not supported on this device";
+    default: return "unknown status";
+  }
+}
+
+const char* blws_last_error(const blws_ctx* ctx) { return ctx ? ctx->last_error : ""; }
+
+uint64_t blws_launch_count(const blws_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+static blws_status make_operator(blws_ctx* ctx, const blws_op* W, cudaStream_t s,
+                                 blws::Operator* op) {
+  const int m = W->m, n = W->n;
+  op->m = m;
+  op->n = n;
+  if (W->W) {
+    if (W->ldw < m) return ctx->fail(BLWS_EINVAL, "operator: ldw < m");
+    op->W = W->W;
+    op->ldw = W->ldw;
+    return BLWS_OK;
+  }
+  if (W->nnz < 0 || !W->rowptr || (W->nnz > 0 && (!W->colidx || !W->val)))
+    return ctx->fail(BLWS_EINVAL, "operator: bad CSR part");
+  if (W->rl < 0 || (W->rl > 0 && (!W->Ul || !W->sl || !W->Vl)))
+    return ctx->fail(BLWS_EINVAL, "operator: bad low-rank term");
+  op->nnz = W->nnz;
+  op->rowptr = W->rowptr;
+  op->colidx = W->colidx;
+  op->val = W->val;
+  int *cp, *ri, *pm;
+  BLWS_TRY(blws::build_csc(ctx, s, m, n, W->nnz, W->rowptr, W->colidx, &cp, &ri, &pm));
+  op->colptr = cp;
+  op->rowidx = ri;
+  op->perm = pm;
+  op->rl = W->rl;
+  op->Ul = W->Ul;
+  op->sl = W->sl;
+  op->Vl = W->Vl;
+  return BLWS_OK;
+}
+
+blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx, int b,
+                       double* P, int ldp, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!W || !X || !P) return ctx->fail(BLWS_EINVAL, "blws_apply: null argument");
+  if (W->m < 1 || W->n < 1 || b < 1 || ldx < W->m + W->n || ldp < W->m + W->n)
+    return ctx->fail(BLWS_EINVAL, "blws_apply: bad sizes");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  blws::Operator op;
+  BLWS_TRY(make_operator(ctx, W, s, &op));
+  BLWS_TRY(blws::blws_reserve(ctx, W->m, W->n, b, 1));
+  return blws::apply_op(ctx, s, op, X, ldx, b, P, ldp);
+}
+
+blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const double* U0,
+                     const double* V0, int w, const double* G, int g, double* U, double* V,
+                     double* sigma, int* count, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!W || !U || !V || !sigma || !count) return ctx->fail(BLWS_EINVAL, "blws_svt: null argument");
+  const int m = W->m, n = W->n;
+  if (m < 1 || n < 1) return ctx->fail(BLWS_EINVAL, "blws_svt: empty operator %d x %d", m, n);
+  if (!(eps > 0.0) || r < 1 || r > std::min(m, n) || w < 0 || g < 0)
+    return ctx->fail(BLWS_EINVAL, "blws_svt: need eps > 0, 1 <= r <= min(m, n), w, g >= 0");
+  if (w > 0 && (!dev_ptr_ok(U0) || !dev_ptr_ok(V0)))
+    return ctx->fail(BLWS_EINVAL, "blws_svt: warm start pointers missing");
+  if (g > 0 && !G) return ctx->fail(BLWS_EINVAL, "blws_svt: g > 0 but G is NULL");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  blws::Operator op;
+  BLWS_TRY(make_operator(ctx, W, s, &op));
+  blws::BlwsArgs a;
+  a.eps = eps;
+  a.r = r;
+  a.U0 = U0;
+  a.ldu0 = m;
+  a.V0 = V0;
+  a.ldv0 = n;
+  a.w = w;
+  a.G = g > 0 ? G : nullptr;
+  a.ldg = m + n;
+  a.g = g;
+  a.cold = (w == 0);
+  a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
+  double* scal;
+  BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
+  int* cdev = reinterpret_cast<int*>(scal + blws::SLOT_COUNT);
+  BLWS_TRY(blws::blws_run(ctx, s, op, a, U, m, V, n, sigma, cdev));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  *count = *reinterpret_cast<int*>(ctx->host_pinned + blws::SLOT_COUNT);
+  return BLWS_OK;
+}
+
+blws_status rpca_params_default(rpca_params* p) {
+  if (!p) return BLWS_EINVAL;
+  p->lambda = 0.0;
+  p->tol = 1e-7;
+  p->max_iter = 1000;
+  p->rho = 1.5;
+  p->mu0 = 0.0;
+  p->mu_bar_ratio = 1e7;
+  p->sv0 = 10;
+  return BLWS_OK;
+}
+
+blws_status rpca_solve(blws_ctx* ctx, const double* D, int m, int n, int ld, const rpca_params* p,
+                       double* A, double* E, rpca_info* info, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!D || !A || !E || !info) return ctx->fail(BLWS_EINVAL, "rpca_solve: null argument");
+  if (m < 1 || n < 1 || ld < m) return ctx->fail(BLWS_EINVAL, "rpca_solve: bad size %d x %d ld %d", m, n, ld);
+  rpca_params q;
+  rpca_params_default(&q);
+  if (p) q = *p;
+  if (!(q.tol > 0) || q.max_iter < 1 || !(q.rho >= 1.0) || q.sv0 < 1 || !(q.mu_bar_ratio >= 1.0))
+    return ctx->fail(BLWS_EINVAL, "rpca_solve: bad parameters");
+  BLWS_TRY(bind_device(ctx));
+  return blws::rpca_run(ctx, reinterpret_cast<cudaStream_t>(stream), D, m, n, ld, q, A, E, info);
+}
+
+blws_status mc_params_default(mc_params* p) {
+  if (!p) return BLWS_EINVAL;
+  p->variant = 0;
+  p->tau = 0.0;
+  p->delta = 0.0;
+  p->tol = 1e-4;
+  p->max_iter = 500;
+  p->incr = 5;
+  p->eta = 0.25;
+  p->tau_min_rel = 1e-4;
+  p->xtol = 1e-3;
+  return BLWS_OK;
+}
+
+blws_status mc_solve(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr, const int* colidx,
+                     const double* vals, const mc_params* p, int max_rank, double* U,
+                     double* theta, double* V, mc_info* info, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!rowptr || !U || !theta || !V || !info || (nnz > 0 && (!colidx || !vals)))
+    return ctx->fail(BLWS_EINVAL, "mc_solve: null argument");
+  if (m < 1 || n < 1 || nnz < 0 || (long long)nnz > (long long)m * n || max_rank < 1)
+    return ctx->fail(BLWS_EINVAL, "mc_solve: bad sizes");
+  mc_params q;
+  mc_params_default(&q);
+  if (p) q = *p;
+  if ((q.variant != 0 && q.variant != 1) || !(q.tol > 0) || q.max_iter < 1)
+    return ctx->fail(BLWS_EINVAL, "mc_solve: bad parameters");
+  if (q.variant == 1 && !(q.eta > 0 && q.eta < 1)) return ctx->fail(BLWS_EINVAL, "mc_solve: eta");
+  BLWS_TRY(bind_device(ctx));
+  return blws::mc_run(ctx, reinterpret_cast<cudaStream_t>(stream), m, n, nnz, rowptr, colidx, vals,
+                      q, max_rank, U, theta, V, info);
+}
+
+}  // extern "C"

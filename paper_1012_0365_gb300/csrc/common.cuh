@@ -1,0 +1,142 @@
+// Shared internals of the BLWS library: context, named workspace buffers,
+// error plumbing and the counter-based generator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/blws.h"
+
+namespace blws {
+
+// ---------------------------------------------------------------- errors --
+#define BLWS_TRY_CUDA(ctx, expr)                                                 \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      return (ctx)->fail(e_ == cudaErrorMemoryAllocation ? BLWS_ENOMEM : BLWS_ECUDA, \
+                         "%s:%d %s: %s", __FILE__, __LINE__, #expr,              \
+                         cudaGetErrorString(e_));                                \
+    }                                                                            \
+  } while (0)
+
+// every kernel launch is followed by this check, which also counts it
+#define BLWS_CHECK_LAUNCH(ctx)             \
+  do {                                     \
+    ++(ctx)->launches;                     \
+    BLWS_TRY_CUDA(ctx, cudaGetLastError()); \
+  } while (0)
+
+#define BLWS_TRY(expr)               \
+  do {                               \
+    blws_status s_ = (expr);         \
+    if (s_ != BLWS_OK) return s_;    \
+  } while (0)
+
+// ------------------------------------------------------------- workspace --
+// Named device buffers owned by the context, each grown on demand.  Growth
+// synchronises the device (cudaFree), so it happens outside steady state:
+// a solver sizes its buffers once before its first iteration.
+enum Buf {
+  BUF_Q = 0,     // Lanczos basis Q_k, (m+n) x (k b)
+  BUF_P,         // W~ X_l / residual R_l, (m+n) x b
+  BUF_P2,        // CholeskyQR intermediate, (m+n) x b
+  BUF_T,         // T_k and its eigenvectors, (k b)^2 each (several)
+  BUF_SMALL,     // b x b scratch matrices and vectors
+  BUF_SPLITK,    // split-K partial sums of the GEMMs
+  BUF_EIG,       // eigen-solver scratch
+  BUF_SCAL,      // device scalars (Slot)
+  BUF_WARM_U,    // solver-held warm start U (m x b)
+  BUF_WARM_V,    // solver-held warm start V (n x b)
+  BUF_SIG,       // Ritz values
+  BUF_Y,         // RPCA multiplier Y (m x n)
+  BUF_W,         // RPCA SVT input W (m x n)
+  BUF_E2,        // RPCA second E buffer (m x n)
+  BUF_RED,       // reduction partials
+  BUF_CSC_PTR,   // MC: CSC column pointers
+  BUF_CSC_ROW,   // MC: CSC row indices
+  BUF_CSC_PERM,  // MC: CSR position of each CSC entry
+  BUF_MC_Y,      // MC: values of the sparse iterate on Omega (CSR order)
+  BUF_MC_X,      // MC: low-rank factors of the current X (PROX)
+  BUF_COUNT_
+};
+
+struct Ctx {
+  blws_config cfg;
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+  void* buf[BUF_COUNT_] = {nullptr};
+  size_t cap[BUF_COUNT_] = {0};
+  double* host_pinned = nullptr;  // small pinned staging area for scalars
+  unsigned long long launches = 0; // kernels launched through this context
+  char last_error[512] = {0};
+
+  blws_status fail(blws_status code, const char* fmt, ...);
+  // device buffer `b` with at least `bytes` bytes (grown on demand)
+  blws_status get(Buf b, size_t bytes, void** out);
+  template <typename T>
+  blws_status get(Buf b, size_t count, T** out) {
+    void* p = nullptr;
+    blws_status s = get(b, count * sizeof(T), &p);
+    *out = reinterpret_cast<T*>(p);
+    return s;
+  }
+};
+
+// Device-side scalar slots used by the procedure (one small array).
+enum Slot {
+  SLOT_SCALE = 0,      // deflation scale: largest column norm of W~ X_1
+  SLOT_COUNT = 1,      // #{sigma > eps} (stored as double)
+  SLOT_NORM = 2,       // generic reduction result
+  SLOT_AUX = 3,
+  SLOT_ONE = 4,        // constant 1.0 (set at context creation)
+  SLOT_FLAG = 5,       // int flag (non-finite input seen)
+  SLOT_NNZ = 6,        // unsigned long long counter
+  SLOT_AUX2 = 7,
+  SLOT_MAX = 16
+};
+
+// ------------------------------------------------------- launch helpers --
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ------------------------------------------------- Philox4x32-10 (Salmon,
+// Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC'11):
+// a counter-based generator; each (counter, key) maps to four 32-bit words.
+struct Philox {
+  static constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  static constexpr uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  __host__ __device__ static inline void round(uint32_t c[4], uint32_t k[2]) {
+    uint64_t p0 = (uint64_t)M0 * c[0];
+    uint64_t p1 = (uint64_t)M1 * c[2];
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c[1] ^ k[0];
+    uint32_t n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k[0] += W0; k[1] += W1;
+  }
+  __host__ __device__ static inline void gen(const uint32_t ctr[4], uint64_t key, uint32_t out[4]) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k[2] = {(uint32_t)key, (uint32_t)(key >> 32)};
+#pragma unroll
+    for (int i = 0; i < 10; ++i) round(c, k);
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+  }
+};
+
+// Standard normal from the generator by the Box-Muller transform.
+__device__ inline double philox_normal(uint64_t key, uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t ctr[4] = {a, b, c, 0x243F6A88u}, o[4];
+  Philox::gen(ctr, key, o);
+  const double inv = 1.0 / 4294967296.0;
+  double u1 = ((double)o[0] + 1.0) * inv;  // (0, 1]
+  double u2 = (double)o[1] * inv;          // [0, 1)
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+}  // namespace blws
+
+struct blws_ctx : public blws::Ctx {};

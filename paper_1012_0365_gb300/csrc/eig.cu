@@ -1,0 +1,464 @@
+// Symmetric eigen-decomposition of the projected matrix T_k (Algorithm 3,
+// "EVD of T_k" with eigenvalues in decreasing order).
+//
+// GB300 has FP64 at 1/64 of the FP32 rate, and a one-SM FP64 Jacobi on a
+// few-hundred-wide T_k costs milliseconds.  So the decomposition is done in
+// two stages:
+//   1. cyclic two-sided Jacobi in FP32 with the parallel (round-robin)
+//      ordering, n/2 disjoint rotations per round applied as 2 x 2 block
+//      updates (Golub & Van Loan, Section 8.5): one CTA with T in shared
+//      memory when it fits, else a cooperative grid with one grid barrier per
+//      round;
+//   2. FP64 iterative refinement of the eigenvector matrix by Ogita & Aishima
+//      ("Iterative refinement for symmetric eigenvalue decomposition", 2018),
+//      which uses only matrix products (FP64 GEMMs over the whole GPU):
+//        R = I - X^T X,  S = X^T T X,  lam_i = s_ii / (1 - r_ii),
+//        E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > d,
+//               r_ij / 2 otherwise,   X <- X + X E,
+//      with d = 2 (||S - diag(lam)|| + ||T|| ||R||) (Frobenius bounds here).
+//      Each step squares the error of well-separated pairs; pairs closer than
+//      d stay as an (orthonormalised) basis of their joint eigenspace.
+// Then the pairs are sorted by decreasing eigenvalue.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "ops.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace blws {
+
+namespace {
+
+constexpr int kJacobiMaxSweeps = 20;
+// FP32 stage: stop when off(A)^2 <= tol2 ||A||_F^2, or once a sweep no longer
+// halves off(A)^2 (the FP32 rounding floor); the FP64 refinement does the rest.
+constexpr float kJacobiTol2 = 1e-11f;
+constexpr int kRefineSteps = 3;
+
+__device__ inline bool jacobi_done(int sweep, float off, float tot, float prev_off) {
+  return off <= kJacobiTol2 * tot || (sweep >= 2 && off > 0.5f * prev_off);
+}
+constexpr int kCtaMaxN = 160;       // A and V (FP32) in shared memory up to this size
+
+struct Rot {
+  int p, q;
+  float c, s;
+};
+
+// Round-robin pairing of N (even) indices, round r in [0, N-1): pair k.
+__device__ inline void rr_pair(int N, int r, int k, int& p, int& q) {
+  if (k == 0) {
+    p = r;
+    q = N - 1;
+  } else {
+    p = (r + k) % (N - 1);
+    q = (r - k + (N - 1)) % (N - 1);
+  }
+  if (p > q) {
+    int t = p; p = q; q = t;
+  }
+}
+
+// Jacobi rotation annihilating a_pq (Golub & Van Loan, Algorithm 8.5.1):
+// J = [[c, s], [-s, c]] on (p, q), A' = J^T A J.
+__device__ inline void jacobi_rot(float app, float aqq, float apq, float& c, float& s) {
+  if (fabsf(apq) <= 1e-30f * (fabsf(app) + fabsf(aqq)) || apq == 0.0f) {
+    c = 1.0f;
+    s = 0.0f;
+    return;
+  }
+  const float tau = (aqq - app) / (2.0f * apq);
+  const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+  c = rsqrtf(1.0f + t * t);
+  s = t * c;
+}
+
+// Apply one round to the 2x2 block (i, j): reads Ain, writes Aout (may alias).
+__device__ inline void apply_block(const float* Ain, float* Aout, int N, const Rot& ri, const Rot& rj,
+                                   bool diag) {
+  const size_t pi = ri.p, qi = ri.q, pj = rj.p, qj = rj.q;
+  const float a = Ain[pi + pj * N], b = Ain[pi + qj * N], c = Ain[qi + pj * N], d = Ain[qi + qj * N];
+  // M = A J_j (columns)
+  const float m_ap = rj.c * a - rj.s * b, m_aq = rj.s * a + rj.c * b;  // row p_i
+  const float m_cp = rj.c * c - rj.s * d, m_cq = rj.s * c + rj.c * d;  // row q_i
+  // J_i^T M (rows)
+  float n_pp = ri.c * m_ap - ri.s * m_cp, n_pq = ri.c * m_aq - ri.s * m_cq;
+  float n_qp = ri.s * m_ap + ri.c * m_cp, n_qq = ri.s * m_aq + ri.c * m_cq;
+  if (diag) {  // the annihilated pair
+    n_pq = 0.0f;
+    n_qp = 0.0f;
+  }
+  Aout[pi + pj * N] = n_pp;
+  Aout[pi + qj * N] = n_pq;
+  Aout[qi + pj * N] = n_qp;
+  Aout[qi + qj * N] = n_qq;
+}
+
+// --------------------------------------------- single-CTA Jacobi (smem) --
+__global__ void __launch_bounds__(1024)
+jacobi_cta_kernel(int n, int N, const double* __restrict__ T, float* __restrict__ Vout,
+                  int* __restrict__ sweeps_out) {
+  extern __shared__ float sm[];
+  float* A = sm;
+  float* V = A + (size_t)N * N;
+  __shared__ Rot rot[kCtaMaxN / 2];
+  __shared__ float red_off[32], red_tot[32];
+  __shared__ int stop;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int half = N / 2;
+  for (int e = tid; e < N * N; e += nt) {
+    const int i = e % N, j = e / N;
+    A[e] = (i < n && j < n) ? (float)T[i + (size_t)j * n] : 0.0f;
+    V[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  if (tid == 0) stop = 0;
+  __syncthreads();
+  int sweep = 0;
+  float prev_off = 3.0e38f;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = tid; k < half; k += nt) {
+        Rot R;
+        rr_pair(N, r, k, R.p, R.q);
+        jacobi_rot(A[R.p + R.p * N], A[R.q + R.q * N], A[R.p + R.q * N], R.c, R.s);
+        rot[k] = R;
+      }
+      __syncthreads();
+      for (int e = tid; e < half * half; e += nt) {
+        const int i = e % half, j = e / half;
+        apply_block(A, A, N, rot[i], rot[j], i == j);
+      }
+      for (int e = tid; e < N * half; e += nt) {
+        const int x = e % N, j = e / N;
+        const Rot R = rot[j];
+        const float vp = V[x + (size_t)R.p * N], vq = V[x + (size_t)R.q * N];
+        V[x + (size_t)R.p * N] = R.c * vp - R.s * vq;
+        V[x + (size_t)R.q * N] = R.s * vp + R.c * vq;
+      }
+      __syncthreads();
+    }
+    // convergence: off(A)^2 <= tol^2 ||A||_F^2
+    float off = 0.0f, tot = 0.0f;
+    for (int e = tid; e < N * N; e += nt) {
+      const float v = A[e];
+      tot += v * v;
+      if (e % N != e / N) off += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (tid % 32 == 0) {
+      red_off[tid / 32] = off;
+      red_tot[tid / 32] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.0f, st = 0.0f;
+      for (int w = 0; w < nt / 32; ++w) {
+        so += red_off[w];
+        st += red_tot[w];
+      }
+      red_tot[0] = so;  // broadcast this sweep's off(A)^2
+      stop = jacobi_done(sweep, so, st, prev_off) ? 1 : 0;
+    }
+    __syncthreads();
+    prev_off = red_tot[0];
+    if (stop) {
+      ++sweep;
+      break;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < N * N; e += nt) Vout[e] = V[e];
+  if (tid == 0) *sweeps_out = sweep;
+}
+
+// ------------------------------------- cooperative-grid Jacobi (global) --
+// A0/A1: double-buffered FP32 matrices (N x N); V: FP32 N x N; part: one
+// float2 per CTA for the convergence test.
+__global__ void __launch_bounds__(512)
+jacobi_grid_kernel(int n, int N, const double* __restrict__ T, float* A0, float* A1, float* V,
+                   float2* part, int* sweeps_out) {
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ Rot rot_dyn[];
+  __shared__ float red_off[16], red_tot[16];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const size_t gtid = (size_t)blockIdx.x * nt + tid, gnt = (size_t)gridDim.x * nt;
+  const int half = N / 2;
+  for (size_t e = gtid; e < (size_t)N * N; e += gnt) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    A0[e] = (i < n && j < n) ? (float)T[i + (size_t)j * n] : 0.0f;
+    V[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  grid.sync();
+  float* cur = A0;
+  float* nxt = A1;
+  int sweep = 0;
+  float prev_off = 3.0e38f;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    float off = 0.0f, tot = 0.0f;
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = tid; k < half; k += nt) {
+        Rot R;
+        rr_pair(N, r, k, R.p, R.q);
+        jacobi_rot(cur[R.p + (size_t)R.p * N], cur[R.q + (size_t)R.q * N], cur[R.p + (size_t)R.q * N],
+                   R.c, R.s);
+        rot_dyn[k] = R;
+      }
+      __syncthreads();
+      const bool last = (r == N - 2);
+      for (size_t e = gtid; e < (size_t)half * half; e += gnt) {
+        const int i = (int)(e % half), j = (int)(e / half);
+        apply_block(cur, nxt, N, rot_dyn[i], rot_dyn[j], i == j);
+        if (last) {
+          const Rot& ri = rot_dyn[i];
+          const Rot& rj = rot_dyn[j];
+          const float a = nxt[ri.p + (size_t)rj.p * N], b = nxt[ri.p + (size_t)rj.q * N];
+          const float c = nxt[ri.q + (size_t)rj.p * N], d = nxt[ri.q + (size_t)rj.q * N];
+          tot += a * a + b * b + c * c + d * d;
+          off += (i == j) ? (b * b + c * c) : (a * a + b * b + c * c + d * d);
+        }
+      }
+      for (size_t e = gtid; e < (size_t)N * half; e += gnt) {
+        const int x = (int)(e % N), j = (int)(e / N);
+        const Rot R = rot_dyn[j];
+        const float vp = V[x + (size_t)R.p * N], vq = V[x + (size_t)R.q * N];
+        V[x + (size_t)R.p * N] = R.c * vp - R.s * vq;
+        V[x + (size_t)R.q * N] = R.s * vp + R.c * vq;
+      }
+      float* t = cur;
+      cur = nxt;
+      nxt = t;
+      grid.sync();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (tid % 32 == 0) {
+      red_off[tid / 32] = off;
+      red_tot[tid / 32] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.0f, st = 0.0f;
+      for (int w = 0; w < nt / 32; ++w) {
+        so += red_off[w];
+        st += red_tot[w];
+      }
+      part[blockIdx.x] = make_float2(so, st);
+    }
+    grid.sync();
+    float so = 0.0f, st = 0.0f;
+    for (int c = 0; c < (int)gridDim.x; ++c) {
+      so += part[c].x;
+      st += part[c].y;
+    }
+    grid.sync();  // everyone has read part before it is rewritten
+    const bool done = jacobi_done(sweep, so, st, prev_off);
+    prev_off = so;
+    if (done) {
+      ++sweep;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
+}
+
+// ------------------------------------------------------ refinement helpers --
+__global__ void f32_to_f64_block(int n, int N, const float* __restrict__ V, double* __restrict__ X) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    X[e] = (double)V[i + (size_t)j * N];
+  }
+}
+
+// R <- I - R (in place, R holds X^T X)
+__global__ void identity_minus(int n, double* R) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    R[e] = (i == j ? 1.0 : 0.0) - R[e];
+  }
+}
+
+// partial sums (per CTA): [0] sum_{i!=j} S_ij^2, [1] sum R_ij^2, [2] sum T_ij^2
+__global__ void oa_norms_partial(int n, const double* __restrict__ S, const double* __restrict__ R,
+                                 const double* __restrict__ T, double* part) {
+  __shared__ double red[3][256];
+  double a = 0.0, b = 0.0, c = 0.0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i != j) a = fma(S[e], S[e], a);
+    b = fma(R[e], R[e], b);
+    c = fma(T[e], T[e], c);
+  }
+  red[0][threadIdx.x] = a;
+  red[1][threadIdx.x] = b;
+  red[2][threadIdx.x] = c;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+      red[2][threadIdx.x] += red[2][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x + 0] = red[0][0];
+    part[3 * blockIdx.x + 1] = red[1][0];
+    part[3 * blockIdx.x + 2] = red[2][0];
+  }
+}
+
+// lam_i = s_ii / (1 - r_ii); the diagonal part of ||S - D|| is added to the
+// off-diagonal partials; writes lam[n] and delta (scal[0]).
+__global__ void oa_lambda(int n, int nparts, const double* __restrict__ S, const double* __restrict__ R,
+                          const double* __restrict__ part, double* lam, double* delta) {
+  __shared__ double red[256];
+  double dsum = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double l = S[i + (size_t)i * n] / (1.0 - R[i + (size_t)i * n]);
+    lam[i] = l;
+    const double dv = S[i + (size_t)i * n] - l;
+    dsum = fma(dv, dv, dsum);
+  }
+  red[threadIdx.x] = dsum;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double s_off = red[0], r2 = 0.0, t2 = 0.0;
+    for (int c = 0; c < nparts; ++c) {
+      s_off += part[3 * c + 0];
+      r2 += part[3 * c + 1];
+      t2 += part[3 * c + 2];
+    }
+    *delta = 2.0 * (sqrt(s_off) + sqrt(t2) * sqrt(r2));
+  }
+}
+
+__global__ void oa_correction(int n, const double* __restrict__ S, const double* __restrict__ R,
+                              const double* __restrict__ lam, const double* __restrict__ delta,
+                              double* E) {
+  const double d = *delta;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    const double rij = R[e];
+    double v;
+    if (i == j) {
+      v = 0.5 * rij;
+    } else {
+      const double gap = lam[j] - lam[i];
+      v = (fabs(gap) > d) ? (S[e] + lam[j] * rij) / gap : 0.5 * rij;
+    }
+    E[e] = v;
+  }
+}
+
+// rank of each eigenvalue in decreasing order (ties by index), then scatter
+__global__ void sort_desc(int n, const double* __restrict__ lam_in, const double* __restrict__ X,
+                          double* lam_out, double* Z) {
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    __shared__ int cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const double li = lam_in[i];
+    int c = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double lj = lam_in[j];
+      c += (lj > li || (lj == li && j < i)) ? 1 : 0;
+    }
+    atomicAdd(&cnt, c);  // integer count: order-independent
+    __syncthreads();
+    const int rank = cnt;
+    if (threadIdx.x == 0) lam_out[rank] = li;
+    for (int x = threadIdx.x; x < n; x += blockDim.x) Z[x + (size_t)rank * n] = X[x + (size_t)i * n];
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z) {
+  if (n <= 0) return BLWS_OK;
+  const int N = n + (n & 1);
+  // scratch: FP32 A0, A1, V (N^2 each) ; FP64 X, X2, R, S, TX, E (n^2 each); small vectors
+  float* f = nullptr;
+  BLWS_TRY(ctx->get(BUF_EIG, (size_t)3 * N * N * sizeof(float) + (size_t)6 * n * n * sizeof(double) +
+                                 (size_t)(4 * n + 3 * 1024 + 64) * sizeof(double),
+                    (void**)&f));
+  float* A0 = f;
+  float* A1 = A0 + (size_t)N * N;
+  float* V = A1 + (size_t)N * N;
+  double* X = reinterpret_cast<double*>(V + (size_t)N * N + ((N * N) & 1));  // 8-byte aligned
+  double* X2 = X + (size_t)n * n;
+  double* R = X2 + (size_t)n * n;
+  double* S = R + (size_t)n * n;
+  double* TX = S + (size_t)n * n;
+  double* E = TX + (size_t)n * n;
+  double* lam_u = E + (size_t)n * n;
+  double* part = lam_u + n;
+  double* delta = part + 3 * 1024;
+  int* sweeps = reinterpret_cast<int*>(delta + 8);
+
+  if (N <= kCtaMaxN) {
+    const size_t smem = 2ull * N * N * sizeof(float);
+    BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(jacobi_cta_kernel,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    jacobi_cta_kernel<<<1, 1024, smem, s>>>(n, N, T, V, sweeps);
+    BLWS_CHECK_LAUNCH(ctx);
+  } else {
+    const int threads = 512;
+    const size_t smem = (size_t)(N / 2) * sizeof(Rot);
+    int per_sm = 0;
+    BLWS_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel,
+                                                                     threads, smem));
+    if (per_sm < 1) return ctx->fail(BLWS_ECUDA, "jacobi_grid_kernel cannot be resident");
+    const long long blocks_needed = ((long long)(N / 2) * (N / 2) + threads - 1) / threads;
+    int grid = (int)std::min<long long>(blocks_needed, (long long)ctx->sms);
+    grid = std::max(grid, 1);
+    float2* fpart = reinterpret_cast<float2*>(part);
+    int nn = n, NN = N;
+    void* args[] = {&nn, &NN, (void*)&T, &A0, &A1, &V, &fpart, &sweeps};
+    BLWS_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((void*)jacobi_grid_kernel, grid, threads, args,
+                                                   smem, s));
+    ++ctx->launches;
+  }
+  const int eb = std::min(ceil_div((long long)n * n, 256), ctx->sms * 4);
+  f32_to_f64_block<<<eb, 256, 0, s>>>(n, N, V, X);
+  BLWS_CHECK_LAUNCH(ctx);
+  const int nparts = std::min(eb, 1024);
+  for (int step = 0; step < kRefineSteps; ++step) {
+    BLWS_TRY(gemm(ctx, s, true, false, n, n, n, 1.0, X, n, X, n, 0.0, R, n));
+    identity_minus<<<eb, 256, 0, s>>>(n, R);
+    BLWS_CHECK_LAUNCH(ctx);
+    BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, T, n, X, n, 0.0, TX, n));
+    BLWS_TRY(gemm(ctx, s, true, false, n, n, n, 1.0, X, n, TX, n, 0.0, S, n));
+    oa_norms_partial<<<nparts, 256, 0, s>>>(n, S, R, T, part);
+    BLWS_CHECK_LAUNCH(ctx);
+    oa_lambda<<<1, 256, 0, s>>>(n, nparts, S, R, part, lam_u, delta);
+    BLWS_CHECK_LAUNCH(ctx);
+    oa_correction<<<eb, 256, 0, s>>>(n, S, R, lam_u, delta, E);
+    BLWS_CHECK_LAUNCH(ctx);
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(X2, X, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+    BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, X, n, E, n, 1.0, X2, n));
+    std::swap(X, X2);
+  }
+  sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, lam, Z);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+}  // namespace blws

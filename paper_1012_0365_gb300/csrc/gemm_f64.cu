@@ -1,0 +1,248 @@
+// FP64 GEMM and reductions on CUDA cores (DFMA).
+//
+// On GB300 FP64 runs at 1/64 of the FP32 rate (about 2 DFMA per clock per
+// SM), so every FP64 product here is bound by the DFMA pipe, not by memory:
+// the tiling only has to keep all 152 SMs busy.  Tiles of BM x BN outputs
+// per 256-thread CTA; when the tile count cannot fill the GPU the K range is
+// split and the partial sums are reduced in a fixed order (deterministic, no
+// atomics).
+#include <algorithm>
+
+#include "ops.cuh"
+
+namespace blws {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBK = 16;
+
+template <bool TA, bool TB, int BM, int BN>
+__global__ void __launch_bounds__(kThreads)
+gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __restrict__ A,
+                int lda, const double* __restrict__ B, int ldb, double beta, double* C, int ldc,
+                double* __restrict__ part) {
+  constexpr int TM = BM / 16, TN = BN / 16;
+  __shared__ double As[kBK][BM + 1];
+  __shared__ double Bs[kBK][BN + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < BM * kBK; e += kThreads) {
+      int i, kk;
+      if (!TA) { i = e % BM; kk = e / BM; } else { kk = e % kBK; i = e / kBK; }
+      const int gi = m0 + i, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < kend) v = TA ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda];
+      As[kk][i] = v;
+    }
+#pragma unroll 4
+    for (int e = threadIdx.x; e < kBK * BN; e += kThreads) {
+      int kk, j;
+      if (!TB) { kk = e % kBK; j = e / kBK; } else { j = e % BN; kk = e / BN; }
+      const int gj = n0 + j, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < kend) v = TB ? B[gj + (size_t)gk * ldb] : B[gk + (size_t)gj * ldb];
+      Bs[kk][j] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; ++kk) {
+      double a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + 16 * j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int gi = m0 + tx + 16 * i;
+    if (gi >= M) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int gj = n0 + ty + 16 * j;
+      if (gj >= N) continue;
+      if (part) {
+        part[(size_t)blockIdx.z * M * N + gi + (size_t)gj * M] = acc[i][j];
+      } else {
+        double* c = C + gi + (size_t)gj * ldc;
+        *c = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+      }
+    }
+  }
+}
+
+__global__ void splitk_reduce(int M, int N, int splits, double alpha, const double* __restrict__ part,
+                              double beta, double* C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * total + e];
+    const int i = (int)(e % M), j = (int)(e / M);
+    double* c = C + i + (size_t)j * ldc;
+    *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
+template <bool TA, bool TB, int BM, int BN>
+blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha,
+                         const double* A, int lda, const double* B, int ldb, double beta,
+                         double* C, int ldc) {
+  const int tm = ceil_div(M, BM), tn = ceil_div(N, BN);
+  const int tiles = tm * tn;
+  const int target = 2 * ctx->sms;
+  int splits = 1;
+  if (tiles < target && K > 4 * kBK) {
+    splits = ceil_div(target, tiles);
+    splits = min(splits, ceil_div(K, 4 * kBK));
+    splits = max(splits, 1);
+  }
+  int kchunk = ceil_div(ceil_div(K, splits), kBK) * kBK;
+  splits = ceil_div(K, kchunk);
+  double* part = nullptr;
+  if (splits > 1) BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)splits * M * N, &part));
+  dim3 grid(tm, tn, splits);
+  gemm_f64_kernel<TA, TB, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, alpha, A, lda, B, ldb,
+                                                            beta, C, ldc, part);
+  BLWS_CHECK_LAUNCH(ctx);
+  if (splits > 1) {
+    const size_t total = (size_t)M * N;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sms * 8);
+    splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, alpha, part, beta, C, ldc);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
+  return BLWS_OK;
+}
+
+template <bool TA, bool TB>
+blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
+                   int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+  if (N <= 16) return launch_tiles<TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (N <= 32) return launch_tiles<TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return launch_tiles<TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+// ------------------------------------------------------------ reductions --
+__global__ void sumsq_partial(int M, int N, const double* __restrict__ A, int ld, double* part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double v = A[(e % M) + (e / M) * (size_t)ld];
+    acc = fma(v, v, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void sum_final(int n, const double* __restrict__ part, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+// one warp per column
+__global__ void col_norms_kernel(int M, int N, const double* __restrict__ A, int ld, double* out) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= N) return;
+  const double* a = A + (size_t)warp * ld;
+  double acc = 0.0;
+  for (int i = lane; i < M; i += 32) acc = fma(a[i], a[i], acc);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[warp] = sqrt(acc);
+}
+
+__global__ void max_final(int n, const double* __restrict__ v, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = fmax(acc, v[i]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void scale_kernel(int M, int N, double beta, double* C, int ldc) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    double* c = C + (e % M) + (e / M) * (size_t)ldc;
+    *c = beta == 0.0 ? 0.0 : beta * *c;
+  }
+}
+
+}  // namespace
+
+blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                 const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                 int ldc) {
+  if (M <= 0 || N <= 0) return BLWS_OK;
+  if (K <= 0) {  // C = beta C
+    const size_t total = (size_t)M * N;
+    scale_kernel<<<(int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
+        M, N, beta, C, ldc);
+    BLWS_CHECK_LAUNCH(ctx);
+    return BLWS_OK;
+  }
+  if (!ta && !tb) return gemm_t<false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (ta && !tb) return gemm_t<true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (!ta && tb) return gemm_t<false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return gemm_t<true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
+blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld, double* out) {
+  double* part = nullptr;
+  const int blocks = ctx->sms * 2;
+  BLWS_TRY(ctx->get(BUF_RED, (size_t)blocks, &part));
+  sumsq_partial<<<blocks, 256, 0, s>>>(M, N, A, ld, part);
+  BLWS_CHECK_LAUNCH(ctx);
+  sum_final<<<1, 256, 0, s>>>(blocks, part, out);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld,
+                      double* out, double* colmax) {
+  col_norms_kernel<<<ceil_div((long long)N * 32, 256), 256, 0, s>>>(M, N, A, ld, out);
+  BLWS_CHECK_LAUNCH(ctx);
+  if (colmax) {
+    max_final<<<1, 256, 0, s>>>(N, out, colmax);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
+  return BLWS_OK;
+}
+
+}  // namespace blws

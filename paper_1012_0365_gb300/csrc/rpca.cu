@@ -1,0 +1,394 @@
+// Robust PCA host (Section 5, Table 1): inexact ALM whose SVT (Eq. 3-4) is
+// evaluated by BLWS each iteration.  The paper takes the host from its
+// references; its step rules, written out:
+//   Y_0 = D / J(D), J(D) = max(||D||_2, ||D||_inf / lambda);  mu_0 = 1.25/||D||_2
+//   E  = Theta_{lambda/mu}(D - A + Y/mu);  A = T_{1/mu}(D - E + Y/mu)
+//   Z  = D - A - E;  Y += mu Z;  mu = min(rho mu, 1e7 mu_0);  stop ||Z||/||D|| < tol
+// and the rank prediction: sv = svp + 1 if svp < sv else svp + round(0.05 n).
+//
+// One fused pass over HBM per iteration (rpca_epilogue): with A kept
+// factored as U diag(theta) V^T it rebuilds each a_ij in registers (rank-c
+// tile product), forms Z, updates Y, shrinks the next E and writes the next
+// SVT input W.  Reads D, E, Y; writes E', Y, W.
+#include <math.h>
+
+#include <algorithm>
+
+#include "blws_core.cuh"
+#include "solver.cuh"
+
+namespace blws {
+
+namespace {
+
+constexpr int kEpBM = 64, kEpBN = 64, kEpBK = 16;
+
+__device__ inline double shrink(double x, double t) {
+  // Theta_t(x) = sgn(x) max(|x| - t, 0)  (Eq. 4)
+  const double ax = fabs(x) - t;
+  return ax > 0.0 ? copysign(ax, x) : 0.0;
+}
+
+enum EpMode { EP_ITER = 0, EP_FINAL = 1 };
+
+// Rank-c tile reconstruction a = U[i,:] diag(th) V[j,:]^T plus the host update.
+template <int MODE>
+__global__ void __launch_bounds__(256)
+rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
+              const double* __restrict__ th, const double* __restrict__ V, int ldv,
+              const int* __restrict__ count_ptr, const double* __restrict__ D,
+              const double* __restrict__ Ein, double* __restrict__ Eout, double* __restrict__ Y,
+              double* __restrict__ Wout, double* __restrict__ Aout, double mu, double mu_next,
+              double lam, double* __restrict__ part) {
+  __shared__ double Us[kEpBK][kEpBM + 1];
+  __shared__ double Vs[kEpBK][kEpBN + 1];
+  __shared__ double red[256];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.x * kEpBM, j0 = blockIdx.y * kEpBN;
+  const int c = *count_ptr;
+  double a[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) a[p][q] = 0.0;
+  for (int t0 = 0; t0 < c; t0 += kEpBK) {
+    for (int e = threadIdx.x; e < kEpBM * kEpBK; e += 256) {
+      const int i = e % kEpBM, t = e / kEpBM;
+      const int gi = i0 + i, gt = t0 + t;
+      Us[t][i] = (gi < m && gt < c) ? U[gi + (size_t)gt * ldu] * th[gt] : 0.0;
+    }
+    for (int e = threadIdx.x; e < kEpBN * kEpBK; e += 256) {
+      const int j = e % kEpBN, t = e / kEpBN;
+      const int gj = j0 + j, gt = t0 + t;
+      Vs[t][j] = (gj < n && gt < c) ? V[gj + (size_t)gt * ldv] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kEpBK; ++t) {
+      double u[4], v[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) u[p] = Us[t][tx + 16 * p];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v[q] = Vs[t][ty + 16 * q];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a[p][q] = fma(u[p], v[q], a[p][q]);
+    }
+    __syncthreads();
+  }
+  double z2 = 0.0;
+  const double inv_mu_next = 1.0 / mu_next;
+  const double thr = lam * inv_mu_next;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int gj = j0 + ty + 16 * q;
+    if (gj >= n) continue;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const int gi = i0 + tx + 16 * p;
+      if (gi >= m) continue;
+      const size_t o = gi + (size_t)gj * ld;
+      if (MODE == EP_FINAL) {
+        Aout[o] = a[p][q];
+      } else {
+        const double d = D[o];
+        const double z = d - a[p][q] - Ein[o];
+        const double y = fma(mu, z, Y[o]);
+        z2 = fma(z, z, z2);
+        const double e = shrink(fma(y, inv_mu_next, d - a[p][q]), thr);
+        Y[o] = y;
+        Eout[o] = e;
+        Wout[o] = fma(y, inv_mu_next, d - e);
+      }
+    }
+  }
+  if (MODE == EP_ITER) {
+    red[threadIdx.x] = z2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x + (size_t)blockIdx.y * gridDim.x] = red[0];
+  }
+}
+
+// First iteration (A = 0): Y = D / J, E = Theta_{lam/mu}(D + Y/mu), W = D - E + Y/mu.
+__global__ void rpca_start(int m, int n, int ld, const double* __restrict__ D, double invJ, double mu,
+                           double lam, double* E, double* Y, double* W) {
+  const size_t total = (size_t)m * n;
+  const double inv_mu = 1.0 / mu;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t o = (e % m) + (e / m) * (size_t)ld;
+    const double d = D[o];
+    const double y = d * invJ;
+    const double ev = shrink(fma(y, inv_mu, d), lam * inv_mu);
+    Y[o] = y;
+    E[o] = ev;
+    W[o] = fma(y, inv_mu, d - ev);
+  }
+}
+
+__global__ void maxabs_partial(int m, int n, int ld, const double* __restrict__ D, double* part,
+                               int* nonfinite) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  int bad = 0;
+  const size_t total = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const double v = D[(e % m) + (e / m) * (size_t)ld];
+    if (!isfinite(v)) bad = 1;
+    acc = fmax(acc, fabs(v));
+  }
+  if (bad) atomicOr(nonfinite, 1);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void reduce_max(int n, const double* __restrict__ part, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = fmax(acc, part[i]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void reduce_sum(int n, const double* __restrict__ part, double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void count_nonzero(int m, int n, int ld, const double* __restrict__ E,
+                              unsigned long long* out) {
+  __shared__ unsigned long long red[256];
+  unsigned long long c = 0;
+  const size_t total = (size_t)m * n;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x)
+    c += E[(e % m) + (e / m) * (size_t)ld] != 0.0 ? 1 : 0;
+  red[threadIdx.x] = c;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, red[0]);  // integer sum: order-independent
+}
+
+__global__ void thresholds(int r, const double* __restrict__ sigma, double eps, double* th) {
+  for (int t = threadIdx.x; t < r; t += blockDim.x) th[t] = fmax(sigma[t] - eps, 0.0);
+}
+
+}  // namespace
+
+blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* out_host) {
+  // block Lanczos from a seeded block, restarted from its own Ritz vectors
+  // (warm start) until the leading Ritz value stops moving
+  const int p = std::min(op.m, op.n), N = op.m + op.n;
+  const int r = std::min(8, p);
+  double *U, *V, *sig, *scal;
+  BLWS_TRY(ctx->get(BUF_WARM_U, (size_t)op.m * r, &U));
+  BLWS_TRY(ctx->get(BUF_WARM_V, (size_t)op.n * r, &V));
+  BLWS_TRY(ctx->get(BUF_SIG, (size_t)2 * r, &sig));
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  double prev = -1.0, cur = 0.0;
+  for (int pass = 0; pass < 40; ++pass) {
+    BlwsArgs a;
+    a.eps = 0.0;
+    a.r = r;
+    a.k = std::max(1, std::min(8, N / r));
+    a.draw = 0xC01Du;
+    if (pass == 0) {
+      a.cold = true;
+    } else {
+      a.U0 = U;
+      a.ldu0 = op.m;
+      a.V0 = V;
+      a.ldv0 = op.n;
+      a.w = r;
+    }
+    BLWS_TRY(blws_run(ctx, s, op, a, U, op.m, V, op.n, sig, reinterpret_cast<int*>(scal + SLOT_COUNT)));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, sig, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    cur = ctx->host_pinned[0];
+    if (fabs(cur - prev) <= 1e-14 * fabs(cur)) break;
+    prev = cur;
+  }
+  *out_host = cur;
+  return BLWS_OK;
+}
+
+blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, int ld,
+                     const rpca_params& p, double* A, double* E, rpca_info* info) {
+  const int N = m + n;
+  const int pmin = std::min(m, n);
+  const double lam = p.lambda > 0 ? p.lambda : 1.0 / sqrt((double)std::max(m, n));
+  double *Y, *W, *E2, *scal, *red;
+  BLWS_TRY(ctx->get(BUF_Y, (size_t)ld * n, &Y));
+  BLWS_TRY(ctx->get(BUF_W, (size_t)ld * n, &W));
+  BLWS_TRY(ctx->get(BUF_E2, (size_t)ld * n, &E2));
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  const int gb = ctx->sms * 4;
+  const dim3 egrid(ceil_div(m, kEpBM), ceil_div(n, kEpBN));
+  const int nparts = egrid.x * egrid.y;
+  // the reduction buffer is taken once, at its largest size, before any
+  // other request can grow it
+  BLWS_TRY(ctx->get(BUF_RED, (size_t)std::max(nparts, ctx->sms * 8) + 4096, &red));
+  double* zpart = red;
+  // norms of D: Frobenius, max-abs (and finiteness)
+  int* nonfinite = reinterpret_cast<int*>(scal + SLOT_FLAG);
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(nonfinite, 0, sizeof(int), s));
+  BLWS_TRY(sumsq(ctx, s, m, n, D, ld, scal + SLOT_NORM));
+  maxabs_partial<<<gb, 256, 0, s>>>(m, n, ld, D, red, nonfinite);
+  BLWS_CHECK_LAUNCH(ctx);
+  reduce_max<<<1, 256, 0, s>>>(gb, red, scal + SLOT_AUX);
+  BLWS_CHECK_LAUNCH(ctx);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  const double d_norm = sqrt(ctx->host_pinned[SLOT_NORM]);
+  const double d_inf = ctx->host_pinned[SLOT_AUX];
+  if (*reinterpret_cast<int*>(ctx->host_pinned + SLOT_FLAG))
+    return ctx->fail(BLWS_ENONFINITE, "rpca_solve: D has NaN/Inf entries");
+  info->iters = 0;
+  info->rank = 0;
+  info->nnzE = 0;
+  info->residual = 0.0;
+  info->status = BLWS_OK;
+  if (d_norm == 0.0) {  // D = 0: A = E = 0
+    BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(A, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
+    BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(E, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    return BLWS_OK;
+  }
+  Operator Dop;
+  Dop.m = m;
+  Dop.n = n;
+  Dop.W = D;
+  Dop.ldw = ld;
+  double norm_two = 0.0;
+  BLWS_TRY(spectral_norm(ctx, s, Dop, &norm_two));
+  info->norm_two = norm_two;
+  const double J = std::max(norm_two, d_inf / lam);
+  double mu = p.mu0 > 0 ? p.mu0 : 1.25 / norm_two;
+  const double mu_bar = mu * p.mu_bar_ratio;
+
+  // warm-start storage sized for the widest block this solve can use
+  const int k = ctx->cfg.k, k_cold = ctx->cfg.k_cold;
+  const int bcap = std::max(1, std::min(pmin, N / std::max(k, k_cold)));
+  double *Uw, *Vw, *sig;
+  BLWS_TRY(ctx->get(BUF_WARM_U, (size_t)m * bcap, &Uw));
+  BLWS_TRY(ctx->get(BUF_WARM_V, (size_t)n * bcap, &Vw));
+  BLWS_TRY(ctx->get(BUF_SIG, (size_t)2 * bcap, &sig));
+  double* th = sig + bcap;
+  int* count_dev = reinterpret_cast<int*>(scal + SLOT_COUNT);
+
+  const size_t total = (size_t)m * n;
+  const int eb = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sms * 8);
+  double* Ecur = E;
+  double* Enext = E2;
+  rpca_start<<<eb, 256, 0, s>>>(m, n, ld, D, 1.0 / J, mu, lam, Ecur, Y, W);
+  BLWS_CHECK_LAUNCH(ctx);
+
+  Operator Wop;
+  Wop.m = m;
+  Wop.n = n;
+  Wop.W = W;
+  Wop.ldw = ld;
+  int sv = std::min(std::max(p.sv0, 1), bcap);
+  int w = 0;
+  int svp = 0;
+  double res = 1.0;
+  int it = 0;
+  bool converged = false;
+  for (it = 1; it <= p.max_iter; ++it) {
+    if (it > 1) std::swap(Ecur, Enext);  // the E shrunk by the last epilogue
+    const double eps = 1.0 / mu;
+    BlwsArgs a;
+    a.eps = eps;
+    a.r = sv;
+    a.draw = (uint32_t)it;  // extra columns depend on the iteration only
+    if (w == 0) {
+      a.cold = true;
+      a.k = std::max(1, std::min(k_cold, N / sv));
+    } else {
+      a.U0 = Uw;
+      a.ldu0 = m;
+      a.V0 = Vw;
+      a.ldv0 = n;
+      a.w = w;
+      a.k = std::max(1, std::min(k, N / std::max(sv, w)));
+    }
+    BLWS_TRY(blws_run(ctx, s, Wop, a, Uw, m, Vw, n, sig, count_dev));
+    thresholds<<<1, 256, 0, s>>>(sv, sig, eps, th);
+    BLWS_CHECK_LAUNCH(ctx);
+    const double mu_next = std::min(mu * p.rho, mu_bar);
+    rpca_epilogue<EP_ITER><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D, Ecur,
+                                                 Enext, Y, W, nullptr, mu, mu_next, lam, zpart);
+    BLWS_CHECK_LAUNCH(ctx);
+    reduce_sum<<<1, 256, 0, s>>>(nparts, zpart, scal + SLOT_NORM);
+    BLWS_CHECK_LAUNCH(ctx);
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
+                                       cudaMemcpyDeviceToHost, s));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    svp = *reinterpret_cast<int*>(ctx->host_pinned + SLOT_COUNT);
+    const double z2 = ctx->host_pinned[SLOT_NORM];
+    if (!isfinite(z2)) return ctx->fail(BLWS_ENONFINITE, "rpca_solve: iterate became non-finite");
+    res = sqrt(z2) / d_norm;
+    w = sv;
+    // [Lin09] rank prediction for the next iteration
+    int nsv = svp < sv ? std::min(svp + 1, n) : std::min(svp + (int)lround(0.05 * n), n);
+    sv = std::max(1, std::min(nsv, bcap));
+    mu = mu_next;
+    if (res < p.tol) {
+      converged = true;
+      break;
+    }
+  }
+  if (!converged) it = p.max_iter;
+  // outputs: A = U diag(th) V^T of the last SVT; E = the E of that iteration
+  rpca_epilogue<EP_FINAL><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, nullptr,
+                                                nullptr, nullptr, nullptr, nullptr, A, 0.0, 1.0,
+                                                0.0, nullptr);
+  BLWS_CHECK_LAUNCH(ctx);
+  if (Ecur != E) {
+    BLWS_TRY_CUDA(ctx, cudaMemcpy2DAsync(E, sizeof(double) * ld, Ecur, sizeof(double) * ld,
+                                         sizeof(double) * m, n, cudaMemcpyDeviceToDevice, s));
+  }
+  unsigned long long* nz = reinterpret_cast<unsigned long long*>(scal + SLOT_NNZ);
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(nz, 0, sizeof(unsigned long long), s));
+  count_nonzero<<<eb, 256, 0, s>>>(m, n, ld, E, nz);
+  BLWS_CHECK_LAUNCH(ctx);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  info->iters = it;
+  info->rank = svp;
+  info->nnzE = (int64_t)*reinterpret_cast<unsigned long long*>(ctx->host_pinned + SLOT_NNZ);
+  info->residual = res;
+  info->status = converged ? BLWS_OK : BLWS_ENOCONV;
+  return converged ? BLWS_OK : BLWS_ENOCONV;
+}
+
+}  // namespace blws
