@@ -33,9 +33,12 @@ Readings where the paper is silent (each listed in the design notes):
     O((m + n) b^2), not a pass over W, and touches no older block.
   * ``full_reorth=True`` (cold start only, when there is no previous
     subspace) projects R_l against every previous block instead.
-  * qr(R_l) deflates: a column whose R-factor diagonal is below
-    ``DEFL_TOL * scale`` is set to zero in X_{l+1} and its row in B_l to zero.
-    ``scale`` is the largest column norm of W~ X_1.
+  * qr(R_l) deflates: Gram-Schmidt (twice per column) in column order; a
+    column whose remainder is below ``DEFL_TOL * scale`` is set to zero in
+    X_{l+1} and its row in B_l to zero.  ``scale`` is the largest column norm
+    of W~ X_1.  (Householder QR followed by zeroing dead columns is not the
+    same: it gives a dead column an arbitrary direction that leaks into the
+    later columns.)
   * Theta is applied to the Ritz values as max(lambda - eps, 0): singular
     values are nonnegative, so a Ritz value <= eps contributes nothing.
 """
@@ -65,11 +68,29 @@ def apply_augmented(W, X):
 
 
 def qr_deflate(R, scale):
-    """(X, B) = qr(R) by Householder QR (LAPACK), with deflation of dead columns."""
-    X, B = np.linalg.qr(R, mode="reduced")
-    dead = np.abs(np.diag(B)) <= DEFL_TOL * scale
-    X[:, dead] = 0.0
-    B[dead, :] = 0.0
+    """(X, B) = qr(R) with deflation, by Gram-Schmidt run twice per column.
+
+    Column j is orthogonalised (twice) against the earlier live columns; if
+    what remains has norm <= DEFL_TOL * scale the column is dead: its column
+    of X and its row of B are zero, and its coefficients on the earlier
+    columns stay in B, so R = X B up to the dropped remainders.
+    """
+    N, b = R.shape
+    X = np.zeros((N, b))
+    B = np.zeros((b, b))
+    live = []
+    for j in range(b):
+        v = np.array(R[:, j], dtype=np.float64)
+        for _ in range(2):
+            if live:
+                c = X[:, live].T @ v
+                v = v - X[:, live] @ c
+                B[live, j] += c
+        nrm = float(np.linalg.norm(v))
+        if nrm > DEFL_TOL * scale:
+            X[:, j] = v / nrm
+            B[j, j] = nrm
+            live.append(j)
     return X, B
 
 

@@ -160,3 +160,30 @@ def test_mixed_start_beats_one_sided_start():
     e_mixed = np.linalg.norm(mixed["A"] - A)
     e_one = np.linalg.norm(one_sided["A"] - A)
     assert e_mixed < e_one
+
+
+def test_qr_deflation_of_a_dependent_middle_column():
+    # Alg. 2 "qr" with deflation: a column in the span of earlier ones dies,
+    # keeps its coefficients in B, and leaks no direction into later columns.
+    rng = np.random.default_rng(70)
+    R = rng.standard_normal((30, 4))
+    R[:, 1] = 2.0 * R[:, 0]  # exactly dependent on column 0
+    X, B = oracle.qr_deflate(R, scale=np.linalg.norm(R, axis=0).max())
+    assert np.all(X[:, 1] == 0) and np.all(B[1, :] == 0)
+    live = [0, 2, 3]
+    np.testing.assert_allclose(X[:, live].T @ X[:, live], np.eye(3), atol=1e-14)
+    np.testing.assert_allclose(X @ B, R, atol=1e-12)
+    # later columns stay in span(R): no component outside it
+    P = R @ np.linalg.pinv(R)
+    np.testing.assert_allclose(P @ X, X, atol=1e-12)
+
+
+def test_blws_adm_stable_far_past_convergence():
+    # BLWS inside inexact ALM run to tol 1e-15 on a case where a deflated
+    # column occurs late: the count of values above eps stays at the rank.
+    from paper_1012_0365_gb300 import synthetic as s2
+    D, L0, _ = s2.rpca_problem(47, 61, 3, 0.05, seed=2)
+    rng = np.random.default_rng(3)
+    out = oracle.rpca_ialm_blws(D, lambda r, c: rng.standard_normal((r, c)), tol=1e-15, max_iter=45)
+    assert max(h[1] for h in out["history"][10:]) == 3
+    assert min(h[0] for h in out["history"]) < 1e-12
