@@ -167,6 +167,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=25)
     ap.add_argument("--ref-sample-iters", type=int, default=2)
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="run one warm-up and one timed-free solve only (for ncu launch lists)")
+    ap.add_argument("--profile-apply", action="store_true",
+                    help="run the block product with W~ a few times only (for ncu captures)")
     args = ap.parse_args()
     ws, rank = dist_env()
 
@@ -201,6 +205,20 @@ def main():
 
     def solve():
         return ctx.rpca_solve(Dg, tol=args.tol, A=A, E=E)
+
+    if args.profile_solve or args.profile_apply:
+        if args.profile_solve:
+            solve()
+            _, _, info = solve()
+            print(json.dumps({"profile": "solve", "iters": info["iters"], "launches": ctx.launches}))
+        else:
+            b = r + 1
+            X = blws.colmajor(torch.randn(m + n, b, dtype=torch.float64, device="cuda"))
+            for _ in range(3):
+                ctx.apply(Dg, X)
+            print(json.dumps({"profile": "apply", "b": b}))
+        torch.cuda.synchronize()
+        return
 
     for _ in range(args.warmup):
         _, _, info = solve()

@@ -140,6 +140,10 @@ typedef struct {
   double mu0;      /* <= 0: 1.25 / ||D||_2 */
   double mu_bar_ratio; /* mu cap = ratio * mu0, default 1e7 */
   int sv0;         /* initial predicted rank, default 10 */
+  double* trace;   /* optional HOST array of 3 * trace_len doubles: per outer
+                      iteration i < trace_len, (residual, count above eps,
+                      predicted rank used).  NULL (default): no trace. */
+  int trace_len;
 } rpca_params;
 
 typedef struct {

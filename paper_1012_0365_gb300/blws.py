@@ -16,8 +16,8 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -
 
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
-           "blws_last_error", "blws_launch_count", "blws_apply", "blws_svt", "rpca_params_default", "rpca_solve",
-           "mc_params_default", "mc_solve")
+           "blws_last_error", "blws_launch_count", "blws_apply",
+           "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -35,7 +35,8 @@ class BlwsOp(ctypes.Structure):
 class RpcaParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("rho", ctypes.c_double), ("mu0", ctypes.c_double), ("mu_bar_ratio", ctypes.c_double),
-                ("sv0", ctypes.c_int)]
+                ("sv0", ctypes.c_int), ("trace", ctypes.POINTER(ctypes.c_double)),
+                ("trace_len", ctypes.c_int)]
 
 
 class RpcaInfo(ctypes.Structure):
@@ -222,9 +223,10 @@ class Context:
 
     # ----------------------------------------------------------------- RPCA --
     def rpca_solve(self, D, lam=0.0, tol=1e-7, max_iter=1000, rho=1.5, sv0=10, mu0=0.0,
-                   mu_bar_ratio=1e7, A=None, E=None, stream=None, allow_noconv=False):
+                   mu_bar_ratio=1e7, A=None, E=None, stream=None, allow_noconv=False, trace=0):
         """Robust PCA by inexact ALM with BLWS.  D: column-major (m, n) FP64.
-        Returns (A, E, info dict)."""
+        Returns (A, E, info dict); with trace=T the dict also holds the first T
+        iterations' (residual, count above eps, predicted rank)."""
         m, n = D.shape
         _check_colmajor(D, m, n, "D")
         A = empty_colmajor(m, n) if A is None else A
@@ -232,13 +234,21 @@ class Context:
         p = RpcaParams()
         load().rpca_params_default(ctypes.byref(p))
         p.lambda_, p.tol, p.max_iter, p.rho, p.sv0, p.mu0, p.mu_bar_ratio = lam, tol, max_iter, rho, sv0, mu0, mu_bar_ratio
+        tr = None
+        if trace:
+            tr = (ctypes.c_double * (3 * trace))()
+            p.trace, p.trace_len = ctypes.cast(tr, ctypes.POINTER(ctypes.c_double)), trace
         info = RpcaInfo()
         st = load().rpca_solve(self._h, _ptr(D), m, n, m, ctypes.byref(p), _ptr(A), _ptr(E),
                                ctypes.byref(info), _stream(stream))
         if st != OK and not (st == ENOCONV and allow_noconv):
             self._raise(st, "rpca_solve")
-        return A, E, {"iters": info.iters, "rank": info.rank, "nnzE": info.nnzE,
-                      "residual": info.residual, "norm_two": info.norm_two, "status": info.status}
+        out = {"iters": info.iters, "rank": info.rank, "nnzE": info.nnzE,
+               "residual": info.residual, "norm_two": info.norm_two, "status": info.status}
+        if tr is not None:
+            k = min(trace, info.iters)
+            out["trace"] = [(tr[3 * i], int(tr[3 * i + 1]), int(tr[3 * i + 2])) for i in range(k)]
+        return A, E, out
 
     # ------------------------------------------------------------------- MC --
     def mc_solve(self, m, n, rowptr, colidx, vals, max_rank, variant=0, tau=0.0, delta=0.0,

@@ -169,7 +169,7 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
                                                                        l * b);
     BLWS_CHECK_LAUNCH(ctx);
   }
-  BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z));
+  BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z, a.eps));
   const double r2 = 1.41421356237309504880;
   BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu));
   BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv));

@@ -228,6 +228,8 @@ blws_status rpca_params_default(rpca_params* p) {
   p->mu0 = 0.0;
   p->mu_bar_ratio = 1e7;
   p->sv0 = 10;
+  p->trace = nullptr;
+  p->trace_len = 0;
   return BLWS_OK;
 }
 

@@ -105,13 +105,16 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
   // scales again (dinv was reused for the diagonal of L)
   for (int j = tid; j < b; j += nt) dinv[j] = 1.0 / d[j];
   __syncthreads();
-  // S(k, j) = Li(j, k) / d_k  (upper);  B(k, j) = L(j, k) d_j (upper)
+  // S(k, j) = Li(j, k) / d_k  (upper);  B(k, j) = L(j, k) d_j (upper).
+  // A dead column has no X column and no row of B, but keeps its
+  // coefficients on the earlier live columns (its column of B above the
+  // diagonal), as Gram-Schmidt with deflation does: R(:, j) = X B(:, j).
   for (int e = tid; e < b * b; e += nt) {
     const int k = e % b, j = e / b;
     double sv = 0.0, bv = 0.0;
-    if (k <= j && !dead[j] && !dead[k]) {
-      sv = Li[j + (size_t)k * b] * dinv[k];
-      bv = L[j + (size_t)k * b] * d[j];
+    if (k <= j && !dead[k]) {
+      if (!dead[j]) sv = Li[j + (size_t)k * b] * dinv[k];
+      if (!dead[j] || k < j) bv = L[j + (size_t)k * b] * d[j];
     }
     S[e] = sv;
     Bout[e] = bv;

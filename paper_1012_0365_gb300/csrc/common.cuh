@@ -47,6 +47,7 @@ enum Buf {
   BUF_SMALL,     // b x b scratch matrices and vectors
   BUF_SPLITK,    // split-K partial sums of the GEMMs
   BUF_EIG,       // eigen-solver scratch
+  BUF_EIG2,      // eigen-solver second level (clusters)
   BUF_SCAL,      // device scalars (Slot)
   BUF_WARM_U,    // solver-held warm start U (m x b)
   BUF_WARM_V,    // solver-held warm start V (n x b)

@@ -15,13 +15,17 @@
 //        R = I - X^T X,  S = X^T T X,  lam_i = s_ii / (1 - r_ii),
 //        E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i)  if |lam_i - lam_j| > d,
 //               r_ij / 2 otherwise,   X <- X + X E,
-//      with d = 2 (||S - diag(lam)|| + ||T|| ||R||) (Frobenius bounds here).
-//      Each step squares the error of well-separated pairs; pairs closer than
-//      d stay as an (orthonormalised) basis of their joint eigenspace.
-// Then the pairs are sorted by decreasing eigenvalue.
+//      with d = 2 (||S - diag(lam)|| + ||T|| ||R||) (Frobenius bounds here),
+//      widened by a safety factor.  Each step squares the error of
+//      well-separated pairs; closer pairs stay as an (orthonormalised) basis
+//      of their joint eigenspace;
+//   3. each cluster that can change the count above eps or a threshold is
+//      solved again on its own (shifted and rescaled to O(1)) by stages 1-2.
+// Pairs are sorted by decreasing eigenvalue.
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "ops.cuh"
 
@@ -32,13 +36,22 @@ namespace blws {
 namespace {
 
 constexpr int kJacobiMaxSweeps = 20;
-// FP32 stage: stop when off(A)^2 <= tol2 ||A||_F^2, or once a sweep no longer
-// halves off(A)^2 (the FP32 rounding floor); the FP64 refinement does the rest.
+// FP32 stage: stop when off(A)^2 <= tol2 ||A||_F^2, or when off(A) is near the
+// FP32 rounding floor (<= 1e-6 ||A||_F) and a sweep no longer halves off(A)^2;
+// the FP64 refinement does the rest.
 constexpr float kJacobiTol2 = 1e-11f;
+constexpr float kJacobiFloor2 = 1e-12f;
 constexpr int kRefineSteps = 3;
+// The first-order refinement is only applied to pairs whose gap exceeds
+// kClusterGamma times the Ogita-Aishima width d: closer pairs may start with
+// O(1) mixing after the FP32 stage, outside the refinement's convergence
+// region, so they are kept as a joint subspace and resolved by the cluster
+// level (sym_eig).
+constexpr double kClusterGamma = 64.0;
 
 __device__ inline bool jacobi_done(int sweep, float off, float tot, float prev_off) {
-  return off <= kJacobiTol2 * tot || (sweep >= 2 && off > 0.5f * prev_off);
+  (void)sweep;
+  return off <= kJacobiTol2 * tot || (off <= kJacobiFloor2 * tot && off > 0.5f * prev_off);
 }
 constexpr int kCtaMaxN = 160;       // A and V (FP32) in shared memory up to this size
 
@@ -344,7 +357,7 @@ __global__ void oa_lambda(int n, int nparts, const double* __restrict__ S, const
       r2 += part[3 * c + 1];
       t2 += part[3 * c + 2];
     }
-    *delta = 2.0 * (sqrt(s_off) + sqrt(t2) * sqrt(r2));
+    *delta = kClusterGamma * 2.0 * (sqrt(s_off) + sqrt(t2) * sqrt(r2));
   }
 }
 
@@ -391,7 +404,10 @@ __global__ void sort_desc(int n, const double* __restrict__ lam_in, const double
 
 }  // namespace
 
-blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z) {
+// One level: FP32 Jacobi, FP64 refinement, sort.  *delta_dev receives the
+// refinement's cluster width d (pairs closer than d are not resolved).
+blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                          double* delta_out) {
   if (n <= 0) return BLWS_OK;
   const int N = n + (n & 1);
   // scratch: FP32 A0, A1, V (N^2 each) ; FP64 X, X2, R, S, TX, E (n^2 each); small vectors
@@ -458,6 +474,76 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   }
   sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, lam, Z);
   BLWS_CHECK_LAUNCH(ctx);
+  if (delta_out)
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(delta_out, delta, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return BLWS_OK;
+}
+
+namespace {
+
+// K = (S - mu I) / scale for the cluster block S (c x c)
+__global__ void shift_scale(int c, const double* __restrict__ S, double mu, double inv_scale, double* K) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
+    const int i = e % c, j = e / c;
+    K[e] = (S[e] - (i == j ? mu : 0.0)) * inv_scale;
+  }
+}
+
+__global__ void unshift(int c, const double* __restrict__ nu, double mu, double scale, double* lam) {
+  for (int i = threadIdx.x; i < c; i += blockDim.x) lam[i] = fma(scale, nu[i], mu);
+}
+
+}  // namespace
+
+blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                    double eps) {
+  if (n <= 0) return BLWS_OK;
+  double* scal;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2));
+  // Second level for clusters: eigenvalues closer than the refinement width d
+  // are only resolved as a joint subspace, with values accurate to ~d (the
+  // FP32 stage's absolute accuracy, ~1e-7 ||T||).  Where that could change
+  // the count above eps or a threshold sigma - eps, the cluster is solved
+  // again on its own: K = (X_C^T T X_C - mu I) / scale has O(1) entries, so
+  // the same two-stage solver resolves it to ~1e-7 of the cluster's width.
+  double* h = ctx->host_pinned;
+  std::vector<double> hl(n);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 32, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  const double d = h[32];
+  if (!(d > 0.0)) return BLWS_OK;
+  int i = 0;
+  while (i < n) {
+    int j = i + 1;
+    while (j < n && hl[j - 1] - hl[j] <= d) ++j;
+    const int c = j - i;
+    if (c >= 2 && hl[i] > eps - 3.0 * d) {
+      const double mu = 0.5 * (hl[i] + hl[j - 1]);
+      const double scale = 0.5 * (hl[i] - hl[j - 1]) + d;
+      double* w;
+      BLWS_TRY(ctx->get(BUF_EIG2, (size_t)n * c * 2 + (size_t)c * c * 3 + c, &w));
+      double* TX = w;                       // n x c
+      double* Zc = TX + (size_t)n * c;      // n x c
+      double* K = Zc + (size_t)n * c;       // c x c
+      double* ZK = K + (size_t)c * c;       // c x c
+      double* S = ZK + (size_t)c * c;       // c x c
+      double* nu = S + (size_t)c * c;       // c
+      const double* Xc = Z + (size_t)i * n;
+      BLWS_TRY(gemm(ctx, s, false, false, n, c, n, 1.0, T, n, Xc, n, 0.0, TX, n));
+      BLWS_TRY(gemm(ctx, s, true, false, c, c, n, 1.0, Xc, n, TX, n, 0.0, S, c));
+      shift_scale<<<ceil_div((long long)c * c, 256), 256, 0, s>>>(c, S, mu, 1.0 / scale, K);
+      BLWS_CHECK_LAUNCH(ctx);
+      BLWS_TRY(sym_eig_level(ctx, s, c, K, nu, ZK, nullptr));
+      unshift<<<1, 256, 0, s>>>(c, nu, mu, scale, lam + i);
+      BLWS_CHECK_LAUNCH(ctx);
+      BLWS_TRY(gemm(ctx, s, false, false, n, c, c, 1.0, Xc, n, ZK, c, 0.0, Zc, n));
+      BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(Z + (size_t)i * n, Zc, sizeof(double) * n * c,
+                                         cudaMemcpyDeviceToDevice, s));
+    }
+    i = j;
+  }
   return BLWS_OK;
 }
 

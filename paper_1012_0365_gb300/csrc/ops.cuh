@@ -21,7 +21,10 @@ blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, i
 
 // Symmetric eigen-decomposition of the n x n FP64 matrix T (ld n):
 // lam (n, decreasing) and Z (n x n, ld n, columns in the same order).
-blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z);
+// Eigenvalue clusters that reach above eps - 3 d (d the first level's
+// resolution) are re-solved on their own (see eig.cu).  Synchronises s once.
+blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                    double eps);
 
 // CholeskyQR2 with column equilibration and deflation: on return X (N x b,
 // ld) holds an orthonormal basis of span(R) with dead columns zeroed and

@@ -356,6 +356,11 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     const double z2 = ctx->host_pinned[SLOT_NORM];
     if (!isfinite(z2)) return ctx->fail(BLWS_ENONFINITE, "rpca_solve: iterate became non-finite");
     res = sqrt(z2) / d_norm;
+    if (p.trace && it <= p.trace_len) {
+      p.trace[3 * (it - 1) + 0] = res;
+      p.trace[3 * (it - 1) + 1] = svp;
+      p.trace[3 * (it - 1) + 2] = sv;
+    }
     w = sv;
     // [Lin09] rank prediction for the next iteration
     int nsv = svp < sv ? std::min(svp + 1, n) : std::min(svp + (int)lround(0.05 * n), n);

@@ -69,8 +69,8 @@ def test_struct_layout_matches_the_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(blws_config), sizeof(blws_op), sizeof(rpca_params),
          sizeof(rpca_info), sizeof(mc_params), sizeof(mc_info));
-  printf("%zu %zu %zu %zu\\n", offsetof(blws_op, val), offsetof(blws_op, Vl),
-         offsetof(rpca_info, nnzE), offsetof(mc_params, xtol));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(blws_op, val), offsetof(blws_op, Vl),
+         offsetof(rpca_info, nnzE), offsetof(mc_params, xtol), offsetof(rpca_params, trace_len));
   return 0;
 }
 """)
@@ -81,4 +81,4 @@ int main(void) {
     assert sizes == [ctypes.sizeof(t) for t in (blws.BlwsConfig, blws.BlwsOp, blws.RpcaParams,
                                                  blws.RpcaInfo, blws.McParams, blws.McInfo)]
     assert offs == [blws.BlwsOp.val.offset, blws.BlwsOp.Vl.offset, blws.RpcaInfo.nnzE.offset,
-                    blws.McParams.xtol.offset]
+                    blws.McParams.xtol.offset, blws.RpcaParams.trace_len.offset]

@@ -62,7 +62,7 @@ def test_svt_matches_oracle(ctx, torch_mod, m, n, r, sdr, seed):
     assert np.linalg.norm(X - Xr) / np.linalg.norm(Xr) < 1e-6
     # a value sitting at tau (theta ~ 0) may be counted on one side only
     assert abs(info["rank"] - ref["rank"]) <= 1
-    assert abs(info["iters"] - ref["iters"]) <= 3
+    assert abs(info["iters"] - ref["iters"]) <= max(3, ref["iters"] // 20)
 
 
 def test_svt_default_tol_pattern(ctx, torch_mod):
