@@ -130,6 +130,42 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r,
 blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx, int b,
                        double* P, int ldp, void* stream);
 
+/* blws_apply for a dense W, without allocating anything.  (The paper has no
+ * counterpart: this is a deployment variant of step a2.)
+ *
+ * For callers that cannot call cudaMalloc: code running inside another
+ * framework's memory pool or a plugin host that forbids its own device
+ * allocations, code that must not trigger the implicit device
+ * synchronisation an allocation or free can cause, or code that may not
+ * create a blws_ctx (creating one allocates its workspace).
+ *
+ * Computes P[0:m] = W X[m:m+n] and P[m:m+n] = W^T X[0:m] exactly as
+ * blws_apply does for a dense operator (same kernels, same split of the
+ * inner dimension).  W is m x n (ld ldw >= m), X and P are (m+n) x b (ld ldx,
+ * ldp >= m+n), all device FP64 owned by the caller.  No context is needed.
+ *
+ * Scratch: the split-K partial sums live in one 16 MiB array
+ * (2,097,152 doubles) that the library declares statically; every GPU that
+ * loads the library holds it until the process exits.  A product of r rows
+ * needs s * r * b doubles of it, where s is the split-K factor the library
+ * picks to fill the GPU (s = 1, i.e. no scratch, once the product has at
+ * least two tiles per SM).  If either product would need more than the
+ * array holds, the call returns BLWS_EINVAL before launching anything.
+ * Every element the call reads from the array was written by the same call,
+ * so nothing needs clearing between calls.
+ *
+ * The first call on a device (that device current) looks up the array's
+ * device address and the SM count; make that first call before any stream
+ * capture.  All calls share the one array: calls that can overlap on the
+ * GPU (different streams, or different host threads) race on it and must
+ * be serialised by the caller.
+ *
+ * Returns BLWS_OK, BLWS_EINVAL (bad pointer or size, or scratch need above
+ * the maximum), BLWS_ECUDA (a launch or the set-up failed) or BLWS_ENOTSUP
+ * (device ordinal >= 64).  Does not synchronise. */
+blws_status blws_apply_noalloc(const double* W, int m, int n, int ldw, const double* X, int ldx,
+                               int b, double* P, int ldp, void* stream);
+
 /* Robust PCA (Section 5, Table 1): min ||A||_* + lambda ||E||_1 s.t. D = A+E
  * by inexact ALM with every SVT evaluated by BLWS. */
 typedef struct {

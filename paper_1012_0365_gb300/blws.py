@@ -16,7 +16,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -
 
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
-           "blws_last_error", "blws_launch_count", "blws_apply",
+           "blws_last_error", "blws_launch_count", "blws_apply", "blws_apply_noalloc",
            "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve")
 
 
@@ -79,6 +79,7 @@ def load():
     lib.blws_svt.argtypes = [vp, ctypes.POINTER(BlwsOp), cd, ci, vp, vp, ci, vp, ci, vp, vp, vp,
                              ctypes.POINTER(ci), vp]
     lib.blws_apply.argtypes = [vp, ctypes.POINTER(BlwsOp), vp, ci, ci, vp, ci, vp]
+    lib.blws_apply_noalloc.argtypes = [vp, ci, ci, ci, vp, ci, ci, vp, ci, vp]
     lib.rpca_params_default.argtypes = [ctypes.POINTER(RpcaParams)]
     lib.rpca_solve.argtypes = [vp, vp, ci, ci, ci, ctypes.POINTER(RpcaParams), vp, vp,
                                ctypes.POINTER(RpcaInfo), vp]
@@ -133,6 +134,19 @@ def _stream(stream):
     torch = _torch()
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def apply_noalloc(W, X, P, stream=None):
+    """P = [W X_v; W^T X_u] through blws_apply_noalloc (no context, no
+    allocation; P must be a preallocated column-major (m+n, b) tensor).
+    Returns the status code."""
+    m, n = W.shape
+    b = X.shape[1]
+    _check_colmajor(W, m, n, "W")
+    _check_colmajor(X, m + n, b, "X")
+    _check_colmajor(P, m + n, b, "P")
+    return load().blws_apply_noalloc(_ptr(W), m, n, m, _ptr(X), m + n, b, _ptr(P), m + n,
+                                     _stream(stream))
 
 
 class Context:

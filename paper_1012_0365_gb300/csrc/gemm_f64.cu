@@ -7,6 +7,7 @@
 // split and the partial sums are reduced in a fixed order (deterministic, no
 // atomics).
 #include <algorithm>
+#include <mutex>
 
 #include "ops.cuh"
 
@@ -246,3 +247,128 @@ blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, i
 }
 
 }  // namespace blws
+
+// ------------------------------------------------ allocation-free product --
+// blws_apply_noalloc: the product with the augmented matrix for callers that
+// cannot allocate device memory.  Its only scratch (the split-K partial sums
+// of the two GEMMs) lives in this file-scope array, which every GPU that
+// loads the library holds until the process exits.
+namespace blws {
+namespace {
+
+constexpr size_t kNoAllocScratchDoubles = (size_t)2 << 20;  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+int g_noalloc_sms[kNoAllocMaxDevices] = {0};
+
+// device address of the scratch array and the SM count, looked up once per
+// device with that device current
+blws_status noalloc_setup(int dev, double** addr, int* sms) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return BLWS_ENOTSUP;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return BLWS_ECUDA;
+    }
+    int count = 0;
+    if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return BLWS_ECUDA;
+    }
+    g_noalloc_sms[dev] = count;
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *addr = g_noalloc_addr[dev];
+  *sms = g_noalloc_sms[dev];
+  return BLWS_OK;
+}
+
+// the split-K factor the allocating path picks for this GEMM (same rule)
+template <int BM, int BN>
+int noalloc_splits(int sms, int M, int N, int K, int* kchunk) {
+  const int tiles = ceil_div(M, BM) * ceil_div(N, BN);
+  const int target = 2 * sms;
+  int splits = 1;
+  if (tiles < target && K > 4 * kBK) {
+    splits = ceil_div(target, tiles);
+    splits = min(splits, ceil_div(K, 4 * kBK));
+    splits = max(splits, 1);
+  }
+  *kchunk = ceil_div(ceil_div(K, splits), kBK) * kBK;
+  return ceil_div(K, *kchunk);
+}
+
+template <bool TA, int BM, int BN>
+size_t noalloc_need(int sms, int M, int N, int K) {
+  int kchunk;
+  const int splits = noalloc_splits<BM, BN>(sms, M, N, K, &kchunk);
+  return splits > 1 ? (size_t)splits * M * N : 0;
+}
+
+template <bool TA, int BM, int BN>
+cudaError_t noalloc_gemm(cudaStream_t s, int sms, double* scratch, int M, int N, int K,
+                         const double* A, int lda, const double* B, int ldb, double* C, int ldc) {
+  int kchunk;
+  const int splits = noalloc_splits<BM, BN>(sms, M, N, K, &kchunk);
+  double* part = splits > 1 ? scratch : nullptr;
+  dim3 grid(ceil_div(M, BM), ceil_div(N, BN), splits);
+  gemm_f64_kernel<TA, false, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, 1.0, A, lda, B, ldb,
+                                                               0.0, C, ldc, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  const size_t total = (size_t)M * N;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
+  splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, 1.0, part, 0.0, C, ldc);
+  return cudaGetLastError();
+}
+
+template <bool TA>
+size_t noalloc_need_any(int sms, int M, int N, int K) {
+  if (N <= 16) return noalloc_need<TA, 128, 16>(sms, M, N, K);
+  if (N <= 32) return noalloc_need<TA, 64, 32>(sms, M, N, K);
+  return noalloc_need<TA, 64, 64>(sms, M, N, K);
+}
+
+template <bool TA>
+cudaError_t noalloc_gemm_any(cudaStream_t s, int sms, double* scratch, int M, int N, int K,
+                             const double* A, int lda, const double* B, int ldb, double* C,
+                             int ldc) {
+  if (N <= 16) return noalloc_gemm<TA, 128, 16>(s, sms, scratch, M, N, K, A, lda, B, ldb, C, ldc);
+  if (N <= 32) return noalloc_gemm<TA, 64, 32>(s, sms, scratch, M, N, K, A, lda, B, ldb, C, ldc);
+  return noalloc_gemm<TA, 64, 64>(s, sms, scratch, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+}  // namespace
+
+}  // namespace blws
+
+extern "C" blws_status blws_apply_noalloc(const double* W, int m, int n, int ldw, const double* X,
+                                          int ldx, int b, double* P, int ldp, void* stream) {
+  using namespace blws;
+  if (!W || !X || !P) return BLWS_EINVAL;
+  if (m < 1 || n < 1 || b < 1 || ldw < m || ldx < m + n || ldp < m + n) return BLWS_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return BLWS_ECUDA;
+  }
+  double* scratch = nullptr;
+  int sms = 0;
+  blws_status st = noalloc_setup(dev, &scratch, &sms);
+  if (st != BLWS_OK) return st;
+  // P_u = W X_v (m x b, inner n) and P_v = W^T X_u (n x b, inner m); they run
+  // one after the other on the stream, so each may use the whole array
+  if (noalloc_need_any<false>(sms, m, b, n) > kNoAllocScratchDoubles ||
+      noalloc_need_any<true>(sms, n, b, m) > kNoAllocScratchDoubles)
+    return BLWS_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (noalloc_gemm_any<false>(s, sms, scratch, m, b, n, W, ldw, X + m, ldx, P, ldp) != cudaSuccess ||
+      noalloc_gemm_any<true>(s, sms, scratch, n, b, m, W, ldw, X, ldx, P + m, ldp) != cudaSuccess)
+    return BLWS_ECUDA;
+  return BLWS_OK;
+}
