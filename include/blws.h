@@ -139,9 +139,9 @@ blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx
  * synchronisation an allocation or free can cause, or code that may not
  * create a blws_ctx (creating one allocates its workspace).
  *
- * Computes P[0:m] = W X[m:m+n] and P[m:m+n] = W^T X[0:m] exactly as
- * blws_apply does for a dense operator (same kernels, same split of the
- * inner dimension).  W is m x n (ld ldw >= m), X and P are (m+n) x b (ld ldx,
+ * Computes P[0:m] = W X[m:m+n] and P[m:m+n] = W^T X[0:m] with the same
+ * kernels as blws_apply for a dense operator; it splits the inner dimension
+ * less finely (for about two CTAs per SM), so the two agree to rounding.  W is m x n (ld ldw >= m), X and P are (m+n) x b (ld ldx,
  * ldp >= m+n), all device FP64 owned by the caller.  No context is needed.
  *
  * Scratch: the split-K partial sums live in one 16 MiB array

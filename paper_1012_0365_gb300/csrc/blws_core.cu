@@ -102,9 +102,11 @@ blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax) {
   BLWS_TRY(ctx->get(BUF_P2, N * bmax * sizeof(double), &p));
   BLWS_TRY(ctx->get(BUF_T, (3 * kb * kb + 2 * kb + (size_t)bmax * bmax * 2 + 64) * sizeof(double), &p));
   BLWS_TRY(ctx->get(BUF_SMALL, 6 * (size_t)bmax * bmax * sizeof(double), &p));
-  // split-K partials: at most 2 * target * BM * BN doubles (see gemm_f64.cu)
-  BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)4 * ctx->sms * 64 * 64 * sizeof(double) + (size_t)6 * kb * kb * sizeof(double), &p));
-  const size_t Ne = kb + (kb & 1);
+  // split-K partials: at most 2 * target * BM * BN doubles, target = 8 SMs-worth
+  // of CTAs (see gemm_f64.cu)
+  BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)16 * ctx->sms * 64 * 64 * sizeof(double), &p));
+  // eigen-solver padding: even (one CTA) or a multiple of 32 (block-pair Jacobi)
+  const size_t Ne = std::max(kb + (kb & 1), (kb + 31) / 32 * 32);
   BLWS_TRY(ctx->get(BUF_EIG, 3 * Ne * Ne * sizeof(float) + 6 * kb * kb * sizeof(double) +
                                  (4 * kb + 3 * 1024 + 64) * sizeof(double), &p));
   BLWS_TRY(ctx->get(BUF_RED, (size_t)ctx->sms * 8 * sizeof(double), &p));

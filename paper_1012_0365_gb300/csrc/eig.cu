@@ -35,12 +35,13 @@ namespace blws {
 
 namespace {
 
-constexpr int kJacobiMaxSweeps = 20;
+constexpr int kJacobiMaxSweeps = 16;
 // FP32 stage: stop when off(A)^2 <= tol2 ||A||_F^2, or when off(A) is near the
-// FP32 rounding floor (<= 1e-6 ||A||_F) and a sweep no longer halves off(A)^2;
+// FP32 rounding floor (<= 3e-5 ||A||_F) and a sweep no longer cuts off(A)^2 by
+// more than 3x;
 // the FP64 refinement does the rest.
 constexpr float kJacobiTol2 = 1e-11f;
-constexpr float kJacobiFloor2 = 1e-12f;
+constexpr float kJacobiFloor2 = 1e-9f;
 constexpr int kRefineSteps = 3;
 // The first-order refinement is only applied to pairs whose gap exceeds
 // kClusterGamma times the Ogita-Aishima width d: closer pairs may start with
@@ -51,7 +52,7 @@ constexpr double kClusterGamma = 64.0;
 
 __device__ inline bool jacobi_done(int sweep, float off, float tot, float prev_off) {
   (void)sweep;
-  return off <= kJacobiTol2 * tot || (off <= kJacobiFloor2 * tot && off > 0.5f * prev_off);
+  return off <= kJacobiTol2 * tot || (off <= kJacobiFloor2 * tot && off > 0.3f * prev_off);
 }
 constexpr int kCtaMaxN = 160;       // A and V (FP32) in shared memory up to this size
 
@@ -283,6 +284,207 @@ jacobi_grid_kernel(int n, int N, const double* __restrict__ T, float* A0, float*
   if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
 }
 
+// --------------------------------- block-pair Jacobi (cooperative grid) --
+// Blocks of kBS indices; each round pairs the nb blocks round-robin.  Phase 1:
+// one CTA per block pair runs ONE cyclic Jacobi sweep on its (2 kBS)^2
+// diagonal sub-block in shared memory and records the accumulated orthogonal
+// Q (2 kBS x 2 kBS).  Phase 2: every off-diagonal block pair (a, b) becomes
+// Q_a^T A_ab Q_b, and every row chunk of V becomes V Q_a.  One grid barrier
+// per phase: 2 (nb - 1) barriers per sweep instead of one per scalar round.
+constexpr int kBS = 16;
+constexpr int kB2 = 2 * kBS;  // 32
+
+__device__ inline int blk_of_pair(int nb, int r, int k, int which) {
+  int p, q;
+  rr_pair(nb, r, k, p, q);
+  return which ? q : p;
+}
+
+// global index of local row i (0..kB2) of pair (bp, bq)
+__device__ inline int pair_index(int bp, int bq, int i) {
+  return i < kBS ? bp * kBS + i : bq * kBS + (i - kBS);
+}
+
+__global__ void __launch_bounds__(256)
+jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float* V, float* Qbuf,
+                    float2* part, int* sweeps_out) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ float S1[kB2][kB2 + 1];
+  __shared__ float S2[kB2][kB2 + 1];
+  __shared__ float S3[kB2][kB2 + 1];
+  __shared__ float S4[kB2][kB2 + 1];
+  __shared__ Rot rot[kB2 / 2];
+  __shared__ float red_off[8], red_tot[8];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nb = N / kBS, P = nb / 2;
+  const size_t gtid = (size_t)blockIdx.x * nt + tid, gnt = (size_t)gridDim.x * nt;
+  for (size_t e = gtid; e < (size_t)N * N; e += gnt) {
+    const int i = (int)(e % N), j = (int)(e / N);
+    A[e] = (i < n && j < n) ? (float)T[i + (size_t)j * n] : 0.0f;
+    V[e] = (i == j) ? 1.0f : 0.0f;
+  }
+  grid.sync();
+  int sweep = 0;
+  float prev_off = 3.0e38f;
+  for (; sweep < kJacobiMaxSweeps; ++sweep) {
+    float off = 0.0f, tot = 0.0f;
+    for (int r = 0; r < nb - 1; ++r) {
+      const bool last = (r == nb - 2);
+      // ---- phase 1: one inner sweep per diagonal block pair
+      for (int k = blockIdx.x; k < P; k += gridDim.x) {
+        const int bp = blk_of_pair(nb, r, k, 0), bq = blk_of_pair(nb, r, k, 1);
+        for (int e = tid; e < kB2 * kB2; e += nt) {
+          const int i = e % kB2, j = e / kB2;
+          S1[i][j] = A[pair_index(bp, bq, i) + (size_t)pair_index(bp, bq, j) * N];
+          S2[i][j] = (i == j) ? 1.0f : 0.0f;
+        }
+        __syncthreads();
+        for (int ir = 0; ir < kB2 - 1; ++ir) {
+          if (tid < kB2 / 2) {
+            Rot R;
+            rr_pair(kB2, ir, tid, R.p, R.q);
+            jacobi_rot(S1[R.p][R.p], S1[R.q][R.q], S1[R.p][R.q], R.c, R.s);
+            rot[tid] = R;
+          }
+          __syncthreads();
+          for (int e = tid; e < (kB2 / 2) * (kB2 / 2); e += nt) {
+            const int i = e % (kB2 / 2), j = e / (kB2 / 2);
+            const Rot ri = rot[i], rj = rot[j];
+            const float a = S1[ri.p][rj.p], b = S1[ri.p][rj.q], c = S1[ri.q][rj.p], d = S1[ri.q][rj.q];
+            const float m_ap = rj.c * a - rj.s * b, m_aq = rj.s * a + rj.c * b;
+            const float m_cp = rj.c * c - rj.s * d, m_cq = rj.s * c + rj.c * d;
+            float n_pq = ri.c * m_aq - ri.s * m_cq, n_qp = ri.s * m_ap + ri.c * m_cp;
+            if (i == j) { n_pq = 0.0f; n_qp = 0.0f; }
+            S1[ri.p][rj.p] = ri.c * m_ap - ri.s * m_cp;
+            S1[ri.p][rj.q] = n_pq;
+            S1[ri.q][rj.p] = n_qp;
+            S1[ri.q][rj.q] = ri.s * m_aq + ri.c * m_cq;
+          }
+          for (int e = tid; e < kB2 * (kB2 / 2); e += nt) {
+            const int x = e % kB2, j = e / kB2;
+            const Rot R = rot[j];
+            const float vp = S2[x][R.p], vq = S2[x][R.q];
+            S2[x][R.p] = R.c * vp - R.s * vq;
+            S2[x][R.q] = R.s * vp + R.c * vq;
+          }
+          __syncthreads();
+        }
+        float lo = 0.0f, lt = 0.0f;
+        for (int e = tid; e < kB2 * kB2; e += nt) {
+          const int i = e % kB2, j = e / kB2;
+          const float v = S1[i][j];
+          A[pair_index(bp, bq, i) + (size_t)pair_index(bp, bq, j) * N] = v;
+          Qbuf[(size_t)k * kB2 * kB2 + e] = S2[i][j];
+          if (last) {
+            lt += v * v;
+            if (i != j) lo += v * v;
+          }
+        }
+        off += lo;
+        tot += lt;
+        __syncthreads();
+      }
+      grid.sync();
+      // ---- phase 2: off-diagonal block pairs (a < b) and row chunks of V
+      const int npairs = P * (P - 1) / 2;
+      const int nv = (N / kB2) * P;
+      for (int item = blockIdx.x; item < npairs + nv; item += gridDim.x) {
+        if (item < npairs) {
+          // unrank item -> (a, b), a < b
+          int a = 0, rem = item;
+          while (rem >= P - 1 - a) { rem -= P - 1 - a; ++a; }
+          const int b = a + 1 + rem;
+          const int ap = blk_of_pair(nb, r, a, 0), aq = blk_of_pair(nb, r, a, 1);
+          const int bp = blk_of_pair(nb, r, b, 0), bq = blk_of_pair(nb, r, b, 1);
+          for (int e = tid; e < kB2 * kB2; e += nt) {
+            const int i = e % kB2, j = e / kB2;
+            S1[i][j] = A[pair_index(ap, aq, i) + (size_t)pair_index(bp, bq, j) * N];
+            S2[i][j] = Qbuf[(size_t)a * kB2 * kB2 + e];
+            S3[i][j] = Qbuf[(size_t)b * kB2 * kB2 + e];
+          }
+          __syncthreads();
+          // S4 = Qa^T S1
+          for (int e = tid; e < kB2 * kB2; e += nt) {
+            const int i = e % kB2, j = e / kB2;
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int t = 0; t < kB2; ++t) acc = fmaf(S2[t][i], S1[t][j], acc);
+            S4[i][j] = acc;
+          }
+          __syncthreads();
+          float lo = 0.0f;
+          for (int e = tid; e < kB2 * kB2; e += nt) {
+            const int i = e % kB2, j = e / kB2;
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int t = 0; t < kB2; ++t) acc = fmaf(S4[i][t], S3[t][j], acc);
+            const int gi = pair_index(ap, aq, i), gj = pair_index(bp, bq, j);
+            A[gi + (size_t)gj * N] = acc;
+            A[gj + (size_t)gi * N] = acc;
+            lo += acc * acc;
+          }
+          if (last) {
+            off += 2.0f * lo;
+            tot += 2.0f * lo;
+          }
+          __syncthreads();
+        } else {
+          const int it2 = item - npairs;
+          const int chunk = it2 % (N / kB2), a = it2 / (N / kB2);
+          const int ap = blk_of_pair(nb, r, a, 0), aq = blk_of_pair(nb, r, a, 1);
+          for (int e = tid; e < kB2 * kB2; e += nt) {
+            const int i = e % kB2, j = e / kB2;
+            S1[i][j] = V[(chunk * kB2 + i) + (size_t)pair_index(ap, aq, j) * N];
+            S2[i][j] = Qbuf[(size_t)a * kB2 * kB2 + e];
+          }
+          __syncthreads();
+          for (int e = tid; e < kB2 * kB2; e += nt) {
+            const int i = e % kB2, j = e / kB2;
+            float acc = 0.0f;
+#pragma unroll 8
+            for (int t = 0; t < kB2; ++t) acc = fmaf(S1[i][t], S2[t][j], acc);
+            V[(chunk * kB2 + i) + (size_t)pair_index(ap, aq, j) * N] = acc;
+          }
+          __syncthreads();
+        }
+      }
+      grid.sync();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    }
+    if (tid % 32 == 0) {
+      red_off[tid / 32] = off;
+      red_tot[tid / 32] = tot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float so = 0.0f, st = 0.0f;
+      for (int w = 0; w < nt / 32; ++w) {
+        so += red_off[w];
+        st += red_tot[w];
+      }
+      part[blockIdx.x] = make_float2(so, st);
+    }
+    grid.sync();
+    float so = 0.0f, st = 0.0f;
+    for (int c = 0; c < (int)gridDim.x; ++c) {
+      so += part[c].x;
+      st += part[c].y;
+    }
+    grid.sync();
+    const bool done = jacobi_done(sweep, so, st, prev_off);
+    prev_off = so;
+    if (done) {
+      ++sweep;
+      break;
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
+}
+
 // ------------------------------------------------------ refinement helpers --
 __global__ void f32_to_f64_block(int n, int N, const float* __restrict__ V, double* __restrict__ X) {
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
@@ -407,9 +609,11 @@ __global__ void sort_desc(int n, const double* __restrict__ lam_in, const double
 // One level: FP32 Jacobi, FP64 refinement, sort.  *delta_dev receives the
 // refinement's cluster width d (pairs closer than d are not resolved).
 blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
-                          double* delta_out) {
+                          double* delta_out, bool sorted = true) {
   if (n <= 0) return BLWS_OK;
-  const int N = n + (n & 1);
+  const bool small = n + (n & 1) <= kCtaMaxN;
+  // padded size: even for the one-CTA solver; an even number of kBS blocks otherwise
+  const int N = small ? n + (n & 1) : ceil_div(n, 2 * kBS) * 2 * kBS;
   // scratch: FP32 A0, A1, V (N^2 each) ; FP64 X, X2, R, S, TX, E (n^2 each); small vectors
   float* f = nullptr;
   BLWS_TRY(ctx->get(BUF_EIG, (size_t)3 * N * N * sizeof(float) + (size_t)6 * n * n * sizeof(double) +
@@ -429,27 +633,28 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
   double* delta = part + 3 * 1024;
   int* sweeps = reinterpret_cast<int*>(delta + 8);
 
-  if (N <= kCtaMaxN) {
+  if (small) {
     const size_t smem = 2ull * N * N * sizeof(float);
     BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(jacobi_cta_kernel,
                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     jacobi_cta_kernel<<<1, 1024, smem, s>>>(n, N, T, V, sweeps);
     BLWS_CHECK_LAUNCH(ctx);
   } else {
-    const int threads = 512;
-    const size_t smem = (size_t)(N / 2) * sizeof(Rot);
+    // block-pair Jacobi: Qbuf (P x 32 x 32) reuses A1
+    const int threads = 256;
     int per_sm = 0;
-    BLWS_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_grid_kernel,
-                                                                     threads, smem));
-    if (per_sm < 1) return ctx->fail(BLWS_ECUDA, "jacobi_grid_kernel cannot be resident");
-    const long long blocks_needed = ((long long)(N / 2) * (N / 2) + threads - 1) / threads;
-    int grid = (int)std::min<long long>(blocks_needed, (long long)ctx->sms);
-    grid = std::max(grid, 1);
+    BLWS_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel,
+                                                                     threads, 0));
+    if (per_sm < 1) return ctx->fail(BLWS_ECUDA, "jacobi_block_kernel cannot be resident");
+    const int P = N / kBS / 2;
+    const int items = P * (P - 1) / 2 + (N / kB2) * P;
+    int grid = std::min(std::max(items, P), ctx->sms * per_sm);
+    grid = std::max(std::min(grid, ctx->sms * per_sm), 1);
     float2* fpart = reinterpret_cast<float2*>(part);
     int nn = n, NN = N;
-    void* args[] = {&nn, &NN, (void*)&T, &A0, &A1, &V, &fpart, &sweeps};
-    BLWS_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((void*)jacobi_grid_kernel, grid, threads, args,
-                                                   smem, s));
+    void* args[] = {&nn, &NN, (void*)&T, &A0, &V, &A1, &fpart, &sweeps};
+    BLWS_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((void*)jacobi_block_kernel, grid, threads, args,
+                                                   0, s));
     ++ctx->launches;
   }
   const int eb = std::min(ceil_div((long long)n * n, 256), ctx->sms * 4);
@@ -472,8 +677,13 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
     BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, X, n, E, n, 1.0, X2, n));
     std::swap(X, X2);
   }
-  sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, lam, Z);
-  BLWS_CHECK_LAUNCH(ctx);
+  if (sorted) {
+    sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, lam, Z);
+    BLWS_CHECK_LAUNCH(ctx);
+  } else {
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(lam, lam_u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(Z, X, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
+  }
   if (delta_out)
     BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(delta_out, delta, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return BLWS_OK;
@@ -481,16 +691,26 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
 
 namespace {
 
-// K = (S - mu I) / scale for the cluster block S (c x c)
-__global__ void shift_scale(int c, const double* __restrict__ S, double mu, double inv_scale, double* K) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
-    const int i = e % c, j = e / c;
-    K[e] = (S[e] - (i == j ? mu : 0.0)) * inv_scale;
+// K = blockdiag over clusters of (S - mu_c I) / scale_c; cross-cluster entries 0
+__global__ void cluster_blocks(int n2, const double* __restrict__ S, const int* __restrict__ blk,
+                               const double* __restrict__ mu, const double* __restrict__ inv_scale,
+                               double* K) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * n2; e += gridDim.x * blockDim.x) {
+    const int a = e % n2, b = e / n2;
+    double v = 0.0;
+    if (blk[a] == blk[b]) v = (S[e] - (a == b ? mu[a] : 0.0)) * inv_scale[a];
+    K[e] = v;
   }
 }
 
-__global__ void unshift(int c, const double* __restrict__ nu, double mu, double scale, double* lam) {
-  for (int i = threadIdx.x; i < c; i += blockDim.x) lam[i] = fma(scale, nu[i], mu);
+// Out(:, p) = In(:, perm[p])
+__global__ void gather_cols(int rows, int cols, const double* __restrict__ In,
+                            const int* __restrict__ perm, double* Out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)rows * cols;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % rows), p = (int)(e / rows);
+    Out[e] = In[r + (size_t)perm[p] * rows];
+  }
 }
 
 }  // namespace
@@ -514,36 +734,87 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   const double d = h[32];
   if (!(d > 0.0)) return BLWS_OK;
-  int i = 0;
-  while (i < n) {
+  // clusters (runs of sorted values closer than d) that reach above eps - 3d
+  struct Cl { int i, j; double mu, scale; };
+  std::vector<Cl> cl;
+  int n2 = 0;
+  for (int i = 0; i < n;) {
     int j = i + 1;
     while (j < n && hl[j - 1] - hl[j] <= d) ++j;
-    const int c = j - i;
-    if (c >= 2 && hl[i] > eps - 3.0 * d) {
-      const double mu = 0.5 * (hl[i] + hl[j - 1]);
-      const double scale = 0.5 * (hl[i] - hl[j - 1]) + d;
-      double* w;
-      BLWS_TRY(ctx->get(BUF_EIG2, (size_t)n * c * 2 + (size_t)c * c * 3 + c, &w));
-      double* TX = w;                       // n x c
-      double* Zc = TX + (size_t)n * c;      // n x c
-      double* K = Zc + (size_t)n * c;       // c x c
-      double* ZK = K + (size_t)c * c;       // c x c
-      double* S = ZK + (size_t)c * c;       // c x c
-      double* nu = S + (size_t)c * c;       // c
-      const double* Xc = Z + (size_t)i * n;
-      BLWS_TRY(gemm(ctx, s, false, false, n, c, n, 1.0, T, n, Xc, n, 0.0, TX, n));
-      BLWS_TRY(gemm(ctx, s, true, false, c, c, n, 1.0, Xc, n, TX, n, 0.0, S, c));
-      shift_scale<<<ceil_div((long long)c * c, 256), 256, 0, s>>>(c, S, mu, 1.0 / scale, K);
-      BLWS_CHECK_LAUNCH(ctx);
-      BLWS_TRY(sym_eig_level(ctx, s, c, K, nu, ZK, nullptr));
-      unshift<<<1, 256, 0, s>>>(c, nu, mu, scale, lam + i);
-      BLWS_CHECK_LAUNCH(ctx);
-      BLWS_TRY(gemm(ctx, s, false, false, n, c, c, 1.0, Xc, n, ZK, c, 0.0, Zc, n));
-      BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(Z + (size_t)i * n, Zc, sizeof(double) * n * c,
-                                         cudaMemcpyDeviceToDevice, s));
+    if (j - i >= 2 && hl[i] > eps - 3.0 * d) {
+      cl.push_back({i, j, 0.5 * (hl[i] + hl[j - 1]), 0.5 * (hl[i] - hl[j - 1]) + d});
+      n2 += j - i;
     }
     i = j;
   }
+  if (cl.empty()) return BLWS_OK;
+  // all clusters in one block-diagonal problem
+  double* w;
+  BLWS_TRY(ctx->get(BUF_EIG2, (size_t)n * n2 * 3 + (size_t)n2 * n2 * 3 + (size_t)n2 * 4, &w));
+  double* Xu = w;                        // n x n2: the clusters' current vectors
+  double* TX = Xu + (size_t)n * n2;      // n x n2
+  double* Zc = TX + (size_t)n * n2;      // n x n2
+  double* S = Zc + (size_t)n * n2;       // n2 x n2
+  double* K = S + (size_t)n2 * n2;       // n2 x n2
+  double* ZK = K + (size_t)n2 * n2;      // n2 x n2
+  double* nu = ZK + (size_t)n2 * n2;     // n2
+  double* bmu = nu + n2;                 // n2
+  double* binv = bmu + n2;               // n2
+  int* bid = reinterpret_cast<int*>(binv + n2);  // n2 ints, then n2 ints of perm
+  int* perm = bid + n2;
+  std::vector<double> hmu(n2), hinv(n2);
+  std::vector<int> hid(n2);
+  for (size_t c = 0, o = 0; c < cl.size(); ++c) {
+    const int sz = cl[c].j - cl[c].i;
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(Xu + o * n, Z + (size_t)cl[c].i * n, sizeof(double) * n * sz,
+                                       cudaMemcpyDeviceToDevice, s));
+    for (int t = 0; t < sz; ++t) {
+      hmu[o + t] = cl[c].mu;
+      hinv[o + t] = 1.0 / cl[c].scale;
+      hid[o + t] = (int)c;
+    }
+    o += sz;
+  }
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(bmu, hmu.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(binv, hinv.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(bid, hid.data(), sizeof(int) * n2, cudaMemcpyHostToDevice, s));
+  BLWS_TRY(gemm(ctx, s, false, false, n, n2, n, 1.0, T, n, Xu, n, 0.0, TX, n));
+  BLWS_TRY(gemm(ctx, s, true, false, n2, n2, n, 1.0, Xu, n, TX, n, 0.0, S, n2));
+  cluster_blocks<<<std::min(ceil_div((long long)n2 * n2, 256), ctx->sms * 4), 256, 0, s>>>(
+      n2, S, bid, bmu, binv, K);
+  BLWS_CHECK_LAUNCH(ctx);
+  // block-diagonal K: cross-block entries stay exactly zero through the Jacobi
+  // rotations and the refinement, so unsorted column a belongs to block bid[a]
+  BLWS_TRY(sym_eig_level(ctx, s, n2, K, nu, ZK, nullptr, false));
+  std::vector<double> hnu(n2);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hnu.data(), nu, sizeof(double) * n2, cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  std::vector<int> hperm(n2);
+  std::vector<double> hlam(n2);
+  for (size_t c = 0, o = 0; c < cl.size(); ++c) {
+    const int sz = cl[c].j - cl[c].i;
+    for (int t = 0; t < sz; ++t) hperm[o + t] = (int)(o + t);
+    std::stable_sort(hperm.begin() + o, hperm.begin() + o + sz,
+                     [&](int a, int b) { return hnu[a] > hnu[b]; });
+    for (int t = 0; t < sz; ++t) hlam[o + t] = cl[c].mu + cl[c].scale * hnu[hperm[o + t]];
+    o += sz;
+  }
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(perm, hperm.data(), sizeof(int) * n2, cudaMemcpyHostToDevice, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(bmu, hlam.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
+  gather_cols<<<std::min(ceil_div((long long)n2 * n2, 256), ctx->sms * 4), 256, 0, s>>>(n2, n2, ZK,
+                                                                                      perm, K);
+  BLWS_CHECK_LAUNCH(ctx);
+  BLWS_TRY(gemm(ctx, s, false, false, n, n2, n2, 1.0, Xu, n, K, n2, 0.0, Zc, n));
+  for (size_t c = 0, o = 0; c < cl.size(); ++c) {
+    const int sz = cl[c].j - cl[c].i;
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(Z + (size_t)cl[c].i * n, Zc + o * n, sizeof(double) * n * sz,
+                                       cudaMemcpyDeviceToDevice, s));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(lam + cl[c].i, bmu + o, sizeof(double) * sz,
+                                       cudaMemcpyDeviceToDevice, s));
+    o += sz;
+  }
+  // the host vectors above are read by asynchronous copies: wait before they go
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   return BLWS_OK;
 }
 

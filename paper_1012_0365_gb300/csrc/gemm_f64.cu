@@ -107,11 +107,14 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
                          double* C, int ldc) {
   const int tm = ceil_div(M, BM), tn = ceil_div(N, BN);
   const int tiles = tm * tn;
-  const int target = 2 * ctx->sms;
+  // DFMA-bound: balance the SMs.  About 8 CTAs per SM (of which ~4 are
+  // resident at once) keeps the tail of the last wave under ~1/8 of the run;
+  // the inner dimension is split (chunks >= 32) until that many CTAs exist.
+  const int target = 8 * ctx->sms;
   int splits = 1;
-  if (tiles < target && K > 4 * kBK) {
+  if (tiles < target && K > 2 * kBK) {
     splits = ceil_div(target, tiles);
-    splits = min(splits, ceil_div(K, 4 * kBK));
+    splits = min(splits, ceil_div(K, 2 * kBK));
     splits = max(splits, 1);
   }
   int kchunk = ceil_div(ceil_div(K, splits), kBK) * kBK;

@@ -64,7 +64,8 @@ CASES = [
     (300, 17, 3, 3, 4, 2),       # tall, ragged
     (17, 300, 3, 4, 4, 3),       # wide
     (129, 130, 20, 18, 24, 3),   # width not a multiple of any tile, padding columns
-    (513, 257, 30, 33, 33, 2),   # T_k wider than the one-CTA eigen-solver
+    (513, 257, 30, 33, 33, 2),   # T_k of 66
+    (600, 400, 40, 60, 60, 3),   # T_k of 180: the block-pair Jacobi path
     (1, 9, 1, 1, 1, 2),          # a single row
 ]
 
