@@ -11,8 +11,13 @@
 // procedure exact when a warm start spans an invariant subspace (R_l = 0).
 //
 // The Gram matrices and the products with the tall block are FP64 GEMMs over
-// the whole GPU; the b x b factorisation runs in one CTA.
+// the whole GPU; the b x b factorisation runs on one thread-block cluster
+// (one CTA for b above kCMaxB).
+#include <cooperative_groups.h>
+
 #include "ops.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace blws {
 
@@ -89,16 +94,26 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
     }
     __syncthreads();
   }
-  // Li = L^-1 (lower), one thread per column; reciprocals of the diagonal first
+  // Li = L^-1 (lower) by forward substitution, one warp per column: the lanes
+  // split each dot product and reduce by shuffles (the column's entries depend
+  // on each other in order, so parallelism is across and within columns).
   for (int i = tid; i < b; i += nt) dinv[i] = 1.0 / L[i + (size_t)i * b];
   __syncthreads();
-  for (int c = tid; c < b; c += nt) {
-    for (int i = 0; i < c; ++i) Li[i + (size_t)c * b] = 0.0;
-    Li[c + (size_t)c * b] = dinv[c];
-    for (int i = c + 1; i < b; ++i) {
-      double acc = 0.0;
-      for (int k = c; k < i; ++k) acc = fma(L[i + (size_t)k * b], Li[k + (size_t)c * b], acc);
-      Li[i + (size_t)c * b] = -acc * dinv[i];
+  {
+    const int lane = tid % 32, warp = tid / 32, nwarps = nt / 32;
+    for (int c = warp; c < b; c += nwarps) {
+      double* lic = Li + (size_t)c * b;
+      for (int i = lane; i < c; i += 32) lic[i] = 0.0;
+      if (lane == 0) lic[c] = dinv[c];
+      __syncwarp();
+      for (int i = c + 1; i < b; ++i) {
+        double acc = 0.0;
+        for (int k = c + lane; k < i; k += 32) acc = fma(L[i + (size_t)k * b], lic[k], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) lic[i] = -acc * dinv[i];
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -121,14 +136,242 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
   }
 }
 
+// ---------------------------------------------------------------------------
+// The same factorisation spread over a cluster of kCC CTAs (b <= kCMaxB).
+// One SM retires about two FP64 FMAs per clock, so the one-CTA kernel above
+// is bound by a single SM's FP64 pipe; here the equilibrated matrix is cut
+// into 16 x 16 tiles, owned round-robin by the CTAs of the cluster and read
+// across CTAs through distributed shared memory.  Tile step jt:
+//   (1) the owner of tile (jt, jt) factors it (pivot and deflation rules as
+//       above), (2) cluster barrier, (3) the owners of tiles (it, jt), it > jt,
+//       solve L_it,jt L_jt,jt^T = A_it,jt (dead columns set to zero),
+//   (4) cluster barrier, (5) every CTA subtracts L_it,jt L_kt,jt^T from its
+//       tiles (it, kt), it >= kt > jt.
+// Then every CTA gathers the factor (packed lower triangle) and its warps
+// compute the columns of L^-1 by forward substitution, writing rows of S and B.
+constexpr int kCT = 16;      // tile size
+constexpr int kCC = 8;       // CTAs per cluster (portable cluster size)
+constexpr int kCMaxB = 192;  // largest b on this path (shared memory bound)
+constexpr int kCThreads = 256;
+
+struct CholLayout {  // offsets in doubles, identical in every CTA of the cluster
+  int nt, ntiles, tiles_per_cta;
+  size_t off_tiles, off_big, off_ld, off_xs, off_d, off_dinv, off_dl, off_dead, total;
+  __host__ __device__ explicit CholLayout(int b) {
+    nt = (b + kCT - 1) / kCT;
+    ntiles = nt * (nt + 1) / 2;
+    tiles_per_cta = (ntiles + kCC - 1) / kCC;
+    const size_t big_panel = (size_t)nt * kCT * kCT;        // column of tiles
+    const size_t big_packed = (size_t)b * (b + 1) / 2;      // packed lower triangle
+    off_tiles = 0;
+    off_big = off_tiles + (size_t)tiles_per_cta * kCT * kCT;
+    off_ld = off_big + (big_panel > big_packed ? big_panel : big_packed);
+    off_xs = off_ld + kCT * kCT;
+    off_d = off_xs + (size_t)(kCThreads / 32) * b;
+    off_dinv = off_d + nt * kCT;
+    off_dl = off_dinv + nt * kCT;
+    off_dead = off_dl + nt * kCT;  // ints, nt * kCT of them
+    total = off_dead + (nt * kCT + 1) / 2;
+  }
+};
+
+__device__ inline void tile_of_lin(int lin, int& it, int& jt) {
+  it = (int)((sqrtf(8.0f * lin + 1.0f) - 1.0f) * 0.5f);
+  while (it * (it + 1) / 2 > lin) --it;
+  while ((it + 1) * (it + 2) / 2 <= lin) ++it;
+  jt = lin - it * (it + 1) / 2;
+}
+
+__global__ void __cluster_dims__(kCC, 1, 1) __launch_bounds__(kCThreads)
+chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restrict__ scale_ptr,
+                    double tol, double* __restrict__ S, double* __restrict__ Bout) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double smem[];
+  const CholLayout lay(b);
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  double* tiles = smem + lay.off_tiles;
+  double* big = smem + lay.off_big;   // panel copy during the factorisation, packed L after
+  double* Ld = smem + lay.off_ld;     // copy of the diagonal tile of the step
+  double* xs = smem + lay.off_xs;     // one column of L^-1 per warp
+  double* d = smem + lay.off_d;
+  double* dinv = smem + lay.off_dinv;
+  double* dl = smem + lay.off_dl;     // 1 / L_jj
+  int* dead = reinterpret_cast<int*>(smem + lay.off_dead);
+  __shared__ double piv_sh;
+  const int nt = lay.nt;
+  const double thr = tol * (*scale_ptr);
+  auto owner = [](int it, int jt) { return (it * (it + 1) / 2 + jt) % kCC; };
+  auto slot = [&](int it, int jt) { return tiles + (size_t)((it * (it + 1) / 2 + jt) / kCC) * 256; };
+
+  for (int j = tid; j < nt * kCT; j += kCThreads) {
+    double dj = 0.0;
+    bool dz = true;
+    if (j < b) {
+      const double g = G[j + (size_t)j * b];
+      dj = g > 0.0 ? sqrt(g) : 0.0;
+      dz = !(dj > thr);
+    }
+    dead[j] = dz ? 1 : 0;
+    d[j] = dz ? 1.0 : dj;
+    dinv[j] = dz ? 1.0 : 1.0 / dj;
+  }
+  __syncthreads();
+  // my tiles of the equilibrated lower triangle; padding rows and columns
+  // (index >= b) are identity, dead columns unit vectors
+  for (int lin = rank; lin < lay.ntiles; lin += kCC) {
+    int it, jt;
+    tile_of_lin(lin, it, jt);
+    double* T = tiles + (size_t)(lin / kCC) * 256;
+    for (int e = tid; e < 256; e += kCThreads) {
+      const int i = it * kCT + e % kCT, j = jt * kCT + e / kCT;
+      double v = 0.0;
+      if (i >= j) {
+        if (i >= b || j >= b || dead[i] || dead[j]) v = (i == j) ? 1.0 : 0.0;
+        else v = G[i + (size_t)j * b] * dinv[i] * dinv[j];
+      }
+      T[e] = v;
+    }
+  }
+  __syncthreads();
+
+  for (int jt = 0; jt < nt; ++jt) {
+    // (1) factor the diagonal tile (one warp)
+    if (rank == owner(jt, jt) && warp == 0) {
+      double* T = slot(jt, jt);
+      for (int c = 0; c < kCT; ++c) {
+        const int j = jt * kCT + c;
+        if (lane == 0) {
+          const double p = T[c + kCT * c];
+          bool dj = dead[j] != 0;
+          if (!dj) {
+            const double rdiag = d[j] * sqrt(p > 0.0 ? p : 0.0);
+            if (!(p > kPivMin) || !(rdiag > thr)) dj = true;
+          }
+          dead[j] = dj ? 1 : 0;
+          piv_sh = dj ? 1.0 : sqrt(p);
+          T[c + kCT * c] = piv_sh;
+        }
+        __syncwarp();
+        const double rl = 1.0 / piv_sh;
+        const bool dj = dead[j] != 0;
+        if (lane > c && lane < kCT) T[lane + kCT * c] = dj ? 0.0 : T[lane + kCT * c] * rl;
+        __syncwarp();
+        if (!dj) {
+          for (int e = lane; e < kCT * kCT; e += 32) {
+            const int r = e % kCT, k = e / kCT;
+            if (k > c && r >= k) T[r + kCT * k] -= T[r + kCT * c] * T[k + kCT * c];
+          }
+        }
+        __syncwarp();
+      }
+    }
+    cl.sync();  // (2)
+    // (3) everyone copies the factored diagonal tile and its dead flags
+    {
+      const int o = owner(jt, jt);
+      const double* rT = cl.map_shared_rank(slot(jt, jt), o);
+      const int* rdead = cl.map_shared_rank(dead, o);
+      for (int e = tid; e < 256; e += kCThreads) Ld[e] = rT[e];
+      if (tid < kCT) dead[jt * kCT + tid] = rdead[jt * kCT + tid];
+    }
+    __syncthreads();
+    for (int it = jt + 1 + tid / kCT; it < nt; it += kCThreads / kCT) {
+      if (owner(it, jt) != rank) continue;
+      double* T = slot(it, jt);
+      const int r = tid % kCT;
+      double x[kCT];
+#pragma unroll
+      for (int c = 0; c < kCT; ++c) {
+        double acc = T[r + kCT * c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) acc = fma(-x[k], Ld[c + kCT * k], acc);
+        x[c] = dead[jt * kCT + c] ? 0.0 : acc / Ld[c + kCT * c];
+      }
+#pragma unroll
+      for (int c = 0; c < kCT; ++c) T[r + kCT * c] = x[c];
+    }
+    cl.sync();  // (4)
+    // (5) copy the factored column of tiles, update my trailing tiles
+    for (int e = tid; e < (nt - jt - 1) * 256; e += kCThreads) {
+      const int it = jt + 1 + e / 256;
+      big[(size_t)it * 256 + e % 256] = cl.map_shared_rank(slot(it, jt), owner(it, jt))[e % 256];
+    }
+    __syncthreads();
+    for (int lin = rank; lin < lay.ntiles; lin += kCC) {
+      int it, kt;
+      tile_of_lin(lin, it, kt);
+      if (kt <= jt) continue;
+      double* T = tiles + (size_t)(lin / kCC) * 256;
+      const double* Pi = big + (size_t)it * 256;
+      const double* Pk = big + (size_t)kt * 256;
+      for (int e = tid; e < 256; e += kCThreads) {
+        const int r = e % kCT, k = e / kCT;
+        if (it == kt && r < k) continue;
+        double acc = T[e];
+#pragma unroll
+        for (int c = 0; c < kCT; ++c) acc = fma(-Pi[r + kCT * c], Pk[k + kCT * c], acc);
+        T[e] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  // gather the whole factor, packed by columns: (i, j) at j b - j (j - 1) / 2 + i - j
+  cl.sync();
+  for (int e = tid; e < lay.ntiles * 256; e += kCThreads) {
+    const int lin = e / 256, rc = e % 256;
+    int it, jt;
+    tile_of_lin(lin, it, jt);
+    const int i = it * kCT + rc % kCT, j = jt * kCT + rc / kCT;
+    if (i < j || i >= b || j >= b) continue;
+    const double* rT = cl.map_shared_rank(tiles + (size_t)(lin / kCC) * 256, lin % kCC);
+    big[(size_t)j * b - (size_t)j * (j - 1) / 2 + (i - j)] = rT[rc];
+  }
+  cl.sync();  // no CTA reads another's shared memory after this point
+  for (int j = tid; j < b; j += kCThreads) dl[j] = 1.0 / big[(size_t)j * b - (size_t)j * (j - 1) / 2];
+  __syncthreads();
+  // columns of L^-1, one warp each; S(c, j) = Li(j, c) / d_c, B(c, j) = L(j, c) d_j
+  double* x = xs + (size_t)warp * b;
+  for (int c = rank * (kCThreads / 32) + warp; c < b; c += kCC * (kCThreads / 32)) {
+    for (int i = c + lane; i < b; i += 32) x[i] = (i == c) ? 1.0 : 0.0;
+    __syncwarp();
+    for (int k = c; k < b; ++k) {
+      const double xk = x[k] * dl[k];
+      const double* Lk = big + (size_t)k * b - (size_t)k * (k - 1) / 2 - k;  // Lk[i] = L(i, k)
+      __syncwarp();
+      if (lane == 0) x[k] = xk;
+      for (int i = k + 1 + lane; i < b; i += 32) x[i] = fma(-Lk[i], xk, x[i]);
+      __syncwarp();
+    }
+    const bool dc = dead[c] != 0;
+    const double* Lc = big + (size_t)c * b - (size_t)c * (c - 1) / 2 - c;
+    for (int j = lane; j < b; j += 32) {
+      double sv = 0.0, bv = 0.0;
+      if (j >= c && !dc) {
+        if (!dead[j]) sv = x[j] * dinv[c];
+        if (!dead[j] || c < j) bv = Lc[j] * d[j];
+      }
+      S[c + (size_t)j * b] = sv;
+      Bout[c + (size_t)j * b] = bv;
+    }
+    __syncwarp();
+  }
+}
+
 blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const double* scale,
                        double tol, double* S, double* B, double* gwork) {
   if (b > 1024) return ctx->fail(BLWS_EINVAL, "block width %d exceeds 1024", b);
+  if (b <= kCMaxB) {
+    const size_t bytes = CholLayout(b).total * sizeof(double);
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL_CLUSTER, (const void*)chol_cluster_kernel, (int)bytes));
+    chol_cluster_kernel<<<kCC, kCThreads, bytes, s>>>(b, G, scale, tol, S, B);
+    BLWS_CHECK_LAUNCH(ctx);
+    return BLWS_OK;
+  }
   const size_t need = 2ull * b * b * sizeof(double);
   const int use_smem = need <= 200 * 1024 ? 1 : 0;
   if (use_smem) {
-    BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(chol_equil_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL, (const void*)chol_equil_kernel, (int)need));
   }
   chol_equil_kernel<<<1, 1024, use_smem ? need : 0, s>>>(b, G, scale, tol, S, B, gwork, use_smem);
   BLWS_CHECK_LAUNCH(ctx);

@@ -191,99 +191,6 @@ jacobi_cta_kernel(int n, int N, const double* __restrict__ T, float* __restrict_
   if (tid == 0) *sweeps_out = sweep;
 }
 
-// ------------------------------------- cooperative-grid Jacobi (global) --
-// A0/A1: double-buffered FP32 matrices (N x N); V: FP32 N x N; part: one
-// float2 per CTA for the convergence test.
-__global__ void __launch_bounds__(512)
-jacobi_grid_kernel(int n, int N, const double* __restrict__ T, float* A0, float* A1, float* V,
-                   float2* part, int* sweeps_out) {
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ Rot rot_dyn[];
-  __shared__ float red_off[16], red_tot[16];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const size_t gtid = (size_t)blockIdx.x * nt + tid, gnt = (size_t)gridDim.x * nt;
-  const int half = N / 2;
-  for (size_t e = gtid; e < (size_t)N * N; e += gnt) {
-    const int i = (int)(e % N), j = (int)(e / N);
-    A0[e] = (i < n && j < n) ? (float)T[i + (size_t)j * n] : 0.0f;
-    V[e] = (i == j) ? 1.0f : 0.0f;
-  }
-  grid.sync();
-  float* cur = A0;
-  float* nxt = A1;
-  int sweep = 0;
-  float prev_off = 3.0e38f;
-  for (; sweep < kJacobiMaxSweeps; ++sweep) {
-    float off = 0.0f, tot = 0.0f;
-    for (int r = 0; r < N - 1; ++r) {
-      for (int k = tid; k < half; k += nt) {
-        Rot R;
-        rr_pair(N, r, k, R.p, R.q);
-        jacobi_rot(cur[R.p + (size_t)R.p * N], cur[R.q + (size_t)R.q * N], cur[R.p + (size_t)R.q * N],
-                   R.c, R.s);
-        rot_dyn[k] = R;
-      }
-      __syncthreads();
-      const bool last = (r == N - 2);
-      for (size_t e = gtid; e < (size_t)half * half; e += gnt) {
-        const int i = (int)(e % half), j = (int)(e / half);
-        apply_block(cur, nxt, N, rot_dyn[i], rot_dyn[j], i == j);
-        if (last) {
-          const Rot& ri = rot_dyn[i];
-          const Rot& rj = rot_dyn[j];
-          const float a = nxt[ri.p + (size_t)rj.p * N], b = nxt[ri.p + (size_t)rj.q * N];
-          const float c = nxt[ri.q + (size_t)rj.p * N], d = nxt[ri.q + (size_t)rj.q * N];
-          tot += a * a + b * b + c * c + d * d;
-          off += (i == j) ? (b * b + c * c) : (a * a + b * b + c * c + d * d);
-        }
-      }
-      for (size_t e = gtid; e < (size_t)N * half; e += gnt) {
-        const int x = (int)(e % N), j = (int)(e / N);
-        const Rot R = rot_dyn[j];
-        const float vp = V[x + (size_t)R.p * N], vq = V[x + (size_t)R.q * N];
-        V[x + (size_t)R.p * N] = R.c * vp - R.s * vq;
-        V[x + (size_t)R.q * N] = R.s * vp + R.c * vq;
-      }
-      float* t = cur;
-      cur = nxt;
-      nxt = t;
-      grid.sync();
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    }
-    if (tid % 32 == 0) {
-      red_off[tid / 32] = off;
-      red_tot[tid / 32] = tot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      float so = 0.0f, st = 0.0f;
-      for (int w = 0; w < nt / 32; ++w) {
-        so += red_off[w];
-        st += red_tot[w];
-      }
-      part[blockIdx.x] = make_float2(so, st);
-    }
-    grid.sync();
-    float so = 0.0f, st = 0.0f;
-    for (int c = 0; c < (int)gridDim.x; ++c) {
-      so += part[c].x;
-      st += part[c].y;
-    }
-    grid.sync();  // everyone has read part before it is rewritten
-    const bool done = jacobi_done(sweep, so, st, prev_off);
-    prev_off = so;
-    if (done) {
-      ++sweep;
-      break;
-    }
-  }
-  if (blockIdx.x == 0 && tid == 0) *sweeps_out = sweep;
-}
-
 // --------------------------------- block-pair Jacobi (cooperative grid) --
 // Blocks of kBS indices; each round pairs the nb blocks round-robin.  Phase 1:
 // one CTA per block pair runs ONE cyclic Jacobi sweep on its (2 kBS)^2
@@ -291,8 +198,13 @@ jacobi_grid_kernel(int n, int N, const double* __restrict__ T, float* A0, float*
 // Q (2 kBS x 2 kBS).  Phase 2: every off-diagonal block pair (a, b) becomes
 // Q_a^T A_ab Q_b, and every row chunk of V becomes V Q_a.  One grid barrier
 // per phase: 2 (nb - 1) barriers per sweep instead of one per scalar round.
-constexpr int kBS = 16;
-constexpr int kB2 = 2 * kBS;  // 32
+// Block width: BS indices per block, 2 BS per pair (template parameters, so
+// the shared-memory tiles and loop bounds are compile-time constants).
+#ifndef BLWS_JACOBI_BS
+#define BLWS_JACOBI_BS 8
+#endif
+constexpr int kBS = BLWS_JACOBI_BS;
+constexpr int kBlockThreads = kBS >= 32 ? 512 : 256;
 
 __device__ inline int blk_of_pair(int nb, int r, int k, int which) {
   int p, q;
@@ -300,23 +212,27 @@ __device__ inline int blk_of_pair(int nb, int r, int k, int which) {
   return which ? q : p;
 }
 
-// global index of local row i (0..kB2) of pair (bp, bq)
+// global index of local row i (0..2 BS) of pair (bp, bq)
+template <int BS>
 __device__ inline int pair_index(int bp, int bq, int i) {
-  return i < kBS ? bp * kBS + i : bq * kBS + (i - kBS);
+  return i < BS ? bp * BS + i : bq * BS + (i - BS);
 }
 
-__global__ void __launch_bounds__(256)
+template <int BS, int NT>
+__global__ void __launch_bounds__(NT)
 jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float* V, float* Qbuf,
                     float2* part, int* sweeps_out) {
+  constexpr int kB2 = 2 * BS;
   cg::grid_group grid = cg::this_grid();
-  __shared__ float S1[kB2][kB2 + 1];
-  __shared__ float S2[kB2][kB2 + 1];
-  __shared__ float S3[kB2][kB2 + 1];
-  __shared__ float S4[kB2][kB2 + 1];
+  extern __shared__ float bsm[];
+  float(*S1)[kB2 + 1] = reinterpret_cast<float(*)[kB2 + 1]>(bsm);
+  float(*S2)[kB2 + 1] = reinterpret_cast<float(*)[kB2 + 1]>(bsm + kB2 * (kB2 + 1));
+  float(*S3)[kB2 + 1] = reinterpret_cast<float(*)[kB2 + 1]>(bsm + 2 * kB2 * (kB2 + 1));
+  float(*S4)[kB2 + 1] = reinterpret_cast<float(*)[kB2 + 1]>(bsm + 3 * kB2 * (kB2 + 1));
   __shared__ Rot rot[kB2 / 2];
-  __shared__ float red_off[8], red_tot[8];
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int nb = N / kBS, P = nb / 2;
+  __shared__ float red_off[NT / 32], red_tot[NT / 32];
+  const int tid = threadIdx.x, nt = NT;
+  const int nb = N / BS, P = nb / 2;
   const size_t gtid = (size_t)blockIdx.x * nt + tid, gnt = (size_t)gridDim.x * nt;
   for (size_t e = gtid; e < (size_t)N * N; e += gnt) {
     const int i = (int)(e % N), j = (int)(e / N);
@@ -335,7 +251,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
         const int bp = blk_of_pair(nb, r, k, 0), bq = blk_of_pair(nb, r, k, 1);
         for (int e = tid; e < kB2 * kB2; e += nt) {
           const int i = e % kB2, j = e / kB2;
-          S1[i][j] = A[pair_index(bp, bq, i) + (size_t)pair_index(bp, bq, j) * N];
+          S1[i][j] = A[pair_index<BS>(bp, bq, i) + (size_t)pair_index<BS>(bp, bq, j) * N];
           S2[i][j] = (i == j) ? 1.0f : 0.0f;
         }
         __syncthreads();
@@ -373,7 +289,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
         for (int e = tid; e < kB2 * kB2; e += nt) {
           const int i = e % kB2, j = e / kB2;
           const float v = S1[i][j];
-          A[pair_index(bp, bq, i) + (size_t)pair_index(bp, bq, j) * N] = v;
+          A[pair_index<BS>(bp, bq, i) + (size_t)pair_index<BS>(bp, bq, j) * N] = v;
           Qbuf[(size_t)k * kB2 * kB2 + e] = S2[i][j];
           if (last) {
             lt += v * v;
@@ -398,7 +314,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
           const int bp = blk_of_pair(nb, r, b, 0), bq = blk_of_pair(nb, r, b, 1);
           for (int e = tid; e < kB2 * kB2; e += nt) {
             const int i = e % kB2, j = e / kB2;
-            S1[i][j] = A[pair_index(ap, aq, i) + (size_t)pair_index(bp, bq, j) * N];
+            S1[i][j] = A[pair_index<BS>(ap, aq, i) + (size_t)pair_index<BS>(bp, bq, j) * N];
             S2[i][j] = Qbuf[(size_t)a * kB2 * kB2 + e];
             S3[i][j] = Qbuf[(size_t)b * kB2 * kB2 + e];
           }
@@ -418,7 +334,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
             float acc = 0.0f;
 #pragma unroll 8
             for (int t = 0; t < kB2; ++t) acc = fmaf(S4[i][t], S3[t][j], acc);
-            const int gi = pair_index(ap, aq, i), gj = pair_index(bp, bq, j);
+            const int gi = pair_index<BS>(ap, aq, i), gj = pair_index<BS>(bp, bq, j);
             A[gi + (size_t)gj * N] = acc;
             A[gj + (size_t)gi * N] = acc;
             lo += acc * acc;
@@ -434,7 +350,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
           const int ap = blk_of_pair(nb, r, a, 0), aq = blk_of_pair(nb, r, a, 1);
           for (int e = tid; e < kB2 * kB2; e += nt) {
             const int i = e % kB2, j = e / kB2;
-            S1[i][j] = V[(chunk * kB2 + i) + (size_t)pair_index(ap, aq, j) * N];
+            S1[i][j] = V[(chunk * kB2 + i) + (size_t)pair_index<BS>(ap, aq, j) * N];
             S2[i][j] = Qbuf[(size_t)a * kB2 * kB2 + e];
           }
           __syncthreads();
@@ -443,7 +359,7 @@ jacobi_block_kernel(int n, int N, const double* __restrict__ T, float* A, float*
             float acc = 0.0f;
 #pragma unroll 8
             for (int t = 0; t < kB2; ++t) acc = fmaf(S1[i][t], S2[t][j], acc);
-            V[(chunk * kB2 + i) + (size_t)pair_index(ap, aq, j) * N] = acc;
+            V[(chunk * kB2 + i) + (size_t)pair_index<BS>(ap, aq, j) * N] = acc;
           }
           __syncthreads();
         }
@@ -635,26 +551,28 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
 
   if (small) {
     const size_t smem = 2ull * N * N * sizeof(float);
-    BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(jacobi_cta_kernel,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_JACOBI_CTA, (const void*)jacobi_cta_kernel, (int)smem));
     jacobi_cta_kernel<<<1, 1024, smem, s>>>(n, N, T, V, sweeps);
     BLWS_CHECK_LAUNCH(ctx);
   } else {
-    // block-pair Jacobi: Qbuf (P x 32 x 32) reuses A1
-    const int threads = 256;
-    int per_sm = 0;
-    BLWS_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_block_kernel,
-                                                                     threads, 0));
-    if (per_sm < 1) return ctx->fail(BLWS_ECUDA, "jacobi_block_kernel cannot be resident");
+    // block-pair Jacobi: Qbuf (P x 2 kBS x 2 kBS) reuses A1
+    auto kern = jacobi_block_kernel<kBS, kBlockThreads>;
+    const int smem = 4 * (2 * kBS) * (2 * kBS + 1) * (int)sizeof(float);
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_JACOBI_BLOCK, (const void*)kern, smem));
+    if (ctx->jacobi_block_per_sm == 0) {
+      BLWS_TRY_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ctx->jacobi_block_per_sm, kern,
+                                                                       kBlockThreads, smem));
+      if (ctx->jacobi_block_per_sm < 1) return ctx->fail(BLWS_ECUDA, "jacobi_block_kernel cannot be resident");
+    }
+    const int per_sm = ctx->jacobi_block_per_sm;
     const int P = N / kBS / 2;
-    const int items = P * (P - 1) / 2 + (N / kB2) * P;
+    const int items = P * (P - 1) / 2 + (N / (2 * kBS)) * P;
     int grid = std::min(std::max(items, P), ctx->sms * per_sm);
     grid = std::max(std::min(grid, ctx->sms * per_sm), 1);
     float2* fpart = reinterpret_cast<float2*>(part);
     int nn = n, NN = N;
     void* args[] = {&nn, &NN, (void*)&T, &A0, &V, &A1, &fpart, &sweeps};
-    BLWS_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((void*)jacobi_block_kernel, grid, threads, args,
-                                                   0, s));
+    BLWS_TRY_CUDA(ctx, cudaLaunchCooperativeKernel((void*)kern, grid, kBlockThreads, args, smem, s));
     ++ctx->launches;
   }
   const int eb = std::min(ceil_div((long long)n * n, 256), ctx->sms * 4);

@@ -93,8 +93,17 @@ __global__ void splitk_reduce(int M, int N, int splits, double alpha, const doub
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
+    // loads issued 8 at a time (independent), summed in split order
     double acc = 0.0;
-    for (int z = 0; z < splits; ++z) acc += part[(size_t)z * total + e];
+    int z = 0;
+    for (; z + 8 <= splits; z += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(z + u) * total + e];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; z < splits; ++z) acc += part[(size_t)z * total + e];
     const int i = (int)(e % M), j = (int)(e / M);
     double* c = C + i + (size_t)j * ldc;
     *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
@@ -134,12 +143,28 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
   return BLWS_OK;
 }
 
+// The tile shape that wastes the fewest FMAs on padding (the DFMA pipe, not
+// shared-memory traffic, bounds every shape here); ties go to the larger tile.
 template <bool TA, bool TB>
 blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
                    int lda, const double* B, int ldb, double beta, double* C, int ldc) {
-  if (N <= 16) return launch_tiles<TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (N <= 32) return launch_tiles<TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  return launch_tiles<TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  static constexpr int kShapes[4][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}};
+  int best = 0;
+  long long best_work = -1;
+  for (int t = 0; t < 4; ++t) {
+    const long long work = (long long)ceil_div(M, kShapes[t][0]) * kShapes[t][0] *
+                           ((long long)ceil_div(N, kShapes[t][1]) * kShapes[t][1]);
+    if (best_work < 0 || work < best_work) {
+      best = t;
+      best_work = work;
+    }
+  }
+  switch (best) {
+    case 0: return launch_tiles<TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 1: return launch_tiles<TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 2: return launch_tiles<TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    default: return launch_tiles<TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  }
 }
 
 // ------------------------------------------------------------ reductions --
