@@ -48,6 +48,14 @@ typedef int blws_status;
  * the Gram matrix, the eigenproblem of T_k, the count of values above eps)
  * are FP64 in every mode. */
 #define BLWS_PREC_FP64 0      /* all arithmetic FP64 */
+/* Mixed: products with a dense W on the tensor cores from split TF32
+ * operands (hi + lo, three products, FP32 accumulation over at most 256
+ * terms, FP64 sums beyond); the other block products (Gram matrices, block
+ * coefficients, residuals, Ritz lift) and the RPCA reconstruction in FP32
+ * arithmetic with FP64 sums.  Block widths above 256 and sparse operators
+ * keep FP64 products.  rpca_solve returns to FP64 products once its
+ * residual falls below rpca_params.mixed_tol (the refinement tail). */
+#define BLWS_PREC_MIXED 1
 
 typedef struct blws_ctx blws_ctx;
 
@@ -180,6 +188,9 @@ typedef struct {
                       iteration i < trace_len, (residual, count above eps,
                       predicted rank used).  NULL (default): no trace. */
   int trace_len;
+  double mixed_tol; /* BLWS_PREC_MIXED contexts: iterations run with mixed
+                      products while the residual is >= mixed_tol, FP64
+                      after (0: never switch).  Default 1e-5. */
 } rpca_params;
 
 typedef struct {
@@ -189,6 +200,7 @@ typedef struct {
   double residual;  /* ||D - A - E||_F / ||D||_F at exit */
   double norm_two;  /* the estimate of ||D||_2 used for mu0 and Y0 */
   int status;       /* BLWS_OK or BLWS_ENOCONV */
+  int mixed_iters;  /* iterations that ran with mixed products */
 } rpca_info;
 
 blws_status rpca_params_default(rpca_params* p);

@@ -13,6 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libblws.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
+PREC_FP64, PREC_MIXED = 0, 1
 
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
@@ -36,13 +37,13 @@ class RpcaParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("rho", ctypes.c_double), ("mu0", ctypes.c_double), ("mu_bar_ratio", ctypes.c_double),
                 ("sv0", ctypes.c_int), ("trace", ctypes.POINTER(ctypes.c_double)),
-                ("trace_len", ctypes.c_int)]
+                ("trace_len", ctypes.c_int), ("mixed_tol", ctypes.c_double)]
 
 
 class RpcaInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rank", ctypes.c_int), ("nnzE", ctypes.c_int64),
                 ("residual", ctypes.c_double), ("norm_two", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("mixed_iters", ctypes.c_int)]
 
 
 class McParams(ctypes.Structure):
@@ -152,11 +153,12 @@ def apply_noalloc(W, X, P, stream=None):
 class Context:
     """Owns a blws_ctx (workspace, generator state) bound to one device."""
 
-    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0):
+    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0):
         lib = load()
         cfg = BlwsConfig()
         lib.blws_config_default(ctypes.byref(cfg))
         cfg.k, cfg.k_cold, cfg.seed, cfg.device = k, k_cold, seed, device
+        cfg.precision = precision
         h = ctypes.c_void_p()
         st = lib.blws_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:
@@ -237,7 +239,8 @@ class Context:
 
     # ----------------------------------------------------------------- RPCA --
     def rpca_solve(self, D, lam=0.0, tol=1e-7, max_iter=1000, rho=1.5, sv0=10, mu0=0.0,
-                   mu_bar_ratio=1e7, A=None, E=None, stream=None, allow_noconv=False, trace=0):
+                   mu_bar_ratio=1e7, A=None, E=None, stream=None, allow_noconv=False, trace=0,
+                   mixed_tol=1e-5):
         """Robust PCA by inexact ALM with BLWS.  D: column-major (m, n) FP64.
         Returns (A, E, info dict); with trace=T the dict also holds the first T
         iterations' (residual, count above eps, predicted rank)."""
@@ -248,6 +251,7 @@ class Context:
         p = RpcaParams()
         load().rpca_params_default(ctypes.byref(p))
         p.lambda_, p.tol, p.max_iter, p.rho, p.sv0, p.mu0, p.mu_bar_ratio = lam, tol, max_iter, rho, sv0, mu0, mu_bar_ratio
+        p.mixed_tol = mixed_tol
         tr = None
         if trace:
             tr = (ctypes.c_double * (3 * trace))()
@@ -258,7 +262,8 @@ class Context:
         if st != OK and not (st == ENOCONV and allow_noconv):
             self._raise(st, "rpca_solve")
         out = {"iters": info.iters, "rank": info.rank, "nnzE": info.nnzE,
-               "residual": info.residual, "norm_two": info.norm_two, "status": info.status}
+               "residual": info.residual, "norm_two": info.norm_two, "status": info.status,
+               "mixed_iters": info.mixed_iters}
         if tr is not None:
             k = min(trace, info.iters)
             out["trace"] = [(tr[3 * i], int(tr[3 * i + 1]), int(tr[3 * i + 2])) for i in range(k)]

@@ -22,6 +22,7 @@ namespace blws {
 namespace {
 
 constexpr double kDeflTol = 1e-12;
+constexpr double kDeflTolMixed = 1e-6;  // FP32 products resolve columns down to ~1e-6
 
 __global__ void build_start(int m, int n, int w, const double* __restrict__ U0, int ldu0,
                             const double* __restrict__ V0, int ldv0, const double* __restrict__ G,
@@ -85,6 +86,8 @@ __global__ void ritz_values(int r, const double* __restrict__ lam, double eps, d
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
                      double* P, int ldp) {
   const int m = op.m, n = op.n;
+  if (op.W && op.Wr && op.Wc && tc_npad(b) > 0)
+    return tc_dual_apply(ctx, s, *op.Wr, *op.Wc, m, n, X, ldx, b, P, ldp);
   if (op.W) {
     BLWS_TRY(gemm(ctx, s, false, false, m, b, n, 1.0, op.W, op.ldw, X + m, ldx, 0.0, P, ldp));
     BLWS_TRY(gemm(ctx, s, true, false, n, b, m, 1.0, op.W, op.ldw, X, ldx, 0.0, P + m, ldp));
@@ -144,37 +147,40 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
   BLWS_CHECK_LAUNCH(ctx);
   // orthonormalise the start block: deflation scale = its largest column norm
   BLWS_TRY(col_norms(ctx, s, N, b, P, N, lam, scal + SLOT_AUX));
-  BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Q, P2, Bblk, scal + SLOT_AUX, kDeflTol));
+  const bool f32 = a.mixed;
+  const double defl = f32 ? kDeflTolMixed : kDeflTol;
+  BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Q, P2, Bblk, scal + SLOT_AUX, defl, f32));
 
   for (int l = 0; l < k; ++l) {
     double* Xl = Q + (size_t)l * b * N;
     BLWS_TRY(apply_op(ctx, s, op, Xl, N, b, P, N));
     if (l == 0) BLWS_TRY(col_norms(ctx, s, N, b, P, N, lam, scal + SLOT_SCALE));
-    BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, Xl, N, P, N, 0.0, Mtmp, b));
+    BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, Xl, N, P, N, 0.0, Mtmp, b, f32));
     put_sym_block<<<ceil_div((long long)b * b, 256), 256, 0, s>>>(b, Mtmp, T, kb, l * b);
     BLWS_CHECK_LAUNCH(ctx);
     if (l == k - 1) break;
     const double* Ml = T + (size_t)l * b + (size_t)l * b * kb;
-    BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl, N, Ml, kb, 1.0, P, N));
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl, N, Ml, kb, 1.0, P, N, f32));
     if (l > 0) {
       const double* Bt = T + (size_t)(l - 1) * b + (size_t)l * b * kb;  // B_{l-1}^T block
-      BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl - (size_t)b * N, N, Bt, kb, 1.0, P, N));
+      BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl - (size_t)b * N, N, Bt, kb, 1.0, P, N,
+                    f32));
     }
     // second projection against the recurrence's blocks (all blocks when cold)
     const int c0 = a.cold ? 0 : std::max(l - 1, 0);
     const int cols = (l + 1 - c0) * b;
     const double* base = Q + (size_t)c0 * b * N;
-    BLWS_TRY(gemm(ctx, s, true, false, cols, b, N, 1.0, base, N, P, N, 0.0, C, cols));
-    BLWS_TRY(gemm(ctx, s, false, false, N, b, cols, -1.0, base, N, C, cols, 1.0, P, N));
-    BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Xl + (size_t)b * N, P2, Bblk, scal + SLOT_SCALE, kDeflTol));
+    BLWS_TRY(gemm(ctx, s, true, false, cols, b, N, 1.0, base, N, P, N, 0.0, C, cols, f32));
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, cols, -1.0, base, N, C, cols, 1.0, P, N, f32));
+    BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Xl + (size_t)b * N, P2, Bblk, scal + SLOT_SCALE, defl, f32));
     put_offdiag_block<<<ceil_div((long long)b * b, 256), 256, 0, s>>>(b, Bblk, T, kb, (l + 1) * b,
                                                                        l * b);
     BLWS_CHECK_LAUNCH(ctx);
   }
   BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z, a.eps));
   const double r2 = 1.41421356237309504880;
-  BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu));
-  BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv));
+  BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu, f32));
+  BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv, f32));
   ritz_values<<<1, 256, 0, s>>>(a.r, lam, a.eps, sigma, count_dev);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;

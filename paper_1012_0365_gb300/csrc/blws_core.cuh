@@ -18,6 +18,10 @@ struct Operator {
   const int* colptr = nullptr;  // CSC mirror of the pattern
   const int* rowidx = nullptr;
   const int* perm = nullptr;    // CSC entry e is CSR entry perm[e]
+  // mixed precision: TF32 planes of the dense W (row-major Wr: m rows,
+  // column-major Wc: n rows); when set, products with W run on tensor cores
+  const TcPlanes* Wr = nullptr;
+  const TcPlanes* Wc = nullptr;
   // low-rank part
   int rl = 0;
   const double* Ul = nullptr;
@@ -39,6 +43,8 @@ struct BlwsArgs {
   int k = 3;                 // blocks
   bool cold = false;         // full reorthogonalisation (no previous subspace)
   uint32_t draw = 0;         // generator stream of the extra columns (per call)
+  bool mixed = false;        // tall products in FP32 arithmetic (eigen-solver and
+                             // Cholesky factorisations stay FP64)
 };
 
 // P = W~ X: P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m]

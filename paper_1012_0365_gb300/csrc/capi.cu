@@ -76,7 +76,8 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   blws_config c;
   blws_config_default(&c);
   if (cfg) c = *cfg;
-  if (c.k < 1 || c.k_cold < 1 || c.precision != BLWS_PREC_FP64) return BLWS_EINVAL;
+  if (c.k < 1 || c.k_cold < 1 || (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED))
+    return BLWS_EINVAL;
   blws_ctx* ctx = new (std::nothrow) blws_ctx();
   if (!ctx) return BLWS_ENOMEM;
   ctx->cfg = c;
@@ -165,6 +166,24 @@ static blws_status make_operator(blws_ctx* ctx, const blws_op* W, cudaStream_t s
   return BLWS_OK;
 }
 
+// Mixed-precision contexts: TF32 planes of a dense W in both orientations
+// (context workspace), so that products with W run on the tensor cores.
+static blws_status attach_planes(blws_ctx* ctx, cudaStream_t s, blws::Operator* op,
+                                 blws::TcPlanes* Wr, blws::TcPlanes* Wc) {
+  if (ctx->cfg.precision != BLWS_PREC_MIXED || !op->W) return BLWS_OK;
+  const int m = op->m, n = op->n;
+  const int ldr = blws::tc_ld(n), ldc = blws::tc_ld(m);
+  float* wp = nullptr;
+  BLWS_TRY(ctx->get(blws::BUF_TC_W, (size_t)2 * m * ldr + (size_t)2 * n * ldc, &wp));
+  *Wr = blws::TcPlanes{wp, wp + (size_t)m * ldr, m, n, ldr};
+  *Wc = blws::TcPlanes{wp + (size_t)2 * m * ldr, wp + (size_t)2 * m * ldr + (size_t)n * ldc, n, m, ldc};
+  BLWS_TRY(blws::tc_planes_from_rows(ctx, s, op->W, op->ldw, m, n, *Wr));
+  BLWS_TRY(blws::tc_planes_from_cols(ctx, s, op->W, op->ldw, 0, m, n, *Wc));
+  op->Wr = Wr;
+  op->Wc = Wc;
+  return BLWS_OK;
+}
+
 blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx, int b,
                        double* P, int ldp, void* stream) {
   if (!ctx) return BLWS_EINVAL;
@@ -176,6 +195,8 @@ blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx
   blws::Operator op;
   BLWS_TRY(make_operator(ctx, W, s, &op));
   BLWS_TRY(blws::blws_reserve(ctx, W->m, W->n, b, 1));
+  blws::TcPlanes Wr, Wc;
+  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc));
   return blws::apply_op(ctx, s, op, X, ldx, b, P, ldp);
 }
 
@@ -208,6 +229,9 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
   a.g = g;
   a.cold = (w == 0);
   a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
+  blws::TcPlanes Wr, Wc;
+  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc));
+  a.mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
   double* scal;
   BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
   int* cdev = reinterpret_cast<int*>(scal + blws::SLOT_COUNT);
@@ -230,6 +254,7 @@ blws_status rpca_params_default(rpca_params* p) {
   p->sv0 = 10;
   p->trace = nullptr;
   p->trace_len = 0;
+  p->mixed_tol = 1e-5;
   return BLWS_OK;
 }
 
@@ -241,7 +266,8 @@ blws_status rpca_solve(blws_ctx* ctx, const double* D, int m, int n, int ld, con
   rpca_params q;
   rpca_params_default(&q);
   if (p) q = *p;
-  if (!(q.tol > 0) || q.max_iter < 1 || !(q.rho >= 1.0) || q.sv0 < 1 || !(q.mu_bar_ratio >= 1.0))
+  if (!(q.tol > 0) || q.max_iter < 1 || !(q.rho >= 1.0) || q.sv0 < 1 || !(q.mu_bar_ratio >= 1.0) ||
+      !(q.mixed_tol >= 0.0))
     return ctx->fail(BLWS_EINVAL, "rpca_solve: bad parameters");
   BLWS_TRY(bind_device(ctx));
   return blws::rpca_run(ctx, reinterpret_cast<cudaStream_t>(stream), D, m, n, ld, q, A, E, info);

@@ -24,13 +24,14 @@ namespace blws {
 namespace {
 
 constexpr double kPivMin = 1e-10;
+constexpr double kPivMinF32 = 1e-6;
 
 // One CTA: equilibrated Cholesky of G (b x b, ld b) with deflation, then
 // S = D^-1 L^-T (upper, X = R S) and B = L^T D (upper, R = X B).
 // work: 2 b^2 doubles (shared or global).
 __global__ void __launch_bounds__(1024)
 chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict__ scale_ptr,
-                  double tol, double* __restrict__ S, double* __restrict__ Bout,
+                  double tol, double pivmin, double* __restrict__ S, double* __restrict__ Bout,
                   double* gwork, int use_smem) {
   extern __shared__ double smem[];
   double* L = use_smem ? smem : gwork;          // b x b, ld b (lower used)
@@ -70,7 +71,7 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
       bool dj = dead[j] != 0;
       if (!dj) {
         const double rdiag = d[j] * sqrt(p > 0.0 ? p : 0.0);
-        if (!(p > kPivMin) || !(rdiag > thr)) dj = true;
+        if (!(p > pivmin) || !(rdiag > thr)) dj = true;
       }
       dead[j] = dj ? 1 : 0;
       piv_sh = dj ? 1.0 : sqrt(p);
@@ -184,7 +185,7 @@ __device__ inline void tile_of_lin(int lin, int& it, int& jt) {
 
 __global__ void __cluster_dims__(kCC, 1, 1) __launch_bounds__(kCThreads)
 chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restrict__ scale_ptr,
-                    double tol, double* __restrict__ S, double* __restrict__ Bout) {
+                    double tol, double pivmin, double* __restrict__ S, double* __restrict__ Bout) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double smem[];
   const CholLayout lay(b);
@@ -246,7 +247,7 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
           bool dj = dead[j] != 0;
           if (!dj) {
             const double rdiag = d[j] * sqrt(p > 0.0 ? p : 0.0);
-            if (!(p > kPivMin) || !(rdiag > thr)) dj = true;
+            if (!(p > pivmin) || !(rdiag > thr)) dj = true;
           }
           dead[j] = dj ? 1 : 0;
           piv_sh = dj ? 1.0 : sqrt(p);
@@ -359,12 +360,12 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
 }
 
 blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const double* scale,
-                       double tol, double* S, double* B, double* gwork) {
+                       double tol, double pivmin, double* S, double* B, double* gwork) {
   if (b > 1024) return ctx->fail(BLWS_EINVAL, "block width %d exceeds 1024", b);
   if (b <= kCMaxB) {
     const size_t bytes = CholLayout(b).total * sizeof(double);
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL_CLUSTER, (const void*)chol_cluster_kernel, (int)bytes));
-    chol_cluster_kernel<<<kCC, kCThreads, bytes, s>>>(b, G, scale, tol, S, B);
+    chol_cluster_kernel<<<kCC, kCThreads, bytes, s>>>(b, G, scale, tol, pivmin, S, B);
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
   }
@@ -373,7 +374,8 @@ blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const d
   if (use_smem) {
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL, (const void*)chol_equil_kernel, (int)need));
   }
-  chol_equil_kernel<<<1, 1024, use_smem ? need : 0, s>>>(b, G, scale, tol, S, B, gwork, use_smem);
+  chol_equil_kernel<<<1, 1024, use_smem ? need : 0, s>>>(b, G, scale, tol, pivmin, S, B, gwork,
+                                                          use_smem);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
@@ -381,7 +383,7 @@ blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const d
 }  // namespace
 
 blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld, double* X,
-                     double* tmp, double* B, const double* scale, double tol) {
+                     double* tmp, double* B, const double* scale, double tol, bool fp32) {
   // small scratch: G, S, B1, B2, work (2 b^2)
   double* sm = nullptr;
   BLWS_TRY(ctx->get(BUF_SMALL, 6ull * b * b, &sm));
@@ -391,15 +393,17 @@ blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld, 
   double* B2 = B1 + (size_t)b * b;
   double* work = B2 + (size_t)b * b;
   // pass 1
-  BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, R, ld, R, ld, 0.0, G, b));
-  BLWS_TRY(chol_equil(ctx, s, b, G, scale, tol, S, B1, work));
-  BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, R, ld, S, b, 0.0, tmp, ld));
+  BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, R, ld, R, ld, 0.0, G, b, fp32));
+  // with FP32 Gram matrices a pivot is only resolved down to ~1e-6
+  const double pivmin = fp32 ? kPivMinF32 : kPivMin;
+  BLWS_TRY(chol_equil(ctx, s, b, G, scale, tol, pivmin, S, B1, work));
+  BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, R, ld, S, b, 0.0, tmp, ld, fp32));
   // pass 2 (columns are now unit or zero: same deflation rule against 1)
-  BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, tmp, ld, tmp, ld, 0.0, G, b));
+  BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, tmp, ld, tmp, ld, 0.0, G, b, fp32));
   double* one = nullptr;
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &one));
-  BLWS_TRY(chol_equil(ctx, s, b, G, one + SLOT_ONE, 0.5, S, B2, work));
-  BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, tmp, ld, S, b, 0.0, X, ld));
+  BLWS_TRY(chol_equil(ctx, s, b, G, one + SLOT_ONE, 0.5, pivmin, S, B2, work));
+  BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, tmp, ld, S, b, 0.0, X, ld, fp32));
   // B = B2 B1
   BLWS_TRY(gemm(ctx, s, false, false, b, b, b, 1.0, B2, b, B1, b, 0.0, B, b));
   return BLWS_OK;

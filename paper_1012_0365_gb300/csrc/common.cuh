@@ -61,6 +61,9 @@ enum Buf {
   BUF_CSC_PERM,  // MC: CSR position of each CSC entry
   BUF_MC_Y,      // MC: values of the sparse iterate on Omega (CSR order)
   BUF_MC_X,      // MC: low-rank factors of the current X (PROX)
+  BUF_TC_W,      // mixed precision: TF32 planes of W (two orientations, hi and lo)
+  BUF_TC_X,      // mixed precision: TF32 planes of the block X
+  BUF_TC_PART,   // mixed precision: split-K partial sums (FP32)
   BUF_COUNT_
 };
 
@@ -110,6 +113,7 @@ enum Slot {
   SLOT_FLAG = 5,       // int flag (non-finite input seen)
   SLOT_NNZ = 6,        // unsigned long long counter
   SLOT_AUX2 = 7,
+  SLOT_TCERR = 8,      // int: a tensor-core kernel's bounded wait ran out
   SLOT_MAX = 16
 };
 

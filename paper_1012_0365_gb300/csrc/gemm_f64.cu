@@ -18,23 +18,26 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kBK = 16;
 
-template <bool TA, bool TB, int BM, int BN>
+// CT: the arithmetic type of the products and of the in-CTA sums (double,
+// or float in the mixed-precision mode); inputs, outputs and the split-K
+// reduction are FP64 either way.
+template <typename CT, bool TA, bool TB, int BM, int BN>
 __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __restrict__ A,
                 int lda, const double* __restrict__ B, int ldb, double beta, double* C, int ldc,
                 double* __restrict__ part) {
   constexpr int TM = BM / 16, TN = BN / 16;
-  __shared__ double As[kBK][BM + 1];
-  __shared__ double Bs[kBK][BN + 1];
+  __shared__ CT As[kBK][BM + 1];
+  __shared__ CT Bs[kBK][BN + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
-  double acc[TM][TN];
+  CT acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = CT(0);
 
   for (int k0 = kbeg; k0 < kend; k0 += kBK) {
 #pragma unroll 4
@@ -44,7 +47,7 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
       const int gi = m0 + i, gk = k0 + kk;
       double v = 0.0;
       if (gi < M && gk < kend) v = TA ? A[gk + (size_t)gi * lda] : A[gi + (size_t)gk * lda];
-      As[kk][i] = v;
+      As[kk][i] = (CT)v;
     }
 #pragma unroll 4
     for (int e = threadIdx.x; e < kBK * BN; e += kThreads) {
@@ -53,12 +56,12 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
       const int gj = n0 + j, gk = k0 + kk;
       double v = 0.0;
       if (gj < N && gk < kend) v = TB ? B[gj + (size_t)gk * ldb] : B[gk + (size_t)gj * ldb];
-      Bs[kk][j] = v;
+      Bs[kk][j] = (CT)v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < kBK; ++kk) {
-      double a[TM], b[TN];
+      CT a[TM], b[TN];
 #pragma unroll
       for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
 #pragma unroll
@@ -78,11 +81,12 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
     for (int j = 0; j < TN; ++j) {
       const int gj = n0 + ty + 16 * j;
       if (gj >= N) continue;
+      const double av = (double)acc[i][j];
       if (part) {
-        part[(size_t)blockIdx.z * M * N + gi + (size_t)gj * M] = acc[i][j];
+        part[(size_t)blockIdx.z * M * N + gi + (size_t)gj * M] = av;
       } else {
         double* c = C + gi + (size_t)gj * ldc;
-        *c = beta == 0.0 ? alpha * acc[i][j] : fma(alpha, acc[i][j], beta * *c);
+        *c = beta == 0.0 ? alpha * av : fma(alpha, av, beta * *c);
       }
     }
   }
@@ -110,7 +114,11 @@ __global__ void splitk_reduce(int M, int N, int splits, double alpha, const doub
   }
 }
 
-template <bool TA, bool TB, int BM, int BN>
+// FP32 sums inside one CTA cover at most this much of K (the rest is summed
+// in FP64 by the split-K reduction)
+constexpr int kF32MaxChunk = 256;
+
+template <typename CT, bool TA, bool TB, int BM, int BN>
 blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha,
                          const double* A, int lda, const double* B, int ldb, double beta,
                          double* C, int ldc) {
@@ -126,13 +134,14 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
     splits = min(splits, ceil_div(K, 2 * kBK));
     splits = max(splits, 1);
   }
+  if (sizeof(CT) < sizeof(double)) splits = max(splits, ceil_div(K, kF32MaxChunk));
   int kchunk = ceil_div(ceil_div(K, splits), kBK) * kBK;
   splits = ceil_div(K, kchunk);
   double* part = nullptr;
   if (splits > 1) BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)splits * M * N, &part));
   dim3 grid(tm, tn, splits);
-  gemm_f64_kernel<TA, TB, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, alpha, A, lda, B, ldb,
-                                                            beta, C, ldc, part);
+  gemm_f64_kernel<CT, TA, TB, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, alpha, A, lda, B,
+                                                                ldb, beta, C, ldc, part);
   BLWS_CHECK_LAUNCH(ctx);
   if (splits > 1) {
     const size_t total = (size_t)M * N;
@@ -145,7 +154,7 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
 
 // The tile shape that wastes the fewest FMAs on padding (the DFMA pipe, not
 // shared-memory traffic, bounds every shape here); ties go to the larger tile.
-template <bool TA, bool TB>
+template <typename CT, bool TA, bool TB>
 blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
                    int lda, const double* B, int ldb, double beta, double* C, int ldc) {
   static constexpr int kShapes[4][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}};
@@ -160,10 +169,10 @@ blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, 
     }
   }
   switch (best) {
-    case 0: return launch_tiles<TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    case 1: return launch_tiles<TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    case 2: return launch_tiles<TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    default: return launch_tiles<TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    default: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   }
 }
 
@@ -237,7 +246,7 @@ __global__ void scale_kernel(int M, int N, double beta, double* C, int ldc) {
 
 blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
                  const double* A, int lda, const double* B, int ldb, double beta, double* C,
-                 int ldc) {
+                 int ldc, bool fp32) {
   if (M <= 0 || N <= 0) return BLWS_OK;
   if (K <= 0) {  // C = beta C
     const size_t total = (size_t)M * N;
@@ -246,10 +255,16 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
   }
-  if (!ta && !tb) return gemm_t<false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (ta && !tb) return gemm_t<true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (!ta && tb) return gemm_t<false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  return gemm_t<true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (fp32) {
+    if (!ta && !tb) return gemm_t<float, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (ta && !tb) return gemm_t<float, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (!ta && tb) return gemm_t<float, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    return gemm_t<float, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  }
+  if (!ta && !tb) return gemm_t<double, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (ta && !tb) return gemm_t<double, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (!ta && tb) return gemm_t<double, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return gemm_t<double, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
 blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld, double* out) {
@@ -345,7 +360,7 @@ cudaError_t noalloc_gemm(cudaStream_t s, int sms, double* scratch, int M, int N,
   const int splits = noalloc_splits<BM, BN>(sms, M, N, K, &kchunk);
   double* part = splits > 1 ? scratch : nullptr;
   dim3 grid(ceil_div(M, BM), ceil_div(N, BN), splits);
-  gemm_f64_kernel<TA, false, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, 1.0, A, lda, B, ldb,
+  gemm_f64_kernel<double, TA, false, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, 1.0, A, lda, B, ldb,
                                                                0.0, C, ldc, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;

@@ -151,6 +151,7 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
       BlwsArgs a;
       a.eps = tau;
       a.r = sk;
+      a.mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
       a.draw = (uint32_t)(it * 64 + (sk - r_prev));
       if (w == 0) {
         a.cold = true;

@@ -7,10 +7,11 @@ namespace blws {
 
 // C = alpha op(A) op(B) + beta C, op = transpose when ta / tb.  M x N result,
 // inner size K.  beta == 0 never reads C.  Split-K partial sums are reduced
-// in a fixed order (deterministic).
+// in a fixed order (deterministic).  fp32: products and in-CTA sums in FP32
+// (at most 256 terms each), FP64 in and out (mixed-precision mode).
 blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
                  double alpha, const double* A, int lda, const double* B, int ldb,
-                 double beta, double* C, int ldc);
+                 double beta, double* C, int ldc, bool fp32 = false);
 
 // sum of squares of an M x N matrix (ld) into *out (device), deterministic
 blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld, double* out);
@@ -31,7 +32,32 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
 // B (b x b upper, ld b) satisfies R = X B (dead rows zero).  R is destroyed.
 // `scale` (device scalar) and `tol`: a column dies when its diagonal of B is
 // <= tol * scale.  `tmp` is an N x b scratch array (ld).
+// fp32: the four tall products (Gram matrices, X = R S) in FP32 arithmetic;
+// the b x b factorisation stays FP64.
 blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld,
-                     double* X, double* tmp, double* B, const double* scale, double tol);
+                     double* X, double* tmp, double* B, const double* scale, double tol,
+                     bool fp32 = false);
+
+// ------------------------------------------- tensor-core products (tc_gemm)
+// A matrix as two TF32 planes (hi + lo) in FP32 containers, K-major:
+// element (r, k) at r * ld + k, ld = tc_ld(inner) (a multiple of 32).
+struct TcPlanes {
+  float* hi;
+  float* lo;
+  int rows, inner, ld;
+};
+int tc_ld(int inner);
+// padded accumulator width for b columns (0 when b > 256)
+int tc_npad(int b);
+// planes of the column-major rows x inner slab: plane(r, k) = A[row0 + k + r lda]
+blws_status tc_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int lda, int row0, int inner,
+                                int rows, const TcPlanes& out);
+// transposed planes of the m x n column-major A: plane(i, j) = A[i + j lda]
+blws_status tc_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int lda, int m, int n,
+                                const TcPlanes& out);
+// P = [W X_v; W^T X_u] (FP64 out) from W's row-major planes Wr (m rows) and
+// column-major planes Wc (n rows); X is (m+n) x b FP64, b <= 256.
+blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const TcPlanes& Wc, int m,
+                          int n, const double* X, int ldx, int b, double* P, int ldp);
 
 }  // namespace blws

@@ -32,7 +32,9 @@ __device__ inline double shrink(double x, double t) {
 enum EpMode { EP_ITER = 0, EP_FINAL = 1 };
 
 // Rank-c tile reconstruction a = U[i,:] diag(th) V[j,:]^T plus the host update.
-template <int MODE>
+// CT: arithmetic of the rank-c reconstruction (double, or float in the
+// mixed-precision mode); the host update itself is FP64.
+template <int MODE, typename CT>
 __global__ void __launch_bounds__(256)
 rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
               const double* __restrict__ th, const double* __restrict__ V, int ldv,
@@ -40,32 +42,32 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
               const double* __restrict__ Ein, double* __restrict__ Eout, double* __restrict__ Y,
               double* __restrict__ Wout, double* __restrict__ Aout, double mu, double mu_next,
               double lam, double* __restrict__ part) {
-  __shared__ double Us[kEpBK][kEpBM + 1];
-  __shared__ double Vs[kEpBK][kEpBN + 1];
+  __shared__ CT Us[kEpBK][kEpBM + 1];
+  __shared__ CT Vs[kEpBK][kEpBN + 1];
   __shared__ double red[256];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int i0 = blockIdx.x * kEpBM, j0 = blockIdx.y * kEpBN;
   const int c = *count_ptr;
-  double a[4][4];
+  CT a[4][4];
 #pragma unroll
   for (int p = 0; p < 4; ++p)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) a[p][q] = 0.0;
+    for (int q = 0; q < 4; ++q) a[p][q] = CT(0);
   for (int t0 = 0; t0 < c; t0 += kEpBK) {
     for (int e = threadIdx.x; e < kEpBM * kEpBK; e += 256) {
       const int i = e % kEpBM, t = e / kEpBM;
       const int gi = i0 + i, gt = t0 + t;
-      Us[t][i] = (gi < m && gt < c) ? U[gi + (size_t)gt * ldu] * th[gt] : 0.0;
+      Us[t][i] = (CT)((gi < m && gt < c) ? U[gi + (size_t)gt * ldu] * th[gt] : 0.0);
     }
     for (int e = threadIdx.x; e < kEpBN * kEpBK; e += 256) {
       const int j = e % kEpBN, t = e / kEpBN;
       const int gj = j0 + j, gt = t0 + t;
-      Vs[t][j] = (gj < n && gt < c) ? V[gj + (size_t)gt * ldv] : 0.0;
+      Vs[t][j] = (CT)((gj < n && gt < c) ? V[gj + (size_t)gt * ldv] : 0.0);
     }
     __syncthreads();
 #pragma unroll
     for (int t = 0; t < kEpBK; ++t) {
-      double u[4], v[4];
+      CT u[4], v[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) u[p] = Us[t][tx + 16 * p];
 #pragma unroll
@@ -89,14 +91,15 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
       const int gi = i0 + tx + 16 * p;
       if (gi >= m) continue;
       const size_t o = gi + (size_t)gj * ld;
+      const double av = (double)a[p][q];
       if (MODE == EP_FINAL) {
-        Aout[o] = a[p][q];
+        Aout[o] = av;
       } else {
         const double d = D[o];
-        const double z = d - a[p][q] - Ein[o];
+        const double z = d - av - Ein[o];
         const double y = fma(mu, z, Y[o]);
         z2 = fma(z, z, z2);
-        const double e = shrink(fma(y, inv_mu_next, d - a[p][q]), thr);
+        const double e = shrink(fma(y, inv_mu_next, d - av), thr);
         Y[o] = y;
         Eout[o] = e;
         Wout[o] = fma(y, inv_mu_next, d - e);
@@ -276,6 +279,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   info->nnzE = 0;
   info->residual = 0.0;
   info->status = BLWS_OK;
+  info->mixed_iters = 0;
   if (d_norm == 0.0) {  // D = 0: A = E = 0
     BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(A, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
     BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(E, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
@@ -316,6 +320,18 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   Wop.n = n;
   Wop.W = W;
   Wop.ldw = ld;
+  // mixed precision: TF32 planes of W in both orientations, rebuilt from W
+  // each iteration until the residual reaches p.mixed_tol
+  bool mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
+  int mixed_iters = 0;
+  TcPlanes Wr{}, Wc{};
+  if (mixed) {
+    const int ldr = tc_ld(n), ldc = tc_ld(m);
+    float* wp = nullptr;
+    BLWS_TRY(ctx->get(BUF_TC_W, (size_t)2 * m * ldr + (size_t)2 * n * ldc, &wp));
+    Wr = TcPlanes{wp, wp + (size_t)m * ldr, m, n, ldr};
+    Wc = TcPlanes{wp + (size_t)2 * m * ldr, wp + (size_t)2 * m * ldr + (size_t)n * ldc, n, m, ldc};
+  }
   int sv = std::min(std::max(p.sv0, 1), bcap);
   int w = 0;
   int svp = 0;
@@ -340,12 +356,28 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       a.w = w;
       a.k = std::max(1, std::min(k, N / std::max(sv, w)));
     }
+    if (mixed) {
+      BLWS_TRY(tc_planes_from_rows(ctx, s, W, ld, m, n, Wr));
+      BLWS_TRY(tc_planes_from_cols(ctx, s, W, ld, 0, m, n, Wc));
+      Wop.Wr = &Wr;
+      Wop.Wc = &Wc;
+      a.mixed = true;
+      ++mixed_iters;
+    } else {
+      Wop.Wr = Wop.Wc = nullptr;
+    }
     BLWS_TRY(blws_run(ctx, s, Wop, a, Uw, m, Vw, n, sig, count_dev));
     thresholds<<<1, 256, 0, s>>>(sv, sig, eps, th);
     BLWS_CHECK_LAUNCH(ctx);
     const double mu_next = std::min(mu * p.rho, mu_bar);
-    rpca_epilogue<EP_ITER><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D, Ecur,
-                                                 Enext, Y, W, nullptr, mu, mu_next, lam, zpart);
+    if (mixed)
+      rpca_epilogue<EP_ITER, float><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                          Ecur, Enext, Y, W, nullptr, mu, mu_next,
+                                                          lam, zpart);
+    else
+      rpca_epilogue<EP_ITER, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                           Ecur, Enext, Y, W, nullptr, mu, mu_next,
+                                                           lam, zpart);
     BLWS_CHECK_LAUNCH(ctx);
     reduce_sum<<<1, 256, 0, s>>>(nparts, zpart, scal + SLOT_NORM);
     BLWS_CHECK_LAUNCH(ctx);
@@ -356,6 +388,8 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     const double z2 = ctx->host_pinned[SLOT_NORM];
     if (!isfinite(z2)) return ctx->fail(BLWS_ENONFINITE, "rpca_solve: iterate became non-finite");
     res = sqrt(z2) / d_norm;
+    if (*reinterpret_cast<int*>(ctx->host_pinned + SLOT_TCERR))
+      return ctx->fail(BLWS_ETIMEOUT, "rpca_solve: a tensor-core wait ran out");
     if (p.trace && it <= p.trace_len) {
       p.trace[3 * (it - 1) + 0] = res;
       p.trace[3 * (it - 1) + 1] = svp;
@@ -370,12 +404,13 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       converged = true;
       break;
     }
+    if (mixed && res < p.mixed_tol) mixed = false;  // FP64 products from here on
   }
   if (!converged) it = p.max_iter;
   // outputs: A = U diag(th) V^T of the last SVT; E = the E of that iteration
-  rpca_epilogue<EP_FINAL><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, nullptr,
-                                                nullptr, nullptr, nullptr, nullptr, A, 0.0, 1.0,
-                                                0.0, nullptr);
+  rpca_epilogue<EP_FINAL, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev,
+                                                        nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                        A, 0.0, 1.0, 0.0, nullptr);
   BLWS_CHECK_LAUNCH(ctx);
   if (Ecur != E) {
     BLWS_TRY_CUDA(ctx, cudaMemcpy2DAsync(E, sizeof(double) * ld, Ecur, sizeof(double) * ld,
@@ -393,6 +428,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   info->nnzE = (int64_t)*reinterpret_cast<unsigned long long*>(ctx->host_pinned + SLOT_NNZ);
   info->residual = res;
   info->status = converged ? BLWS_OK : BLWS_ENOCONV;
+  info->mixed_iters = mixed_iters;
   return converged ? BLWS_OK : BLWS_ENOCONV;
 }
 

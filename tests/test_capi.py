@@ -45,6 +45,7 @@ def test_defaults(lib):
     p = blws.RpcaParams()
     assert lib.rpca_params_default(ctypes.byref(p)) == 0
     assert p.tol == 1e-7 and p.rho == 1.5 and p.sv0 == 10 and p.mu_bar_ratio == 1e7
+    assert p.mixed_tol == 1e-5
     q = blws.McParams()
     assert lib.mc_params_default(ctypes.byref(q)) == 0
     assert q.variant == 0 and q.tol == 1e-4 and q.incr == 5
@@ -69,8 +70,9 @@ def test_struct_layout_matches_the_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(blws_config), sizeof(blws_op), sizeof(rpca_params),
          sizeof(rpca_info), sizeof(mc_params), sizeof(mc_info));
-  printf("%zu %zu %zu %zu %zu\\n", offsetof(blws_op, val), offsetof(blws_op, Vl),
-         offsetof(rpca_info, nnzE), offsetof(mc_params, xtol), offsetof(rpca_params, trace_len));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(blws_op, val), offsetof(blws_op, Vl),
+         offsetof(rpca_info, nnzE), offsetof(mc_params, xtol), offsetof(rpca_params, trace_len),
+         offsetof(rpca_params, mixed_tol), offsetof(rpca_info, mixed_iters));
   return 0;
 }
 """)
@@ -81,4 +83,5 @@ int main(void) {
     assert sizes == [ctypes.sizeof(t) for t in (blws.BlwsConfig, blws.BlwsOp, blws.RpcaParams,
                                                  blws.RpcaInfo, blws.McParams, blws.McInfo)]
     assert offs == [blws.BlwsOp.val.offset, blws.BlwsOp.Vl.offset, blws.RpcaInfo.nnzE.offset,
-                    blws.McParams.xtol.offset, blws.RpcaParams.trace_len.offset]
+                    blws.McParams.xtol.offset, blws.RpcaParams.trace_len.offset,
+                    blws.RpcaParams.mixed_tol.offset, blws.RpcaInfo.mixed_iters.offset]
