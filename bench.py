@@ -155,6 +155,135 @@ def fullsvd_gpu_sample(torch, Dg, lam, iters_full, sample_iters=2):
                       "GPU, scaled to %d iterations" % (sample_iters, iters_full)}
 
 
+def run_batch(args):
+    """Uneven instances (m, n ~ U{100..1000}, rank 5% of min(m, n), 5-10%
+    corruption) solved by the library's server: all submitted at once, solved
+    concurrently by --workers workers.  Compared with the same instances solved
+    one at a time through one context.  Prints its own JSON line."""
+    import torch
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+    specs = syn.batched_rpca_specs(args.batch_count, seed=0)
+    probs = [syn.rpca_problem(s["m"], s["n"], s["rank"], s["frac"], seed=s["seed"]) for s in specs]
+    Ds = [blws.colmajor(torch.from_numpy(p[0])) for p in probs]
+    prec = blws.PREC_MIXED if args.precision == "mixed" else blws.PREC_FP64
+    srv = blws.Server(workers=args.workers, precision=prec)
+    for t in [srv.submit_rpca(D, tol=args.tol) for D in Ds[:args.workers]]:  # warm the workers up
+        srv.wait(t)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = [srv.submit_rpca(D, tol=args.tol) for D in Ds]
+    outs = [srv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    rel = [float(torch.linalg.norm(A - torch.from_numpy(p[1]).cuda()) / np.linalg.norm(p[1]))
+           for (A, _, _), p in zip(outs, probs)]
+    ok = sum(1 for _, _, i in outs if i["status"] == 0)
+    # one at a time, one context, on a sample of the same instances
+    ctx = blws.Context(k=args.k, precision=prec)
+    sample = min(len(Ds), 32)
+    for D in Ds[:2]:
+        ctx.rpca_solve(D, tol=args.tol)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for D in Ds[:sample]:
+        ctx.rpca_solve(D, tol=args.tol)
+    torch.cuda.synchronize()
+    seq = sample / (time.perf_counter() - t1)
+    lat = np.array([i["queue_ms"] + i["run_ms"] for _, _, i in outs])
+    return {"metric": "rpca_batched_solves_per_s", "value": len(Ds) / wall, "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == 0 else "mixed",
+            "data": "synthetic",
+            "config": {"workload": "rpca_batch_%d_uneven_100_1000" % len(Ds), "workers": args.workers,
+                       "tol": args.tol, "k": args.k},
+            "wall_s": wall, "solved_ok": ok, "relerr_vs_planted": {"median": float(np.median(rel)),
+                                                                   "max": float(np.max(rel))},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "peak_running": st["peak_running"],
+            "sequential": {"value": seq, "unit": "solves/s", "sample": "%d of the instances, one at a "
+                           "time through one context" % sample},
+            "speedup_vs_sequential": (len(Ds) / wall) / seq}
+
+
+def run_serve(args):
+    """Serving: a Poisson stream of mixed RPCA / MC requests (a pool of seeded
+    problems reused round-robin) at offered rates swept around the measured
+    capacity; per rate the achieved solves/s and the p50 / p99 latency
+    (submit to result).  Prints its own JSON line."""
+    import torch
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+    specs = syn.serving_specs(args.pool, seed=1)
+    pool = []
+    for sp in specs:
+        if sp["kind"] == "rpca":
+            D = syn.rpca_problem(sp["m"], sp["n"], sp["rank"], sp["frac"], seed=sp["seed"])[0]
+            pool.append(("rpca", blws.colmajor(torch.from_numpy(D)), sp))
+        else:
+            P = syn.mc_problem(sp["m"], sp["n"], sp["rank"], sp["frac"], seed=sp["seed"])
+            pool.append(("mc", (sp["m"], sp["n"], torch.from_numpy(P["rowptr"]).cuda(),
+                                torch.from_numpy(P["cols"]).cuda(), torch.from_numpy(P["vals"]).cuda()),
+                         sp))
+    prec = blws.PREC_MIXED if args.precision == "mixed" else blws.PREC_FP64
+    srv = blws.Server(workers=args.workers, precision=prec)
+
+    def submit(item):
+        kind, data, sp = item
+        if kind == "rpca":
+            return srv.submit_rpca(data, tol=args.tol)
+        return srv.submit_mc(*data, max_rank=min(sp["rank"] + 40, min(sp["m"], sp["n"])))
+
+    for t in [submit(it) for it in pool]:  # warm-up, and every worker context sized
+        srv.wait(t)
+    t0 = time.perf_counter()
+    outs = [srv.wait(t) for t in [submit(it) for it in pool]]
+    capacity = len(pool) / (time.perf_counter() - t0)
+    rng = np.random.default_rng(2)
+    sweep = []
+    for frac in args.serve_rates:
+        rate = frac * capacity
+        gaps = rng.exponential(1.0 / rate, size=args.serve_requests)
+        arrivals = np.cumsum(gaps)
+        tickets = [None] * len(arrivals)
+        start = time.perf_counter()
+
+        def producer():
+            for i, ta in enumerate(arrivals):
+                delay = start + ta - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[i] = submit(pool[i % len(pool)])
+
+        th = threading.Thread(target=producer)
+        th.start()
+        lat, bad = [], 0
+        for i in range(len(arrivals)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            out = srv.wait(tickets[i])
+            info = out[-1]
+            lat.append(info["queue_ms"] + info["run_ms"])
+            bad += info["status"] != 0
+        th.join()
+        span = time.perf_counter() - start
+        lat = np.array(lat)
+        sweep.append({"offered_per_s": rate, "offered_frac_of_capacity": frac,
+                      "achieved_per_s": len(arrivals) / span, "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "failed": int(bad)})
+    st = srv.stats()
+    srv.close()
+    n_rpca = sum(1 for k, _, _ in pool if k == "rpca")
+    return {"metric": "serving_solves_per_s_and_latency", "value": capacity, "unit": "solves/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == 0 else "mixed",
+            "data": "synthetic",
+            "config": {"workload": "serve_mixed_rpca%d_mc%d" % (n_rpca, len(pool) - n_rpca),
+                       "workers": args.workers, "requests_per_rate": args.serve_requests,
+                       "tol_rpca": args.tol, "tol_mc": 1e-4},
+            "pool": [{"kind": k, "m": sp["m"], "n": sp["n"], "rank": sp["rank"],
+                      "frac": round(sp["frac"], 3)} for k, _, sp in pool],
+            "sweep": sweep, "peak_running": st["peak_running"], "budget_bytes": st["budget"],
+            "peak_in_use_bytes": st["peak_in_use"]}
+
+
 def run_reference(args, ws, rank):
     """--impl reference: the FP64 CPU oracle on the host cores."""
     from paper_1012_0365_gb300 import synthetic as syn
@@ -208,6 +337,15 @@ def main():
                     help="run one untimed solve only (for ncu launch lists)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="run the block product with W~ a few times only (for ncu captures)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+                    help="context precision of --profile-solve / --profile-apply / --batch / --serve")
+    ap.add_argument("--batch", action="store_true", help="uneven batch through the server (own JSON line)")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve", action="store_true", help="Poisson serving sweep (own JSON line)")
+    ap.add_argument("--pool", type=int, default=12)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5])
+    ap.add_argument("--workers", type=int, default=16)
     args = ap.parse_args()
     ws, rank = dist_env()
 
@@ -215,6 +353,11 @@ def main():
         out = run_reference(args, ws, rank)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.batch or args.serve:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_batch(args) if args.batch else run_serve(args)))
         return
 
     import torch
@@ -244,10 +387,12 @@ def main():
         return ctx.rpca_solve(Dg, tol=args.tol, A=A, E=E)
 
     if args.profile_solve or args.profile_apply:
+        if args.precision == "mixed":
+            ctx = blws.Context(k=args.k, device=local_rank, precision=blws.PREC_MIXED)
         if args.profile_solve:
             l0 = ctx.launches
             _, _, info = solve()
-            print(json.dumps({"profile": "solve", "iters": info["iters"],
+            print(json.dumps({"profile": "solve", "precision": args.precision, "iters": info["iters"],
                               "launches": ctx.launches - l0}))
         else:
             b = r + 1

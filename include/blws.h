@@ -28,6 +28,7 @@
 #ifndef BLWS_H
 #define BLWS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -250,6 +251,81 @@ blws_status mc_solve(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr,
                      const mc_params* p, int max_rank,
                      double* U, double* theta, double* V,
                      mc_info* info, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving and batching (no counterpart in the paper: a runtime around the
+ * solvers).  A server owns `workers` host threads, each with its own context
+ * (workspace, generator) and its own CUDA stream, on one device.  Requests
+ * (Robust PCA or matrix completion, device buffers owned by the caller)
+ * queue in arrival order; the head of the queue is admitted when a worker is
+ * free and its estimated device memory (blws_request_bytes) fits in what the
+ * admitted requests leave of the budget (a request larger than the whole
+ * budget runs alone).  Admitted solves run concurrently on their streams, so
+ * requests that arrive while others run overlap with them on the GPU.  Each
+ * solve is the same computation as a direct rpca_solve / mc_solve call with
+ * the server's configuration (fixed reduction orders: the result does not
+ * depend on what else runs).  The caller must keep a request's buffers
+ * alive and untouched until blws_server_wait has returned its result.
+ * ---------------------------------------------------------------------- */
+#define BLWS_REQ_RPCA 0
+#define BLWS_REQ_MC 1
+
+typedef struct blws_server blws_server;
+
+typedef struct {
+  int workers;          /* concurrent solves (host threads / streams), default 8 */
+  size_t hbm_budget;    /* device bytes the admitted solves may hold; 0 (default):
+                           70% of the free device memory at creation */
+  blws_config cfg;      /* configuration of every worker context */
+} blws_server_config;
+
+typedef struct {
+  int kind;             /* BLWS_REQ_RPCA or BLWS_REQ_MC */
+  /* BLWS_REQ_RPCA: rpca_solve arguments */
+  const double* D;
+  int m, n, ld;
+  rpca_params rpca;
+  double* A;
+  double* E;
+  /* BLWS_REQ_MC: mc_solve arguments (m, n above) */
+  int nnz;
+  const int* rowptr;
+  const int* colidx;
+  const double* vals;
+  mc_params mc;
+  int max_rank;
+  double* U;
+  double* theta;
+  double* V;
+} blws_request;
+
+typedef struct {
+  int status;           /* the solver's status (BLWS_OK, BLWS_ENOCONV, ...) */
+  double queue_ms;      /* submit -> admitted */
+  double run_ms;        /* admitted -> finished (device work complete) */
+  rpca_info rpca;       /* filled for BLWS_REQ_RPCA */
+  mc_info mc;           /* filled for BLWS_REQ_MC */
+} blws_result;
+
+typedef struct {
+  uint64_t submitted, completed;
+  size_t budget, in_use, peak_in_use;  /* admission accounting, bytes */
+  int peak_running;                     /* most solves admitted at once */
+} blws_server_stats;
+
+blws_status blws_server_config_default(blws_server_config* cfg);
+/* Start the workers (each creates its context on cfg->cfg.device). */
+blws_status blws_server_create(blws_server** srv, const blws_server_config* cfg);
+/* Estimated device bytes of a request's solve (its admission weight). */
+size_t blws_request_bytes(const blws_request* req, int precision);
+/* Queue a request (copied); *ticket identifies it.  Never blocks on the GPU. */
+blws_status blws_server_submit(blws_server* srv, const blws_request* req, uint64_t* ticket);
+/* Block until the ticket's solve has finished; fills *out.  Each ticket can
+ * be waited for once.  BLWS_EINVAL for an unknown ticket. */
+blws_status blws_server_wait(blws_server* srv, uint64_t ticket, blws_result* out);
+blws_status blws_server_stats_get(blws_server* srv, blws_server_stats* out);
+/* Finish every queued request, stop the workers, free the contexts. */
+blws_status blws_server_destroy(blws_server* srv);
 
 #ifdef __cplusplus
 }

@@ -18,7 +18,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
            "blws_last_error", "blws_launch_count", "blws_apply", "blws_apply_noalloc",
-           "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve")
+           "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
+           "blws_server_config_default", "blws_server_create", "blws_request_bytes",
+           "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -58,6 +60,31 @@ class McInfo(ctypes.Structure):
                 ("norm_two", ctypes.c_double), ("status", ctypes.c_int)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("workers", ctypes.c_int), ("hbm_budget", ctypes.c_size_t), ("cfg", BlwsConfig)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("D", ctypes.c_void_p), ("m", ctypes.c_int), ("n", ctypes.c_int),
+                ("ld", ctypes.c_int), ("rpca", RpcaParams), ("A", ctypes.c_void_p), ("E", ctypes.c_void_p),
+                ("nnz", ctypes.c_int), ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("mc", McParams), ("max_rank", ctypes.c_int),
+                ("U", ctypes.c_void_p), ("theta", ctypes.c_void_p), ("V", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("queue_ms", ctypes.c_double), ("run_ms", ctypes.c_double),
+                ("rpca", RpcaInfo), ("mc", McInfo)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("budget", ctypes.c_size_t), ("in_use", ctypes.c_size_t),
+                ("peak_in_use", ctypes.c_size_t), ("peak_running", ctypes.c_int)]
+
+
+REQ_RPCA, REQ_MC = 0, 1
+
 _lib = None
 
 
@@ -88,10 +115,18 @@ def load():
     lib.mc_solve.argtypes = [vp, ci, ci, ci, vp, vp, vp, ctypes.POINTER(McParams), ci, vp, vp, vp,
                              ctypes.POINTER(McInfo), vp]
     lib.blws_launch_count.argtypes = [vp]
+    lib.blws_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
+    lib.blws_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]
+    lib.blws_request_bytes.argtypes = [ctypes.POINTER(Request), ci]
+    lib.blws_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.blws_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
+    lib.blws_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.blws_server_destroy.argtypes = [vp]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
     lib.blws_launch_count.restype = ctypes.c_uint64
+    lib.blws_request_bytes.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -293,3 +328,93 @@ class Context:
         return U[:, :r], th[:r], V[:, :r], {"iters": info.iters, "rank": r,
                                             "residual": info.residual, "norm_two": info.norm_two,
                                             "status": info.status}
+
+
+class Server:
+    """The library's request server (include/blws.h, "Serving and batching"):
+    `workers` concurrent solves, each on its own context and stream, admitted
+    in arrival order while their estimated device memory fits `hbm_budget`
+    (0: 70% of the free memory).  Tensors handed to submit_* are kept alive
+    here until wait() returns their result."""
+
+    def __init__(self, workers=8, hbm_budget=0, k=3, k_cold=4, seed=0x5EED, device=0, precision=0):
+        lib = load()
+        cfg = ServerConfig()
+        lib.blws_server_config_default(ctypes.byref(cfg))
+        cfg.workers, cfg.hbm_budget = workers, hbm_budget
+        cfg.cfg.k, cfg.cfg.k_cold, cfg.cfg.seed, cfg.cfg.device, cfg.cfg.precision = k, k_cold, seed, device, precision
+        h = ctypes.c_void_p()
+        st = lib.blws_server_create(ctypes.byref(h), ctypes.byref(cfg))
+        if st != OK:
+            raise BlwsError(st, "blws_server_create")
+        self._h = h
+        self._keep = {}
+        self.precision = precision
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().blws_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _submit(self, req, keep):
+        t = ctypes.c_uint64(0)
+        st = load().blws_server_submit(self._h, ctypes.byref(req), ctypes.byref(t))
+        if st != OK:
+            raise BlwsError(st, "blws_server_submit")
+        self._keep[t.value] = keep
+        return t.value
+
+    def submit_rpca(self, D, tol=1e-7, max_iter=1000, sv0=10, lam=0.0, mixed_tol=1e-5):
+        """Queue a Robust PCA solve of the column-major (m, n) FP64 CUDA tensor D."""
+        m, n = D.shape
+        _check_colmajor(D, m, n, "D")
+        A, E = empty_colmajor(m, n), empty_colmajor(m, n)
+        req = Request()
+        req.kind, req.D, req.m, req.n, req.ld = REQ_RPCA, D.data_ptr(), m, n, m
+        load().rpca_params_default(ctypes.byref(req.rpca))
+        req.rpca.tol, req.rpca.max_iter, req.rpca.sv0, req.rpca.lambda_ = tol, max_iter, sv0, lam
+        req.rpca.mixed_tol = mixed_tol
+        req.A, req.E = A.data_ptr(), E.data_ptr()
+        return self._submit(req, ("rpca", D, A, E))
+
+    def submit_mc(self, m, n, rowptr, colidx, vals, max_rank, variant=0, tol=1e-4, max_iter=500):
+        """Queue a matrix completion solve (CSR int32 pattern, FP64 values, CUDA tensors)."""
+        torch = _torch()
+        U, V = empty_colmajor(m, max_rank), empty_colmajor(n, max_rank)
+        th = torch.empty(max_rank, dtype=torch.float64, device="cuda")
+        req = Request()
+        req.kind, req.m, req.n = REQ_MC, m, n
+        req.nnz, req.rowptr, req.colidx, req.vals = int(vals.numel()), rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr()
+        load().mc_params_default(ctypes.byref(req.mc))
+        req.mc.variant, req.mc.tol, req.mc.max_iter = variant, tol, max_iter
+        req.max_rank, req.U, req.theta, req.V = max_rank, U.data_ptr(), th.data_ptr(), V.data_ptr()
+        return self._submit(req, ("mc", rowptr, colidx, vals, U, th, V))
+
+    def wait(self, ticket):
+        """Block until the ticket's solve finished.  RPCA: (A, E, info); MC: (U, theta, V, info)."""
+        res = Result()
+        st = load().blws_server_wait(self._h, ctypes.c_uint64(ticket), ctypes.byref(res))
+        if st != OK:
+            raise BlwsError(st, "blws_server_wait")
+        keep = self._keep.pop(ticket)
+        info = {"status": res.status, "queue_ms": res.queue_ms, "run_ms": res.run_ms}
+        if keep[0] == "rpca":
+            r = res.rpca
+            info.update(iters=r.iters, rank=r.rank, nnzE=r.nnzE, residual=r.residual, mixed_iters=r.mixed_iters)
+            return keep[2], keep[3], info
+        r = res.mc
+        info.update(iters=r.iters, rank=r.rank, residual=r.residual)
+        return keep[4][:, :r.rank], keep[5][:r.rank], keep[6][:, :r.rank], info
+
+    def stats(self):
+        s = ServerStats()
+        load().blws_server_stats_get(self._h, ctypes.byref(s))
+        return {"submitted": s.submitted, "completed": s.completed, "budget": s.budget,
+                "in_use": s.in_use, "peak_in_use": s.peak_in_use, "peak_running": s.peak_running}

@@ -2,6 +2,7 @@
 #include <stdarg.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "mc_kernels.cuh"
@@ -15,6 +16,23 @@ blws_status Ctx::fail(blws_status code, const char* fmt, ...) {
   vsnprintf(last_error, sizeof(last_error), fmt, ap);
   va_end(ap);
   return code;
+}
+
+namespace {
+std::mutex g_attr_mutex;
+constexpr int kAttrDevices = 64;
+int g_attr_bytes[kAttrDevices][Ctx::ATTR_COUNT_] = {};
+}  // namespace
+
+blws_status Ctx::smem_limit(SmemAttr which, const void* func, int bytes) {
+  if (device < 0 || device >= kAttrDevices) return fail(BLWS_ENOTSUP, "device ordinal %d", device);
+  std::lock_guard<std::mutex> lock(g_attr_mutex);
+  if (bytes <= g_attr_bytes[device][which]) return BLWS_OK;
+  const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess)
+    return fail(BLWS_ECUDA, "cudaFuncSetAttribute(%d bytes): %s", bytes, cudaGetErrorString(e));
+  g_attr_bytes[device][which] = bytes;
+  return BLWS_OK;
 }
 
 blws_status Ctx::get(Buf b, size_t bytes, void** out) {

@@ -23,6 +23,18 @@ namespace blws {
 
 namespace {
 
+// 1 / sqrt(p) for a pivot p in (1e-30, 1e30): an FP32 estimate and two
+// Newton-Raphson steps y <- y (3 - p y^2) / 2 in FP64 (each step squares the
+// relative error: ~1e-7 -> 1e-14 -> rounding).  On this GPU an FP64 divide or
+// square root is a long dependent chain of FP64 operations; this is six, and
+// it gives both the pivot sqrt(p) = p y and its reciprocal y.
+__device__ __forceinline__ double rsqrt_newton(double p) {
+  double y = (double)rsqrtf((float)p);
+  y = y * fma(-0.5 * p * y, y, 1.5);
+  y = y * fma(-0.5 * p * y, y, 1.5);
+  return y;
+}
+
 constexpr double kPivMin = 1e-10;
 constexpr double kPivMinF32 = 1e-6;
 
@@ -39,7 +51,7 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
   __shared__ double d[1024 + 1];                // column scales (b <= 1024)
   __shared__ double dinv[1024 + 1];             // 1 / d, then 1 / L_jj
   __shared__ int dead[1024 + 1];
-  __shared__ double piv_sh;
+  __shared__ double piv_sh, rpiv_sh;
   const int tid = threadIdx.x, nt = blockDim.x;
   const double scale = *scale_ptr;
   const double thr = tol * scale;
@@ -68,17 +80,19 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
       double p = L[j + (size_t)j * b];
-      bool dj = dead[j] != 0;
+      bool dj = dead[j] != 0 || !(p > pivmin);
+      double y = 1.0;
       if (!dj) {
-        const double rdiag = d[j] * sqrt(p > 0.0 ? p : 0.0);
-        if (!(p > pivmin) || !(rdiag > thr)) dj = true;
+        y = rsqrt_newton(p);
+        if (!(d[j] * (p * y) > thr)) dj = true;
       }
       dead[j] = dj ? 1 : 0;
-      piv_sh = dj ? 1.0 : sqrt(p);
+      piv_sh = dj ? 1.0 : p * y;
+      rpiv_sh = dj ? 1.0 : y;
     }
     __syncthreads();
     const double lj = piv_sh;
-    const double rlj = 1.0 / lj;  // one FP64 division per column (divisions are slow here)
+    const double rlj = rpiv_sh;
     const bool dj = dead[j] != 0;
     for (int i = j + 1 + tid; i < b; i += nt) {
       double* lij = &L[i + (size_t)j * b];
@@ -199,7 +213,8 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
   double* dinv = smem + lay.off_dinv;
   double* dl = smem + lay.off_dl;     // 1 / L_jj
   int* dead = reinterpret_cast<int*>(smem + lay.off_dead);
-  __shared__ double piv_sh;
+  __shared__ double piv_sh, rpiv_sh;
+  __shared__ double rdg[kCT];  // reciprocals of the diagonal of the step's tile
   const int nt = lay.nt;
   const double thr = tol * (*scale_ptr);
   auto owner = [](int it, int jt) { return (it * (it + 1) / 2 + jt) % kCC; };
@@ -237,34 +252,31 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
   __syncthreads();
 
   for (int jt = 0; jt < nt; ++jt) {
-    // (1) factor the diagonal tile (one warp)
-    if (rank == owner(jt, jt) && warp == 0) {
+    // (1) factor the diagonal tile (the owner's 256 threads, one element each)
+    if (rank == owner(jt, jt)) {
       double* T = slot(jt, jt);
+      const int r = tid % kCT, k = tid / kCT;  // element (r, k) of the tile
       for (int c = 0; c < kCT; ++c) {
         const int j = jt * kCT + c;
-        if (lane == 0) {
+        if (tid == 0) {
           const double p = T[c + kCT * c];
-          bool dj = dead[j] != 0;
+          bool dj = dead[j] != 0 || !(p > pivmin);
+          double y = 1.0;
           if (!dj) {
-            const double rdiag = d[j] * sqrt(p > 0.0 ? p : 0.0);
-            if (!(p > pivmin) || !(rdiag > thr)) dj = true;
+            y = rsqrt_newton(p);
+            if (!(d[j] * (p * y) > thr)) dj = true;
           }
           dead[j] = dj ? 1 : 0;
-          piv_sh = dj ? 1.0 : sqrt(p);
+          piv_sh = dj ? 1.0 : p * y;
+          rpiv_sh = dj ? 1.0 : y;
           T[c + kCT * c] = piv_sh;
         }
-        __syncwarp();
-        const double rl = 1.0 / piv_sh;
+        __syncthreads();
         const bool dj = dead[j] != 0;
-        if (lane > c && lane < kCT) T[lane + kCT * c] = dj ? 0.0 : T[lane + kCT * c] * rl;
-        __syncwarp();
-        if (!dj) {
-          for (int e = lane; e < kCT * kCT; e += 32) {
-            const int r = e % kCT, k = e / kCT;
-            if (k > c && r >= k) T[r + kCT * k] -= T[r + kCT * c] * T[k + kCT * c];
-          }
-        }
-        __syncwarp();
+        if (k == c && r > c) T[r + kCT * c] = dj ? 0.0 : T[r + kCT * c] * rpiv_sh;
+        __syncthreads();
+        if (!dj && k > c && r >= k) T[r + kCT * k] -= T[r + kCT * c] * T[k + kCT * c];
+        __syncthreads();
       }
     }
     cl.sync();  // (2)
@@ -274,7 +286,10 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
       const double* rT = cl.map_shared_rank(slot(jt, jt), o);
       const int* rdead = cl.map_shared_rank(dead, o);
       for (int e = tid; e < 256; e += kCThreads) Ld[e] = rT[e];
-      if (tid < kCT) dead[jt * kCT + tid] = rdead[jt * kCT + tid];
+      if (tid < kCT) {
+        dead[jt * kCT + tid] = rdead[jt * kCT + tid];
+        rdg[tid] = 1.0 / rT[tid + kCT * tid];  // 16 divisions side by side, none in the solve
+      }
     }
     __syncthreads();
     for (int it = jt + 1 + tid / kCT; it < nt; it += kCThreads / kCT) {
@@ -287,7 +302,7 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
         double acc = T[r + kCT * c];
 #pragma unroll
         for (int k = 0; k < c; ++k) acc = fma(-x[k], Ld[c + kCT * k], acc);
-        x[c] = dead[jt * kCT + c] ? 0.0 : acc / Ld[c + kCT * c];
+        x[c] = dead[jt * kCT + c] ? 0.0 : acc * rdg[c];
       }
 #pragma unroll
       for (int c = 0; c < kCT; ++c) T[r + kCT * c] = x[c];

@@ -81,19 +81,13 @@ struct Ctx {
   blws_status fail(blws_status code, const char* fmt, ...);
   // device buffer `b` with at least `bytes` bytes (grown on demand)
   blws_status get(Buf b, size_t bytes, void** out);
-  // dynamic shared memory limit of a kernel, raised only when it grows
-  // (the attribute call is host work that would otherwise sit between launches)
+  // dynamic shared memory limit of a kernel.  The attribute belongs to the
+  // kernel (process-wide, per device), not to a context: it only ever grows,
+  // under a lock, so that contexts on other threads never lower it under a
+  // launch that needs more (defined in capi.cu).
   enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_COUNT_ };
-  int smem_attr[ATTR_COUNT_] = {0};
+  blws_status smem_limit(SmemAttr which, const void* func, int bytes);
   int jacobi_block_per_sm = 0;  // occupancy of the block Jacobi kernel (queried once)
-  blws_status smem_limit(SmemAttr which, const void* func, int bytes) {
-    if (bytes <= smem_attr[which]) return BLWS_OK;
-    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess)
-      return fail(BLWS_ECUDA, "cudaFuncSetAttribute(%d bytes): %s", bytes, cudaGetErrorString(e));
-    smem_attr[which] = bytes;
-    return BLWS_OK;
-  }
   template <typename T>
   blws_status get(Buf b, size_t count, T** out) {
     void* p = nullptr;

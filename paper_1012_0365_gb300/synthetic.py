@@ -79,3 +79,25 @@ def batched_rpca_specs(count, lo=100, hi=1000, seed=0):
 def lam_default(m, n):
     """lambda = 1/sqrt(max(m, n)) (Section 5 uses 1/sqrt(m) for m x m data)."""
     return 1.0 / math.sqrt(max(m, n))
+
+
+def serving_specs(count, seed=0):
+    """A stream of mixed requests: 70% Robust PCA with m, n ~ U{200..4000},
+    30% matrix completion with m, n ~ U{1000..8000} and 5-20% of the entries
+    observed; ranks ~ U{5..100}, an MC rank clamped so that the samples per
+    degree of freedom s / (r (m + n - r)) stay >= 3."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        r = int(rng.integers(5, 101))
+        if rng.uniform() < 0.7:
+            m, n = int(rng.integers(200, 4001)), int(rng.integers(200, 4001))
+            r = min(r, max(1, min(m, n) // 20))
+            out.append({"kind": "rpca", "m": m, "n": n, "rank": r, "frac": 0.1, "seed": seed * 7919 + i})
+        else:
+            m, n = int(rng.integers(1000, 8001)), int(rng.integers(1000, 8001))
+            frac = float(rng.uniform(0.05, 0.20))
+            while r > 1 and frac * m * n < 3 * r * (m + n - r):
+                r -= 1
+            out.append({"kind": "mc", "m": m, "n": n, "rank": r, "frac": frac, "seed": seed * 7919 + i})
+    return out

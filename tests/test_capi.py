@@ -20,7 +20,7 @@ def lib():
 def header_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(?:blws_status|const char\*|uint64_t)\s+(\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(?:blws_status|const char\*|uint64_t|size_t)\s+(\w+)\s*\(", text)))
 
 
 def test_header_declares_the_binding_exports():
@@ -57,6 +57,32 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert lib.blws_svt(None, None, 1.0, 1, None, None, 0, None, 0, None, None, None, None, None) == blws.EINVAL
     assert lib.rpca_solve(None, None, 1, 1, 1, None, None, None, None, None) == blws.EINVAL
     assert lib.blws_destroy(None) == 0
+    assert lib.blws_server_config_default(None) == blws.EINVAL
+    assert lib.blws_server_create(None, None) == blws.EINVAL
+    assert lib.blws_server_submit(None, None, None) == blws.EINVAL
+    assert lib.blws_server_wait(None, 1, None) == blws.EINVAL
+    assert lib.blws_server_stats_get(None, None) == blws.EINVAL
+    assert lib.blws_server_destroy(None) == 0
+    assert lib.blws_request_bytes(None, 0) == 0
+    cfg = blws.ServerConfig()
+    assert lib.blws_server_config_default(ctypes.byref(cfg)) == 0
+    assert cfg.workers == 8 and cfg.hbm_budget == 0 and cfg.cfg.k == 3
+
+
+def test_request_bytes_grow_with_the_problem(lib):
+    # the admission weight: RPCA holds Y, W and a second E (3 m n doubles) plus
+    # the Lanczos blocks; mixed precision adds the TF32 planes (16 m n bytes)
+    req = blws.Request()
+    req.kind, req.m, req.n, req.ld = blws.REQ_RPCA, 1000, 800, 1000
+    lib.rpca_params_default(ctypes.byref(req.rpca))
+    b64 = lib.blws_request_bytes(ctypes.byref(req), 0)
+    bmx = lib.blws_request_bytes(ctypes.byref(req), 1)
+    assert b64 >= 3 * 1000 * 800 * 8 and bmx - b64 >= 16 * 1000 * 800
+    req.m, req.ld = 2000, 2000
+    assert lib.blws_request_bytes(ctypes.byref(req), 0) > b64
+    mc = blws.Request()
+    mc.kind, mc.m, mc.n, mc.nnz, mc.max_rank = blws.REQ_MC, 1000, 1000, 100000, 50
+    assert lib.blws_request_bytes(ctypes.byref(mc), 0) >= 100000 * 24
 
 
 def test_struct_layout_matches_the_header(tmp_path):
@@ -68,20 +94,28 @@ def test_struct_layout_matches_the_header(tmp_path):
 #include <stdio.h>
 #include "blws.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(blws_config), sizeof(blws_op), sizeof(rpca_params),
-         sizeof(rpca_info), sizeof(mc_params), sizeof(mc_info));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(blws_config), sizeof(blws_op),
+         sizeof(rpca_params), sizeof(rpca_info), sizeof(mc_params), sizeof(mc_info),
+         sizeof(blws_server_config), sizeof(blws_request), sizeof(blws_result),
+         sizeof(blws_server_stats));
   printf("%zu %zu %zu %zu %zu %zu %zu\\n", offsetof(blws_op, val), offsetof(blws_op, Vl),
          offsetof(rpca_info, nnzE), offsetof(mc_params, xtol), offsetof(rpca_params, trace_len),
          offsetof(rpca_params, mixed_tol), offsetof(rpca_info, mixed_iters));
+  printf("%zu %zu %zu %zu\\n", offsetof(blws_request, mc), offsetof(blws_request, V),
+         offsetof(blws_result, mc), offsetof(blws_server_stats, peak_running));
   return 0;
 }
 """)
     exe = tmp_path / "probe"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
-    sizes, offs = [list(map(int, line.split())) for line in
-                   subprocess.check_output([str(exe)]).decode().split("\n")[:2]]
+    sizes, offs, offs2 = [list(map(int, line.split())) for line in
+                          subprocess.check_output([str(exe)]).decode().split("\n")[:3]]
     assert sizes == [ctypes.sizeof(t) for t in (blws.BlwsConfig, blws.BlwsOp, blws.RpcaParams,
-                                                 blws.RpcaInfo, blws.McParams, blws.McInfo)]
+                                                 blws.RpcaInfo, blws.McParams, blws.McInfo,
+                                                 blws.ServerConfig, blws.Request, blws.Result,
+                                                 blws.ServerStats)]
     assert offs == [blws.BlwsOp.val.offset, blws.BlwsOp.Vl.offset, blws.RpcaInfo.nnzE.offset,
                     blws.McParams.xtol.offset, blws.RpcaParams.trace_len.offset,
                     blws.RpcaParams.mixed_tol.offset, blws.RpcaInfo.mixed_iters.offset]
+    assert offs2 == [blws.Request.mc.offset, blws.Request.V.offset, blws.Result.mc.offset,
+                     blws.ServerStats.peak_running.offset]

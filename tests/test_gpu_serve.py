@@ -1,0 +1,149 @@
+"""GPU checks of the request server (include/blws.h, "Serving and batching").
+
+* Each result is the same alone and in the mix: a request solved by a
+  one-worker server with nothing else queued, and the same request solved
+  while seven other workers run other solves, give bit-identical outputs
+  (every reduction has a fixed order; no floating-point atomics).
+* Results in the mix still match the FP64 oracle (config 1 and a ragged
+  case) within the parity bar of the direct solver.
+* Admission keeps the admitted requests' estimated bytes within the budget
+  (a request larger than the whole budget runs alone).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_0365_gb300 import synthetic as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch
+
+
+def rpca_inputs(torch):
+    from paper_1012_0365_gb300 import blws
+    specs = [(200, 200, 10, 0.05, 0), (61, 47, 3, 0.05, 1), (400, 40, 2, 0.10, 3),
+             (300, 500, 8, 0.08, 4), (130, 250, 12, 0.08, 5)]
+    out = []
+    for m, n, r, f, seed in specs:
+        D, _, _ = syn.rpca_problem(m, n, r, f, amp=50.0, seed=seed)
+        out.append((D, blws.colmajor(torch.from_numpy(D))))
+    return out
+
+
+def mc_inputs(torch):
+    out = []
+    for m, n, r, seed in [(300, 300, 10, 0), (257, 190, 5, 1)]:
+        s = 6 * r * (m + n - r)
+        P = syn.mc_problem(m, n, r, s / (m * n), seed=seed)
+        out.append((m, n, torch.from_numpy(P["rowptr"]).cuda(), torch.from_numpy(P["cols"]).cuda(),
+                    torch.from_numpy(P["vals"]).cuda()))
+    return out
+
+
+def test_same_result_alone_and_in_the_mix(torch_mod):
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    rp = rpca_inputs(torch)
+    mc = mc_inputs(torch)
+    # alone: one worker, one request at a time
+    alone = blws.Server(workers=1)
+    ref_r = []
+    for _, Dt in rp:
+        A, E, info = alone.wait(alone.submit_rpca(Dt, tol=1e-9))
+        ref_r.append((A.clone(), E.clone(), info))
+    ref_m = []
+    for args in mc:
+        U, th, V, info = alone.wait(alone.submit_mc(*args, max_rank=60))
+        ref_m.append(((U * th) @ V.t(), info))
+    alone.close()
+    # in the mix: eight workers, everything queued at once, twice over
+    mix = blws.Server(workers=8)
+    tickets = []
+    for rep in range(2):
+        for _, Dt in rp:
+            tickets.append(("r", mix.submit_rpca(Dt, tol=1e-9)))
+        for args in mc:
+            tickets.append(("m", mix.submit_mc(*args, max_rank=60)))
+    res = [mix.wait(t) for _, t in tickets]
+    st = mix.stats()
+    mix.close()
+    assert st["completed"] == len(tickets) and st["peak_running"] > 1
+    per = len(rp) + len(mc)
+    for rep in range(2):
+        for i in range(len(rp)):
+            A, E, info = res[rep * per + i]
+            assert info["status"] == 0
+            assert torch.equal(A, ref_r[i][0]) and torch.equal(E, ref_r[i][1])
+            assert info["iters"] == ref_r[i][2]["iters"]
+        for j in range(len(mc)):
+            U, th, V, info = res[rep * per + len(rp) + j]
+            assert info["status"] == 0
+            assert torch.equal((U * th) @ V.t(), ref_m[j][0])
+
+
+def test_results_in_the_mix_match_the_oracle(torch_mod):
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    rp = rpca_inputs(torch)[:2]
+    srv = blws.Server(workers=4)
+    tickets = [srv.submit_rpca(Dt, tol=1e-10) for _, Dt in rp]
+    for (D, _), t in zip(rp, tickets):
+        A, E, info = srv.wait(t)
+        ref = oracle.rpca_ialm_full(D, tol=1e-10)
+        A = A.cpu().numpy()
+        assert info["status"] == 0
+        assert np.linalg.norm(A - ref["A"]) / np.linalg.norm(ref["A"]) < 1e-6
+    srv.close()
+
+
+def test_admission_respects_the_budget(torch_mod):
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    D, _, _ = syn.rpca_problem(300, 300, 5, 0.05, seed=7)
+    Dt = blws.colmajor(torch.from_numpy(D))
+    req = blws.Request()
+    req.kind, req.m, req.n, req.ld = blws.REQ_RPCA, 300, 300, 300
+    blws.load().rpca_params_default(__import__("ctypes").byref(req.rpca))
+    one = blws.load().blws_request_bytes(__import__("ctypes").byref(req), 0)
+    # room for one request at a time: never two admitted together
+    srv = blws.Server(workers=4, hbm_budget=int(one * 1.5))
+    ts = [srv.submit_rpca(Dt) for _ in range(6)]
+    infos = [srv.wait(t)[2] for t in ts]
+    st = srv.stats()
+    srv.close()
+    assert all(i["status"] == 0 for i in infos)
+    assert st["peak_running"] == 1 and st["peak_in_use"] <= st["budget"]
+    # a budget below one request: it still runs, alone
+    srv = blws.Server(workers=4, hbm_budget=one // 2)
+    ts = [srv.submit_rpca(Dt) for _ in range(3)]
+    assert all(srv.wait(t)[2]["status"] == 0 for t in ts)
+    assert srv.stats()["peak_running"] == 1
+    srv.close()
+    # room for four: they overlap
+    srv = blws.Server(workers=4, hbm_budget=one * 4)
+    ts = [srv.submit_rpca(Dt) for _ in range(8)]
+    assert all(srv.wait(t)[2]["status"] == 0 for t in ts)
+    st = srv.stats()
+    assert 1 < st["peak_running"] <= 4 and st["peak_in_use"] <= st["budget"]
+    srv.close()
+
+
+def test_wait_twice_is_rejected(torch_mod):
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    D, _, _ = syn.rpca_problem(40, 30, 2, 0.05, seed=2)
+    srv = blws.Server(workers=2)
+    t = srv.submit_rpca(blws.colmajor(torch.from_numpy(D)))
+    srv.wait(t)
+    with pytest.raises(blws.BlwsError):
+        srv.wait(t)
+    srv.close()
