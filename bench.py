@@ -34,6 +34,9 @@ WORKLOADS = {
 }
 DEFAULT = "rpca_2000x2000_r100"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9  # SMs x DFMA/clk x flops x max clock
+# DRAM bytes of one product with the augmented matrix (both gemm_f64 launches), from the
+# ncu capture in profiles/gemm_f64_dual_apply_2000x2000_b101.md (b = 101)
+APPLY_TRAFFIC = {"rpca_2000x2000_r100": 2 * 33.63e6}
 
 
 def dist_env():
@@ -230,7 +233,9 @@ def run_serve(args):
         kind, data, sp = item
         if kind == "rpca":
             return srv.submit_rpca(data, tol=args.tol)
-        return srv.submit_mc(*data, max_rank=min(sp["rank"] + 40, min(sp["m"], sp["n"])))
+        # output capacity: SVT's early iterates can hold many more values above tau than
+        # the final rank when the sampling is thin (s / d_r near 3)
+        return srv.submit_mc(*data, max_rank=min(max(4 * sp["rank"], sp["rank"] + 100), min(sp["m"], sp["n"])))
 
     for t in [submit(it) for it in pool]:  # warm-up, and every worker context sized
         srv.wait(t)
@@ -255,7 +260,7 @@ def run_serve(args):
 
         th = threading.Thread(target=producer)
         th.start()
-        lat, bad = [], 0
+        lat, bad, statuses = [], 0, {}
         for i in range(len(arrivals)):
             while tickets[i] is None:
                 time.sleep(0.0005)
@@ -263,12 +268,15 @@ def run_serve(args):
             info = out[-1]
             lat.append(info["queue_ms"] + info["run_ms"])
             bad += info["status"] != 0
+            if info["status"] != 0:
+                statuses[str(info["status"])] = statuses.get(str(info["status"]), 0) + 1
         th.join()
         span = time.perf_counter() - start
         lat = np.array(lat)
         sweep.append({"offered_per_s": rate, "offered_frac_of_capacity": frac,
                       "achieved_per_s": len(arrivals) / span, "p50_ms": float(np.percentile(lat, 50)),
-                      "p99_ms": float(np.percentile(lat, 99)), "failed": int(bad)})
+                      "p99_ms": float(np.percentile(lat, 99)), "failed": int(bad),
+                      "failed_statuses": statuses})
     st = srv.stats()
     srv.close()
     n_rpca = sum(1 for k, _, _ in pool if k == "rpca")
@@ -538,7 +546,10 @@ def main():
         "roofline": {"kernel": "gemm_f64 (block product with the augmented matrix, b=%d)" % b,
                      "bound": "alu", "achieved": achieved * 1e3, "peak": FP64_PEAK_GFLOPS,
                      "unit": "GFLOP/s", "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
-                     "traffic": None, "peak_source": "FP64 152 SMs x 2 DFMA/clk x 2.07 GHz"},
+                     "traffic": APPLY_TRAFFIC.get(args.workload) if b == 101 else None,
+                     "algorithmic_bytes": 2.0 * m * n * 8,
+                     "peak_source": "FP64 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts "
+                                    "and the maximum SM clock; MEASURED_PEAKS.json has no FP64 figure)"},
         "clocks": clocks,
         "wall_s": t_wall,
     }
