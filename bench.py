@@ -33,6 +33,11 @@ WORKLOADS = {
     "rpca_200x200_r10": (200, 200, 10, 0.05),
 }
 DEFAULT = "rpca_2000x2000_r100"
+PRECISIONS = {"fp64": 0, "mixed": 1, "fp64tc": 2}
+MC_WORKLOADS = {
+    # name: (m, n, rank, observed fraction)
+    "mc_5000x5000_r50": (5000, 5000, 50, 0.10),
+}
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9  # SMs x DFMA/clk x flops x max clock
 # DRAM bytes of one product with the augmented matrix (both gemm_f64 launches), from the
 # ncu capture in profiles/gemm_f64_dual_apply_2000x2000_b101.md (b = 101)
@@ -158,6 +163,77 @@ def fullsvd_gpu_sample(torch, Dg, lam, iters_full, sample_iters=2):
                       "GPU, scaled to %d iterations" % (sample_iters, iters_full)}
 
 
+def run_mc(args):
+    """Matrix completion, m = n = 5000, rank 50, 10% observed (2.5M entries, CSR int32):
+    SVT of [Cai08] with every SVT by BLWS over the CSR operator, to tol 1e-4.  Prints its
+    own JSON line (metric mc_solves_per_s)."""
+    import torch
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+    m, n, r, frac = MC_WORKLOADS[args.workload]
+    P = syn.mc_problem(m, n, r, frac, seed=0)
+    rowptr = torch.from_numpy(P["rowptr"]).cuda()
+    cols = torch.from_numpy(P["cols"]).cuda()
+    vals = torch.from_numpy(P["vals"]).cuda()
+    prec = PRECISIONS[args.precision]
+    ctx = blws.Context(k=args.k, precision=prec)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    max_rank = 4 * r
+    for _ in range(args.warmup):
+        U, th, V, info = ctx.mc_solve(m, n, rowptr, cols, vals, max_rank=max_rank)
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        U, th, V, info = ctx.mc_solve(m, n, rowptr, cols, vals, max_rank=max_rank)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # relerr of the factored X against the planted M = ML MR^T, from the factors
+    Un, thn, Vn = U.cpu().numpy(), th.cpu().numpy(), V.cpu().numpy()
+    ML, MR = P["ML"], P["MR"]
+    xx = float(np.sum(thn ** 2))
+    mm = float(np.trace((ML.T @ ML) @ (MR.T @ MR)))
+    xm = float(np.trace((thn[:, None] * (Un.T @ ML)) @ (MR.T @ Vn)))
+    rel = math.sqrt(max(xx + mm - 2 * xm, 0.0) / mm)
+    # the sparse product [S X_v; S^T X_u] at b = rank + 1, with the CSC mirror built once
+    b = r + 1
+    mirror = ctx.csc_mirror(m, n, rowptr, cols)
+    X = blws.colmajor(torch.randn(m + n, b, dtype=torch.float64, device="cuda"))
+    Pm = blws.empty_colmajor(m + n, b)
+    for _ in range(2):
+        ctx.apply_sparse(m, n, rowptr, cols, vals, X, P=Pm, mirror=mirror)
+    reps = 10
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.apply_sparse(m, n, rowptr, cols, vals, X, P=Pm, mirror=mirror)
+    e1.record(stream)
+    e1.synchronize()
+    spmm_ms = e0.elapsed_time(e1) / reps
+    nnz = int(vals.numel())
+    flops = 4.0 * nnz * b
+    achieved = flops / (spmm_ms / 1e3) / 1e9
+    lat = np.array(ms)
+    return {"metric": "mc_solves_per_s", "value": args.steps / (float(np.sum(ms)) / 1e3), "unit": "solves/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
+            "higher_is_better": True, "dtype": ["f64", "mixed", "f64 (tensor-core digits)"][prec], "data": "synthetic",
+            "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "observed": frac, "nnz": nnz,
+                       "tol": 1e-4, "k": args.k, "l2": "flushed between steps (512 MB write)"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "solve": {"iters": info["iters"], "rank": info["rank"], "residual": info["residual"],
+                      "relerr_vs_planted": rel},
+            "roofline": {"kernel": "spmm_rows (S X_v and S^T X_u, b=%d)" % b, "bound": "alu",
+                         "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "ms_per_product": spmm_ms,
+                         "note": "blws_apply on the sparse operator with a prebuilt CSC mirror (includes "
+                                 "the row-major copy of X)"}}
+
+
 def run_batch(args):
     """Uneven instances (m, n ~ U{100..1000}, rank 5% of min(m, n), 5-10%
     corruption) solved by the library's server: all submitted at once, solved
@@ -168,7 +244,7 @@ def run_batch(args):
     specs = syn.batched_rpca_specs(args.batch_count, seed=0)
     probs = [syn.rpca_problem(s["m"], s["n"], s["rank"], s["frac"], seed=s["seed"]) for s in specs]
     Ds = [blws.colmajor(torch.from_numpy(p[0])) for p in probs]
-    prec = blws.PREC_MIXED if args.precision == "mixed" else blws.PREC_FP64
+    prec = PRECISIONS[args.precision]
     srv = blws.Server(workers=args.workers, precision=prec)
     for t in [srv.submit_rpca(D, tol=args.tol) for D in Ds[:args.workers]]:  # warm the workers up
         srv.wait(t)
@@ -195,7 +271,7 @@ def run_batch(args):
     seq = sample / (time.perf_counter() - t1)
     lat = np.array([i["queue_ms"] + i["run_ms"] for _, _, i in outs])
     return {"metric": "rpca_batched_solves_per_s", "value": len(Ds) / wall, "unit": "solves/s",
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == 0 else "mixed",
+            "n_gpus": 1, "higher_is_better": True, "dtype": ["f64", "mixed", "f64 (tensor-core digits)"][prec],
             "data": "synthetic",
             "config": {"workload": "rpca_batch_%d_uneven_100_1000" % len(Ds), "workers": args.workers,
                        "tol": args.tol, "k": args.k},
@@ -226,7 +302,7 @@ def run_serve(args):
             pool.append(("mc", (sp["m"], sp["n"], torch.from_numpy(P["rowptr"]).cuda(),
                                 torch.from_numpy(P["cols"]).cuda(), torch.from_numpy(P["vals"]).cuda()),
                          sp))
-    prec = blws.PREC_MIXED if args.precision == "mixed" else blws.PREC_FP64
+    prec = PRECISIONS[args.precision]
     srv = blws.Server(workers=args.workers, precision=prec)
 
     def submit(item):
@@ -281,7 +357,7 @@ def run_serve(args):
     srv.close()
     n_rpca = sum(1 for k, _, _ in pool if k == "rpca")
     return {"metric": "serving_solves_per_s_and_latency", "value": capacity, "unit": "solves/s",
-            "n_gpus": 1, "higher_is_better": True, "dtype": "f64" if prec == 0 else "mixed",
+            "n_gpus": 1, "higher_is_better": True, "dtype": ["f64", "mixed", "f64 (tensor-core digits)"][prec],
             "data": "synthetic",
             "config": {"workload": "serve_mixed_rpca%d_mc%d" % (n_rpca, len(pool) - n_rpca),
                        "workers": args.workers, "requests_per_rate": args.serve_requests,
@@ -298,6 +374,8 @@ def run_reference(args, ws, rank):
     import oracle
     if rank != 0:
         return None
+    if args.workload not in WORKLOADS:
+        return {"impl": "reference", "unavailable": "the CPU reference arm is defined on the RPCA workloads"}
     m, n, r, f = WORKLOADS[args.workload]
     D, L0, _ = syn.rpca_problem(m, n, r, f, seed=0)
     # one full solve's iteration count is fixed by the workload (the GPU path
@@ -333,7 +411,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="blws", choices=["blws", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(MC_WORKLOADS))
     ap.add_argument("--tol", type=float, default=1e-7)
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -345,7 +423,7 @@ def main():
                     help="run one untimed solve only (for ncu launch lists)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="run the block product with W~ a few times only (for ncu captures)")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64tc"],
                     help="context precision of --profile-solve / --profile-apply / --batch / --serve")
     ap.add_argument("--batch", action="store_true", help="uneven batch through the server (own JSON line)")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -361,6 +439,11 @@ def main():
         out = run_reference(args, ws, rank)
         if out is not None:
             print(json.dumps(out))
+        return
+    if args.workload in MC_WORKLOADS and args.impl != "reference":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(run_mc(args)))
         return
     if args.batch or args.serve:
         import torch
@@ -395,8 +478,8 @@ def main():
         return ctx.rpca_solve(Dg, tol=args.tol, A=A, E=E)
 
     if args.profile_solve or args.profile_apply:
-        if args.precision == "mixed":
-            ctx = blws.Context(k=args.k, device=local_rank, precision=blws.PREC_MIXED)
+        if args.precision != "fp64":
+            ctx = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[args.precision])
         if args.profile_solve:
             l0 = ctx.launches
             _, _, info = solve()
@@ -508,6 +591,31 @@ def main():
                  "iters": minfo["iters"], "mixed_iters": minfo["mixed_iters"],
                  "residual": minfo["residual"], "relerr_vs_planted": mrel}
 
+    # ---- FP64-equivalent products on the tensor cores (BF16 digit planes) ----
+    fp64tc = None
+    if not args.no_mixed:
+        ctxt = blws.Context(k=args.k, device=local_rank, precision=blws.PREC_FP64_TC)
+        for _ in range(args.warmup):
+            ctxt.rpca_solve(Dg, tol=args.tol, A=A, E=E)
+        tc_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            _, _, tinfo = ctxt.rpca_solve(Dg, tol=args.tol, A=A, E=E)
+            ev1.record(stream)
+            ev1.synchronize()
+            tc_ms.append(ev0.elapsed_time(ev1))
+        trel = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
+        fp64tc = {"value": ws * args.steps / (float(np.sum(tc_ms)) / 1e3), "unit": "solves/s",
+                  "ms_per_step": float(np.mean(tc_ms)),
+                  "latency_ms": {"p50": float(np.percentile(tc_ms, 50)),
+                                 "p99": float(np.percentile(tc_ms, 99))},
+                  "dtype": "products with W from 7 BF16 digit planes per operand on tcgen05 (exact "
+                           "FP32 sums, ~1e-14 relative); everything else f64",
+                  "iters": tinfo["iters"], "residual": tinfo["residual"], "relerr_vs_planted": trel}
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -557,6 +665,8 @@ def main():
         out["cpu_baseline"] = cpu
     if mixed:
         out["mixed_precision"] = mixed
+    if fp64tc:
+        out["fp64_tensor_core"] = fp64tc
     if fullsvd:
         out["fullsvd_same_gpu"] = fullsvd
         out["fullsvd_same_gpu"]["blws_speedup"] = value / fullsvd["value"]

@@ -57,6 +57,14 @@ typedef int blws_status;
  * keep FP64 products.  rpca_solve returns to FP64 products once its
  * residual falls below rpca_params.mixed_tol (the refinement tail). */
 #define BLWS_PREC_MIXED 1
+/* FP64-equivalent products on the tensor cores (dense W only): every row of W
+ * and every column of X is written as 7 balanced base-128 digits under one
+ * power-of-two scale (exact in BF16); the 28 digit products with the leading
+ * weights are formed by tensor cores with exact FP32 sums (256 terms at a
+ * time) and combined in double-FP32 / FP64.  Error ~2^-47 of the leading
+ * term per product term, against the DFMA GEMM's ~2^-53.  Everything else
+ * is FP64, as in BLWS_PREC_FP64. */
+#define BLWS_PREC_FP64_TC 2
 
 typedef struct blws_ctx blws_ctx;
 
@@ -92,7 +100,10 @@ const char* blws_last_error(const blws_ctx* ctx);
  *   sparse: W == NULL, CSR (rowptr[m+1], colidx[nnz], val[nnz]) plus an
  *           optional low-rank term Ul diag(sl) Vl^T (rl columns, Ul m x rl
  *           with ld m, Vl n x rl with ld n; rl = 0 means none).  This is the
- *           "sparse residual plus low-rank" input of matrix completion. */
+ *           "sparse residual plus low-rank" input of matrix completion.
+ *           W^T X needs the pattern by columns: colptr/rowidx/perm may give
+ *           a mirror built by blws_csc_mirror for this pattern (reused across
+ *           calls); NULL (default) builds one in the context at each call. */
 typedef struct {
   int m, n;
   const double* W;
@@ -105,7 +116,19 @@ typedef struct {
   const double* Ul;
   const double* sl;
   const double* Vl;
+  const int* colptr;   /* optional CSC mirror: n + 1 column pointers */
+  const int* rowidx;   /* nnz row indices, rows increasing within a column */
+  const int* perm;     /* nnz: CSC entry e is CSR entry perm[e] */
 } blws_op;
+
+/* The column-major mirror of a CSR pattern (m x n, nnz entries): colptr
+ * (n + 1), rowidx (nnz) and perm (nnz), caller-owned device arrays, written
+ * on `stream`; within each column the rows increase (deterministic).  For
+ * callers that apply the same sparse operator many times (blws_op.colptr).
+ * Does not synchronise. */
+blws_status blws_csc_mirror(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr,
+                            const int* colidx, int* colptr, int* rowidx, int* perm,
+                            void* stream);
 
 /* One SVT evaluation T_eps(W) by BLWS (Sections 4, 4.1, 4.2; Eq. (4)).
  *

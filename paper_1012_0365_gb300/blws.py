@@ -13,14 +13,15 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libblws.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
            "blws_last_error", "blws_launch_count", "blws_apply", "blws_apply_noalloc",
            "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
-           "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy")
+           "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
+           "blws_csc_mirror")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -32,7 +33,8 @@ class BlwsOp(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("n", ctypes.c_int), ("W", ctypes.c_void_p),
                 ("ldw", ctypes.c_int), ("nnz", ctypes.c_int), ("rowptr", ctypes.c_void_p),
                 ("colidx", ctypes.c_void_p), ("val", ctypes.c_void_p), ("rl", ctypes.c_int),
-                ("Ul", ctypes.c_void_p), ("sl", ctypes.c_void_p), ("Vl", ctypes.c_void_p)]
+                ("Ul", ctypes.c_void_p), ("sl", ctypes.c_void_p), ("Vl", ctypes.c_void_p),
+                ("colptr", ctypes.c_void_p), ("rowidx", ctypes.c_void_p), ("perm", ctypes.c_void_p)]
 
 
 class RpcaParams(ctypes.Structure):
@@ -122,6 +124,7 @@ def load():
     lib.blws_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(Result)]
     lib.blws_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.blws_server_destroy.argtypes = [vp]
+    lib.blws_csc_mirror.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, vp, vp]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
@@ -266,6 +269,37 @@ class Context:
         P = empty_colmajor(m + n, b) if P is None else P
         op = BlwsOp()
         op.m, op.n, op.W, op.ldw = m, n, W.data_ptr(), m
+        st = load().blws_apply(self._h, ctypes.byref(op), _ptr(X), m + n, b, _ptr(P), m + n,
+                               _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_apply")
+        return P
+
+    def csc_mirror(self, m, n, rowptr, colidx, stream=None):
+        """(colptr, rowidx, perm): the column-major mirror of a CSR pattern (int32 tensors)."""
+        torch = _torch()
+        nnz = int(colidx.numel())
+        colptr = torch.empty(n + 1, dtype=torch.int32, device="cuda")
+        rowidx = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        perm = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        st = load().blws_csc_mirror(self._h, m, n, nnz, rowptr.data_ptr(), colidx.data_ptr(),
+                                    colptr.data_ptr(), rowidx.data_ptr(), perm.data_ptr(), _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_csc_mirror")
+        return colptr, rowidx, perm
+
+    def apply_sparse(self, m, n, rowptr, colidx, vals, X, P=None, stream=None, mirror=None):
+        """P = [S X_v; S^T X_u] for the CSR matrix S (int32 rowptr/colidx, FP64 vals):
+        the matrix-completion product.  mirror: (colptr, rowidx, perm) from
+        csc_mirror, else the call builds one."""
+        b = X.shape[1]
+        _check_colmajor(X, m + n, b, "X")
+        P = empty_colmajor(m + n, b) if P is None else P
+        op = BlwsOp()
+        op.m, op.n, op.W, op.ldw = m, n, None, m
+        op.nnz, op.rowptr, op.colidx, op.val = int(vals.numel()), rowptr.data_ptr(), colidx.data_ptr(), vals.data_ptr()
+        if mirror is not None:
+            op.colptr, op.rowidx, op.perm = (t.data_ptr() for t in mirror)
         st = load().blws_apply(self._h, ctypes.byref(op), _ptr(X), m + n, b, _ptr(P), m + n,
                                _stream(stream))
         if st != OK:

@@ -86,6 +86,7 @@ __global__ void ritz_values(int r, const double* __restrict__ lam, double eps, d
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
                      double* P, int ldp) {
   const int m = op.m, n = op.n;
+  if (op.W && op.Or && op.Oc) return oz_dual_apply(ctx, s, *op.Or, *op.Oc, m, n, X, ldx, b, P, ldp);
   if (op.W && op.Wr && op.Wc && tc_npad(b) > 0)
     return tc_dual_apply(ctx, s, *op.Wr, *op.Wc, m, n, X, ldx, b, P, ldp);
   if (op.W) {

@@ -22,6 +22,9 @@ struct Operator {
   // column-major Wc: n rows); when set, products with W run on tensor cores
   const TcPlanes* Wr = nullptr;
   const TcPlanes* Wc = nullptr;
+  // FP64-equivalent tensor-core products: digit planes of W (both orientations)
+  const OzPlanes* Or = nullptr;
+  const OzPlanes* Oc = nullptr;
   // low-rank part
   int rl = 0;
   const double* Ul = nullptr;

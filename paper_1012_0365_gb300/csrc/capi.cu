@@ -94,7 +94,8 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   blws_config c;
   blws_config_default(&c);
   if (cfg) c = *cfg;
-  if (c.k < 1 || c.k_cold < 1 || (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED))
+  if (c.k < 1 || c.k_cold < 1 ||
+      (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED && c.precision != BLWS_PREC_FP64_TC))
     return BLWS_EINVAL;
   blws_ctx* ctx = new (std::nothrow) blws_ctx();
   if (!ctx) return BLWS_ENOMEM;
@@ -172,11 +173,17 @@ static blws_status make_operator(blws_ctx* ctx, const blws_op* W, cudaStream_t s
   op->rowptr = W->rowptr;
   op->colidx = W->colidx;
   op->val = W->val;
-  int *cp, *ri, *pm;
-  BLWS_TRY(blws::build_csc(ctx, s, m, n, W->nnz, W->rowptr, W->colidx, &cp, &ri, &pm));
-  op->colptr = cp;
-  op->rowidx = ri;
-  op->perm = pm;
+  if (W->colptr && W->rowidx && W->perm) {  // the caller's mirror of this pattern
+    op->colptr = W->colptr;
+    op->rowidx = W->rowidx;
+    op->perm = W->perm;
+  } else {
+    int *cp, *ri, *pm;
+    BLWS_TRY(blws::build_csc(ctx, s, m, n, W->nnz, W->rowptr, W->colidx, &cp, &ri, &pm));
+    op->colptr = cp;
+    op->rowidx = ri;
+    op->perm = pm;
+  }
   op->rl = W->rl;
   op->Ul = W->Ul;
   op->sl = W->sl;
@@ -187,8 +194,18 @@ static blws_status make_operator(blws_ctx* ctx, const blws_op* W, cudaStream_t s
 // Mixed-precision contexts: TF32 planes of a dense W in both orientations
 // (context workspace), so that products with W run on the tensor cores.
 static blws_status attach_planes(blws_ctx* ctx, cudaStream_t s, blws::Operator* op,
-                                 blws::TcPlanes* Wr, blws::TcPlanes* Wc) {
-  if (ctx->cfg.precision != BLWS_PREC_MIXED || !op->W) return BLWS_OK;
+                                 blws::TcPlanes* Wr, blws::TcPlanes* Wc, blws::OzPlanes* Or,
+                                 blws::OzPlanes* Oc) {
+  if (!op->W) return BLWS_OK;
+  if (ctx->cfg.precision == BLWS_PREC_FP64_TC) {
+    BLWS_TRY(blws::oz_alloc(ctx, op->m, op->n, Or, Oc));
+    BLWS_TRY(blws::oz_planes_from_rows(ctx, s, op->W, op->ldw, op->m, op->n, *Or));
+    BLWS_TRY(blws::oz_planes_from_cols(ctx, s, op->W, op->ldw, 0, op->m, op->n, *Oc));
+    op->Or = Or;
+    op->Oc = Oc;
+    return BLWS_OK;
+  }
+  if (ctx->cfg.precision != BLWS_PREC_MIXED) return BLWS_OK;
   const int m = op->m, n = op->n;
   const int ldr = blws::tc_ld(n), ldc = blws::tc_ld(m);
   float* wp = nullptr;
@@ -199,6 +216,23 @@ static blws_status attach_planes(blws_ctx* ctx, cudaStream_t s, blws::Operator* 
   BLWS_TRY(blws::tc_planes_from_cols(ctx, s, op->W, op->ldw, 0, m, n, *Wc));
   op->Wr = Wr;
   op->Wc = Wc;
+  return BLWS_OK;
+}
+
+blws_status blws_csc_mirror(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr,
+                            const int* colidx, int* colptr, int* rowidx, int* perm, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (m < 1 || n < 1 || nnz < 0 || !rowptr || !colptr || (nnz > 0 && (!colidx || !rowidx || !perm)))
+    return ctx->fail(BLWS_EINVAL, "blws_csc_mirror: bad arguments");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int *cp, *ri, *pm;
+  BLWS_TRY(blws::build_csc(ctx, s, m, n, nnz, rowptr, colidx, &cp, &ri, &pm));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(colptr, cp, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, s));
+  if (nnz > 0) {
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(rowidx, ri, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(perm, pm, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, s));
+  }
   return BLWS_OK;
 }
 
@@ -214,7 +248,8 @@ blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx
   BLWS_TRY(make_operator(ctx, W, s, &op));
   BLWS_TRY(blws::blws_reserve(ctx, W->m, W->n, b, 1));
   blws::TcPlanes Wr, Wc;
-  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc));
+  blws::OzPlanes Or, Oc;
+  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc, &Or, &Oc));
   return blws::apply_op(ctx, s, op, X, ldx, b, P, ldp);
 }
 
@@ -248,7 +283,8 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
   a.cold = (w == 0);
   a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
   blws::TcPlanes Wr, Wc;
-  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc));
+  blws::OzPlanes Or, Oc;
+  BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc, &Or, &Oc));
   a.mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
   double* scal;
   BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));

@@ -64,6 +64,7 @@ enum Buf {
   BUF_TC_W,      // mixed precision: TF32 planes of W (two orientations, hi and lo)
   BUF_TC_X,      // mixed precision: TF32 planes of the block X
   BUF_TC_PART,   // mixed precision: split-K partial sums (FP32)
+  BUF_OZ_E,      // FP64-equivalent tensor-core products: scale exponents
   BUF_COUNT_
 };
 

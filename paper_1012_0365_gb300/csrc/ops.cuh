@@ -1,6 +1,8 @@
 // Internal operations of the BLWS library (host launchers of the kernels).
 // All matrices are column-major FP64 unless a name says otherwise.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace blws {
@@ -59,5 +61,30 @@ blws_status tc_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int l
 // column-major planes Wc (n rows); X is (m+n) x b FP64, b <= 256.
 blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const TcPlanes& Wc, int m,
                           int n, const double* X, int ldx, int b, double* P, int ldp);
+
+// ---------------------------------- FP64-equivalent tensor-core products (tc_ozaki)
+// A matrix as S BF16 planes of balanced base-128 digits with one power-of-two
+// scale per row: plane t, element (r, k) at d[t rows ld + r ld + k]; e[r] the
+// scale exponent of row r.  ld = oz_ld(inner) (a multiple of 64).
+struct OzPlanes {
+  __nv_bfloat16* d;
+  int* e;
+  int rows, inner, ld;
+};
+int oz_ld(int inner);
+int oz_digits();
+// digit planes of an m x n W in both orientations, in the context's workspace
+blws_status oz_alloc(Ctx* ctx, int m, int n, OzPlanes* Or, OzPlanes* Oc);
+// transposed digit planes of the m x n column-major A (rows of A, scale per row)
+blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int lda, int m, int n,
+                                const OzPlanes& out);
+// digit planes of the column-major slab (row r of the planes = column r of A,
+// K along A's rows row0 .. row0 + inner; scale per column)
+blws_status oz_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int lda, int row0, int inner,
+                                int rows, const OzPlanes& out);
+// P = [W X_v; W^T X_u] (FP64 out, errors at the FP64 level) from W's digit
+// planes in both orientations (Wr: m rows, Wc: n rows).
+blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const OzPlanes& Wc, int m, int n,
+                          const double* X, int ldx, int b, double* P, int ldp);
 
 }  // namespace blws

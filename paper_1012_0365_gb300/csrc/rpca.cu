@@ -323,8 +323,11 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   // mixed precision: TF32 planes of W in both orientations, rebuilt from W
   // each iteration until the residual reaches p.mixed_tol
   bool mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
+  const bool fp64tc = ctx->cfg.precision == BLWS_PREC_FP64_TC;
   int mixed_iters = 0;
   TcPlanes Wr{}, Wc{};
+  OzPlanes Or{}, Oc{};
+  if (fp64tc) BLWS_TRY(oz_alloc(ctx, m, n, &Or, &Oc));
   if (mixed) {
     const int ldr = tc_ld(n), ldc = tc_ld(m);
     float* wp = nullptr;
@@ -365,6 +368,12 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       ++mixed_iters;
     } else {
       Wop.Wr = Wop.Wc = nullptr;
+    }
+    if (fp64tc) {  // FP64-equivalent digit planes of this iteration's W
+      BLWS_TRY(oz_planes_from_rows(ctx, s, W, ld, m, n, Or));
+      BLWS_TRY(oz_planes_from_cols(ctx, s, W, ld, 0, m, n, Oc));
+      Wop.Or = &Or;
+      Wop.Oc = &Oc;
     }
     BLWS_TRY(blws_run(ctx, s, Wop, a, Uw, m, Vw, n, sig, count_dev));
     thresholds<<<1, 256, 0, s>>>(sv, sig, eps, th);

@@ -57,22 +57,67 @@ __global__ void scatter_csc(int m, const int* __restrict__ rowptr, const int* __
 }
 
 // sort each column segment by row (the scatter above leaves it in arrival
-// order); insertion sort by one thread per column is enough for the short
-// segments of a sampled pattern, and makes the CSC mirror deterministic.
-__global__ void sort_segments(int n, const int* __restrict__ colptr, int* rowidx, int* perm) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-    const int lo = colptr[j], hi = colptr[j + 1];
-    for (int a = lo + 1; a < hi; ++a) {
-      const int r = rowidx[a], p = perm[a];
-      int b = a - 1;
-      while (b >= lo && rowidx[b] > r) {
-        rowidx[b + 1] = rowidx[b];
-        perm[b + 1] = perm[b];
-        --b;
+// order), which makes the CSC mirror deterministic: one CTA per column, a
+// bitonic sort of (row, CSR position) pairs in shared memory (rows within a
+// column are distinct, so the order is unique); a segment longer than the
+// shared buffer falls back to an insertion sort by one thread.
+constexpr int kSortMax = 4096;
+
+__global__ void __launch_bounds__(256)
+sort_segments(int n, const int* __restrict__ colptr, int* rowidx, int* perm) {
+  __shared__ int key[kSortMax];
+  __shared__ int val[kSortMax];
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const int lo = colptr[j], len = colptr[j + 1] - lo;
+    if (len <= 1) continue;
+    if (len > kSortMax) {
+      if (threadIdx.x == 0) {
+        for (int a = lo + 1; a < lo + len; ++a) {
+          const int r = rowidx[a], p = perm[a];
+          int b = a - 1;
+          while (b >= lo && rowidx[b] > r) {
+            rowidx[b + 1] = rowidx[b];
+            perm[b + 1] = perm[b];
+            --b;
+          }
+          rowidx[b + 1] = r;
+          perm[b + 1] = p;
+        }
       }
-      rowidx[b + 1] = r;
-      perm[b + 1] = p;
+      __syncthreads();
+      continue;
     }
+    int P = 1;
+    while (P < len) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      key[i] = i < len ? rowidx[lo + i] : 0x7fffffff;
+      val[i] = i < len ? perm[lo + i] : 0;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+      for (int h = k >> 1; h > 0; h >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int l = i ^ h;
+          if (l > i) {
+            const bool up = (i & k) == 0;
+            const int a = key[i], b = key[l];
+            if ((a > b) == up) {
+              key[i] = b;
+              key[l] = a;
+              const int t = val[i];
+              val[i] = val[l];
+              val[l] = t;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      rowidx[lo + i] = key[i];
+      perm[lo + i] = val[i];
+    }
+    __syncthreads();
   }
 }
 
@@ -212,7 +257,7 @@ blws_status build_csc(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int
   if (nnz > 0) {
     scatter_csc<<<ceil_div(m, 256), 256, 0, s>>>(m, rowptr, colidx, cnt, ri, pm);
     BLWS_CHECK_LAUNCH(ctx);
-    sort_segments<<<ceil_div(n, 128), 128, 0, s>>>(n, cp, ri, pm);
+    sort_segments<<<std::min(n, ctx->sms * 16), 256, 0, s>>>(n, cp, ri, pm);
     BLWS_CHECK_LAUNCH(ctx);
   }
   *colptr = cp;

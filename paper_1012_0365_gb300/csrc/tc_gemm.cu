@@ -28,16 +28,18 @@
 #include <mutex>
 
 #include "ops.cuh"
+#include "tc_ptx.cuh"
 
 namespace blws {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kTcBM = 128;      // accumulator rows (tensor-memory lanes)
 constexpr int kTcBK = 32;       // K block: 32 FP32 = one 128-byte swizzle row
 constexpr int kTcThreads = 128;
 constexpr int kTcMaxChunk = 256;  // K terms summed in FP32 inside the tensor core
-constexpr uint32_t kWaitLimit = 1u << 24;  // bounded mbarrier polls (seconds)
 
 struct TcJob {
   CUtensorMap a_hi, a_lo, b_hi, b_lo;  // 64-byte aligned (CUtensorMap is)
@@ -51,107 +53,6 @@ struct TcJobs {
   int N;        // columns of the products (b)
   int* err;     // error word (nonzero: a wait ran out)
 };
-
-// ------------------------------------------------------------ PTX helpers --
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-// true when the phase with the given parity has completed; false after the poll limit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t i = 0; i < kWaitLimit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile with the 128-byte
-// swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte
-// offset), descriptor version 1, swizzle mode 2 (128B).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1u << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1u << 46;                 // version
-  d |= (uint64_t)2u << 61;                 // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major.
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
-  return (1u << 4)                      // D format F32
-         | (2u << 7)                    // A format TF32
-         | (2u << 10)                   // B format TF32
-         | ((uint32_t)(N >> 3) << 17)   // N / 8
-         | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
 
 template <int NPAD>
 __host__ __device__ constexpr int tmem_cols() {
@@ -442,7 +343,7 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
   // job 0: P_u = W X_v (A = Wr: m rows, K = n); job 1: P_v = W^T X_u (A = Wc: n rows, K = m)
   const int Ms[2] = {m, n}, Ks[2] = {n, m};
   const int tiles0 = ceil_div(m, kTcBM), tiles1 = ceil_div(n, kTcBM);
-  const int per = std::max(1, ctx->sms / (tiles0 + tiles1));
+
   TcJobs jobs;
   memset(&jobs, 0, sizeof(jobs));
   size_t part_off[2] = {0, 0}, part_total = 0;
@@ -451,6 +352,7 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
     // the tensor core's FP32 accumulation error grows with the number of
     // terms: at most kTcMaxChunk of K per accumulator, then FP64 sums
     const int kblocks = ceil_div(Ks[t], kTcBK);
+    const int per = ceil_div(ctx->sms, std::max(1, tiles[t]));  // each product fills about a wave
     int sp = std::max(1, std::min(per, kblocks));
     sp = std::max(sp, ceil_div(Ks[t], kTcMaxChunk));
     kchunk[t] = ceil_div(kblocks, sp) * kTcBK;

@@ -1,0 +1,539 @@
+// FP64-equivalent products with the augmented matrix on the tensor cores
+// (Ozaki-type splitting): P = [W X_v; W^T X_u] for BLWS_PREC_FP64_TC.
+//
+// Every row i of an A operand (and every column j of a B operand) is scaled by
+// a power of two, 2^E_i >= max |entries|, and written in balanced base-128
+// digits: w = 2^E_i sum_{t=1..S} a_t 128^-t with integers |a_1| <= 128 and
+// |a_t| <= 64 (t >= 2), each exact in BF16 (S = 7: 49 bits).  Then
+//   (W X)_ij = 2^{E_i + F_j} sum_{L} 128^-L acc_L,
+//   acc_L = sum_k sum_{t+u=L} a_t(i,k) b_u(k,j),
+// and pairs with t + u > S + 1 are dropped (below 2^-47 of the leading
+// term).  Each level L = 2..S+1 is one FP32 accumulator in tensor memory,
+// filled by tcgen05.mma.kind::f16 on the BF16 digit planes; a level's sum over
+// 256 terms stays below 2^24 in magnitude with integer values, so it is exact.
+// Every 256 terms the four epilogue warps move the levels out of tensor
+// memory into a double-FP32 (hi + lo) accumulator per output (FP64 is slow on
+// this GPU; two FP32 words carry 48 bits), and at the end multiply by the
+// scales in FP64.  Split-K partials are added in FP64 in a fixed order.
+//
+// Operands are K-major BF16 planes with 64-byte swizzle (32 elements per
+// K block), loaded by 3-D TMA (K, row, digit plane).
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "ops.cuh"
+#include "tc_ptx.cuh"
+
+namespace blws {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kOzS = 7;          // digits per value
+constexpr int kOzBM = 128;       // rows per CTA (tensor-memory lanes)
+constexpr int kOzBN = 64;        // columns per CTA (one accumulator level = 64 columns)
+constexpr int kOzBK = 32;        // K block: 32 BF16 = one 64-byte swizzle row
+constexpr int kOzChunk = 256;    // exact FP32 sums: at most 256 K terms per level between drains
+constexpr int kOzStages = 2;
+constexpr int kOzThreads = 256;   // warp 0 TMA, warp 1 MMA, warp 2 TMEM, warps 4-7 drain/epilogue
+constexpr int kOzLevels = kOzS;  // levels L = 2 .. S + 1
+constexpr int kOzPairs = kOzS * (kOzS + 1) / 2;  // pairs (t, u) with t + u <= S + 1
+
+struct OzJob {
+  CUtensorMap a, b;     // 3-D maps: (K, rows, plane)
+  const int* ea;        // row scales of A (rows)
+  const int* eb;        // column scales of B (b columns)
+  float2* part;         // [splits][npad][Mpad] (hi, lo) partial sums, unscaled
+  int M, K, tiles, ngroups, splits, kchunk, Mpad, npad;
+};
+
+struct OzJobs {
+  OzJob job[2];
+  int blocks0;
+  int N;
+  int* err;
+};
+
+// (t, u) digit pairs ordered by level, the first pair of each level first
+struct PairTable {
+  int t[kOzPairs], u[kOzPairs];
+  __host__ __device__ constexpr PairTable() : t{}, u{} {
+    int p = 0;
+    for (int L = 2; L <= kOzS + 1; ++L)
+      for (int tt = 1; tt <= kOzS; ++tt) {
+        const int uu = L - tt;
+        if (uu >= 1 && uu <= kOzS) {
+          t[p] = tt;
+          u[p] = uu;
+          ++p;
+        }
+      }
+  }
+};
+
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  // (hi, lo) += v with the rounding error of hi + v kept in lo (Knuth's TwoSum)
+  const float s = hi + v;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (v - bb);
+  hi = s;
+  lo += err;
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant__ OzJobs jobs) {
+  // the drain warps hold 2 x 64 FP32 accumulators per thread
+  constexpr int A_BYTES = kOzBM * kOzBK * 2;  // 8 KB per digit plane
+  constexpr int B_BYTES = kOzBN * kOzBK * 2;  // 4 KB
+  constexpr int STAGE = kOzS * (A_BYTES + B_BYTES);
+  constexpr uint32_t NCOLS = 512;
+  constexpr PairTable PT;
+  static_assert(kOzLevels * kOzBN <= 512, "levels x columns fit the tensor memory");
+  static_assert(STAGE % 1024 == 0, "stage alignment");
+  extern __shared__ uint8_t oz_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(oz_smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full_bar[kOzStages];
+  __shared__ __align__(8) uint64_t empty_bar[kOzStages];
+  __shared__ __align__(8) uint64_t chunk_bar;    // MMA -> drain: a chunk's levels are complete
+  __shared__ __align__(8) uint64_t drained_bar;  // drain -> MMA: the levels may be overwritten
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail_sh;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int jb = (int)blockIdx.x < jobs.blocks0 ? 0 : 1;
+  const OzJob& J = jobs.job[jb];
+  const int local = jb ? (int)blockIdx.x - jobs.blocks0 : (int)blockIdx.x;
+  const int tile = local % J.tiles;
+  const int ng = (local / J.tiles) % J.ngroups;
+  const int split = local / (J.tiles * J.ngroups);
+  const int row0 = tile * kOzBM, col0 = ng * kOzBN;
+  const int kbeg = split * J.kchunk;
+  const int kend = min(J.K, kbeg + J.kchunk);
+  const int nk = (kend - kbeg + kOzBK - 1) / kOzBK;
+  constexpr int kPerChunk = kOzChunk / kOzBK;
+  const int nchunks = (nk + kPerChunk - 1) / kPerChunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOzStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&chunk_bar, 1);
+    mbar_init(&drained_bar, 128);  // the four drain warps
+    fail_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // producer: S A-planes and S B-planes per K block (two 3-D boxes)
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kOzStages;
+      const uint32_t round = (uint32_t)(kb / kOzStages);
+      if (kb >= kOzStages && !mbar_wait(&empty_bar[s], (round & 1u) ^ 1u)) {
+        fail_sh = 1;
+        break;
+      }
+      uint8_t* st = smem + (size_t)s * STAGE;
+      mbar_expect_tx(&full_bar[s], STAGE);
+      const int kx = kbeg + kb * kOzBK;
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(st)),
+          "l"(reinterpret_cast<uint64_t>(&J.a)), "r"(kx), "r"(row0), "r"(0), "r"(smem_u32(&full_bar[s]))
+          : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(st + kOzS * A_BYTES)),
+          "l"(reinterpret_cast<uint64_t>(&J.b)), "r"(kx), "r"(col0), "r"(0), "r"(smem_u32(&full_bar[s]))
+          : "memory");
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = bf16_idesc(kOzBM, kOzBN);
+    int kb = 0;
+    for (int c = 0; c < nchunks && !fail_sh; ++c) {
+      if (c > 0 && !mbar_wait(&drained_bar, (uint32_t)((c - 1) & 1))) {
+        fail_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const int kb_end = min(nk, kb + kPerChunk);
+      for (int kc = 0; kb < kb_end; ++kb, ++kc) {
+        const int s = kb % kOzStages;
+        const uint32_t round = (uint32_t)(kb / kOzStages);
+        if (!mbar_wait(&full_bar[s], round & 1u)) {
+          fail_sh = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t st = smem_u32(smem + (size_t)s * STAGE);
+#pragma unroll
+        for (int kk = 0; kk < kOzBK / 16; ++kk) {
+#pragma unroll
+          for (int p = 0; p < kOzPairs; ++p) {
+            const int t = PT.t[p], u = PT.u[p], L = t + u;
+            const bool first_of_level = (p == 0) || (PT.t[p - 1] + PT.u[p - 1] != L);
+            const uint64_t ad = sw64_desc(st + (uint32_t)(t - 1) * A_BYTES + kk * 32);
+            const uint64_t bd = sw64_desc(st + kOzS * A_BYTES + (uint32_t)(u - 1) * B_BYTES + kk * 32);
+            const uint32_t acc = (kc > 0 || kk > 0 || !first_of_level) ? 1u : 0u;
+            mma_bf16(tbase + (uint32_t)((L - 2) * kOzBN), ad, bd, idesc, acc);
+          }
+        }
+        mma_commit(&empty_bar[s]);
+      }
+      mma_commit(&chunk_bar);  // this chunk's levels complete once the MMAs above are done
+    }
+  }
+  __syncwarp();
+
+  if (warp < 4) {  // producer, MMA issuer and allocator wait for the drain warps below
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2) {
+      tc_fence_after();
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(NCOLS)
+                   : "memory");
+    }
+    return;
+  }
+  // drain (warps 4-7; warp w reads tensor-memory lanes 32 (w - 4) ..): every
+  // chunk, levels -> double-FP32 accumulators, one row per thread
+  const int q = warp - 4;
+  float hi[kOzBN], lo[kOzBN];
+#pragma unroll
+  for (int j = 0; j < kOzBN; ++j) {
+    hi[j] = 0.0f;
+    lo[j] = 0.0f;
+  }
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    if (!mbar_wait(&chunk_bar, (uint32_t)(c & 1))) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+#pragma unroll 1
+    for (int L = 2; L <= kOzS + 1; ++L) {
+      const float scale = __uint_as_float((uint32_t)(127 - 7 * L) << 23);  // 2^(-7 L), exact
+#pragma unroll
+      for (int c0 = 0; c0 < kOzBN; c0 += 16) {
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * kOzBN + c0), v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j] * scale);
+      }
+    }
+    tc_fence_before();
+    mbar_arrive(&drained_bar);
+  }
+  if (ok && !fail_sh) {
+    // (hi, lo) pairs out; the FP64 combination and the power-of-two scales are
+    // applied by the grid-wide reduction (FP64 on one SM would cost more than
+    // this CTA's tensor work)
+    const int row = row0 + q * 32 + lane;
+    if (row < J.M) {
+      float2* out = J.part + (size_t)split * J.npad * J.Mpad;
+#pragma unroll
+      for (int j = 0; j < kOzBN; ++j) {
+        const int col = col0 + j;
+        if (col < jobs.N) out[(size_t)col * J.Mpad + row] = make_float2(hi[j], lo[j]);
+      }
+    }
+  } else if (threadIdx.x == 128) {
+    atomicExch(jobs.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();  // matches the one above: tensor memory is freed after the last read
+}
+
+// ------------------------------------------------------------- splitting --
+// exponent E with max |v| < 2^E (0 for an all-zero vector)
+__device__ __forceinline__ int scale_exp(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+
+// balanced base-128 digits of x = v 2^-E (|x| < 1): M = rint(x 2^(7S)),
+// digits from the least significant: d = ((M + 64) mod 128) - 64
+__device__ __forceinline__ void digits(double v, int E, int (&a)[kOzS]) {
+  long long M = llrint(ldexp(v, 7 * kOzS - E));
+#pragma unroll
+  for (int t = kOzS - 1; t >= 1; --t) {
+    const long long d = ((M + 64) & 127) - 64;
+    a[t] = (int)d;
+    M = (M - d) >> 7;
+  }
+  a[0] = (int)M;
+}
+
+// E[i] for the rows of the column-major m x n block A (ld), from 32 x 32 tiles:
+// each tile's row maxima enter by an integer atomic max of their exponents
+// (E starts below every exponent; an all-zero row keeps that value, and its
+// digits are zero whatever E is)
+constexpr int kOzNoExp = -4000;
+
+__global__ void oz_row_scales(int m, int n, const double* __restrict__ A, int lda, int* E) {
+  __shared__ double t[32][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = i0 + tx, j = j0 + jj;
+    t[jj][tx] = (i < m && j < n) ? fabs(A[i + (size_t)j * lda]) : 0.0;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    double mx = 0.0;
+#pragma unroll 8
+    for (int jj = 0; jj < 32; ++jj) mx = fmax(mx, t[jj][tx]);
+    if (mx > 0.0 && i0 + tx < m) atomicMax(&E[i0 + tx], scale_exp(mx));
+  }
+}
+
+__global__ void oz_fill(int n, int v, int* E) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) E[i] = v;
+}
+
+// digit planes of the column-major slab, one CTA per plane row r (= column r
+// of A, K along A's rows row0 .. row0 + inner): the column's maximum, its
+// exponent E[r], then its digits (plane t, (r, k) at t plane_rows ld + r ld + k;
+// zero padding up to ld)
+__global__ void __launch_bounds__(256)
+oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __restrict__ A, int lda,
+               int row0, int* E, __nv_bfloat16* planes) {
+  __shared__ double red[8];
+  __shared__ int e_sh;
+  const size_t plane = (size_t)plane_rows * ld;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const double* col = A + row0 + (size_t)r * lda;
+    double mx = 0.0;
+    for (int k = threadIdx.x; k < inner; k += blockDim.x) mx = fmax(mx, fabs(col[k]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m2 = 0.0;
+      for (int w = 0; w < (int)blockDim.x / 32; ++w) m2 = fmax(m2, red[w]);
+      e_sh = scale_exp(m2);
+      E[r] = e_sh;
+    }
+    __syncthreads();
+    const int er = e_sh;
+    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+      int a[kOzS];
+      if (k < inner) {
+        digits(col[k], er, a);
+      } else {
+#pragma unroll
+        for (int t = 0; t < kOzS; ++t) a[t] = 0;
+      }
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t) planes[t * plane + (size_t)r * ld + k] = __float2bfloat16_rn((float)a[t]);
+    }
+    __syncthreads();
+  }
+}
+
+// transposed digit planes of the m x n column-major A: plane t, (i, j) = A[i + j lda],
+// split with the scale of row i
+__global__ void oz_planes_rows(int m, int n, int ld, const double* __restrict__ A, int lda,
+                               const int* __restrict__ E, __nv_bfloat16* planes) {
+  __shared__ double tile[32][33];
+  const size_t plane = (size_t)m * ld;
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = i0 + tx, j = j0 + jj;
+    tile[jj][tx] = (i < m && j < n) ? A[i + (size_t)j * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = i0 + ii, j = j0 + tx;
+    if (i < m && j < ld) {
+      int a[kOzS];
+      digits(tile[tx][ii], E[i], a);
+#pragma unroll
+      for (int t = 0; t < kOzS; ++t)
+        planes[t * plane + (size_t)i * ld + j] = __float2bfloat16_rn((float)a[t]);
+    }
+  }
+}
+
+// P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64, split order
+__global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const float2* __restrict__ part,
+                          const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ P,
+                          int ldp) {
+  const size_t total = (size_t)M * N;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e % M), j = (int)(e / M);
+    double acc = 0.0;
+    for (int z = 0; z < splits; ++z) {
+      const float2 v = part[((size_t)z * npad + j) * Mpad + r];
+      acc += (double)v.x + (double)v.y;
+    }
+    P[r + (size_t)j * ldp] = ldexp(acc, ea[r] + eb[j]);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_oz_encode = nullptr;
+std::mutex g_oz_mutex;
+
+blws_status oz_encoder(Ctx* ctx) {
+  std::lock_guard<std::mutex> lock(g_oz_mutex);
+  if (g_oz_encode) return BLWS_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  const cudaError_t e =
+      cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return ctx->fail(BLWS_ENOTSUP, "cuTensorMapEncodeTiled is not available from the driver");
+  g_oz_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return BLWS_OK;
+}
+
+// 3-D map over S digit planes of rows x inner BF16 (ld elements per row)
+blws_status oz_encode(Ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int rows, int inner, int ld,
+                      int box_rows) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld % 8))
+    return ctx->fail(BLWS_EINVAL, "digit plane not 16-byte aligned");
+  cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)kOzS};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)kOzS};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = g_oz_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base),
+                                 dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return ctx->fail(BLWS_ECUDA, "cuTensorMapEncodeTiled (digits) failed (%d)", (int)r);
+  return BLWS_OK;
+}
+
+size_t oz_smem_bytes() { return (size_t)kOzStages * kOzS * (kOzBM + kOzBN) * kOzBK * 2 + 1024; }
+
+}  // namespace
+
+int oz_ld(int inner) { return ceil_div(inner, 64) * 64; }
+int oz_digits() { return kOzS; }
+
+blws_status oz_alloc(Ctx* ctx, int m, int n, OzPlanes* Or, OzPlanes* Oc) {
+  const int ldr = oz_ld(n), ldc = oz_ld(m);
+  const size_t dr = (size_t)kOzS * m * ldr, dc = (size_t)kOzS * n * ldc;
+  uint8_t* p = nullptr;
+  const size_t bytes = (dr + dc) * sizeof(__nv_bfloat16) + ((size_t)m + n + 64) * sizeof(int);
+  BLWS_TRY(ctx->get(BUF_TC_W, bytes, (void**)&p));
+  __nv_bfloat16* d = reinterpret_cast<__nv_bfloat16*>(p);
+  int* e = reinterpret_cast<int*>(p + (dr + dc) * sizeof(__nv_bfloat16));
+  *Or = OzPlanes{d, e, m, n, ldr};
+  *Oc = OzPlanes{d + dr, e + m, n, m, ldc};
+  return BLWS_OK;
+}
+
+blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int lda, int m, int n,
+                                const OzPlanes& out) {
+  if (m <= 0 || n <= 0) return BLWS_OK;
+  oz_fill<<<ceil_div(m, 256), 256, 0, s>>>(m, kOzNoExp, out.e);
+  BLWS_CHECK_LAUNCH(ctx);
+  oz_row_scales<<<dim3(ceil_div(m, 32), ceil_div(n, 32)), 256, 0, s>>>(m, n, A, lda, out.e);
+  BLWS_CHECK_LAUNCH(ctx);
+  dim3 grid(ceil_div(m, 32), ceil_div(out.ld, 32));
+  oz_planes_rows<<<grid, 256, 0, s>>>(m, n, out.ld, A, lda, out.e, out.d);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+blws_status oz_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int lda, int row0, int inner,
+                                int rows, const OzPlanes& out) {
+  if (rows <= 0) return BLWS_OK;
+  oz_planes_cols<<<std::min(rows, ctx->sms * 16), 256, 0, s>>>(rows, out.rows, inner, out.ld, A, lda,
+                                                               row0, out.e, out.d);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const OzPlanes& Wc, int m, int n,
+                          const double* X, int ldx, int b, double* P, int ldp) {
+  BLWS_TRY(oz_encoder(ctx));
+  const int ngroups = ceil_div(b, kOzBN), npad = ngroups * kOzBN;
+  // digit planes of X_u (rows 0..m) and X_v (rows m..m+n): b rows each, scale per column
+  const int ldu = oz_ld(m), ldv = oz_ld(n);
+  __nv_bfloat16* xp = nullptr;
+  int* xe = nullptr;
+  BLWS_TRY(ctx->get(BUF_TC_X, (size_t)kOzS * npad * (ldu + ldv) * sizeof(__nv_bfloat16), (void**)&xp));
+  BLWS_TRY(ctx->get(BUF_OZ_E, (size_t)2 * npad * sizeof(int), (void**)&xe));
+  OzPlanes Xu{xp, xe, npad, m, ldu};
+  OzPlanes Xv{xp + (size_t)kOzS * npad * ldu, xe + npad, npad, n, ldv};
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(xe, 0, sizeof(int) * 2 * npad, s));
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(xp, 0, (size_t)kOzS * npad * (ldu + ldv) * sizeof(__nv_bfloat16), s));
+  BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, 0, m, b, Xu));
+  BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, m, n, b, Xv));
+
+  const int Ms[2] = {m, n}, Ks[2] = {n, m};
+  const int tiles[2] = {ceil_div(m, kOzBM), ceil_div(n, kOzBM)};
+  OzJobs jobs;
+  memset(&jobs, 0, sizeof(jobs));
+  int splits[2], kchunk[2];
+  size_t off[2], total = 0;
+  for (int t = 0; t < 2; ++t) {
+    // each product alone fills about one wave (a tall W gives one product
+    // few row tiles and a long K: it needs the split)
+    const int kchunks = ceil_div(Ks[t], kOzChunk);
+    const int per = ceil_div(ctx->sms, std::max(1, tiles[t] * ngroups));
+    const int sp = std::max(1, std::min(per, kchunks));
+    kchunk[t] = ceil_div(kchunks, sp) * kOzChunk;
+    splits[t] = ceil_div(Ks[t], kchunk[t]);
+    off[t] = total;
+    total += (size_t)splits[t] * npad * tiles[t] * kOzBM;
+  }
+  float2* part = nullptr;
+  BLWS_TRY(ctx->get(BUF_TC_PART, total * sizeof(float2), (void**)&part));
+  const OzPlanes* A[2] = {&Wr, &Wc};
+  const OzPlanes* B[2] = {&Xv, &Xu};
+  for (int t = 0; t < 2; ++t) {
+    OzJob& J = jobs.job[t];
+    BLWS_TRY(oz_encode(ctx, &J.a, A[t]->d, Ms[t], Ks[t], A[t]->ld, kOzBM));
+    BLWS_TRY(oz_encode(ctx, &J.b, B[t]->d, npad, Ks[t], B[t]->ld, kOzBN));
+    J.ea = A[t]->e;
+    J.eb = B[t]->e;
+    J.part = part + off[t];
+    J.M = Ms[t];
+    J.K = Ks[t];
+    J.tiles = tiles[t];
+    J.ngroups = ngroups;
+    J.splits = splits[t];
+    J.kchunk = kchunk[t];
+    J.Mpad = tiles[t] * kOzBM;
+    J.npad = npad;
+  }
+  double* scal = nullptr;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  jobs.blocks0 = tiles[0] * ngroups * splits[0];
+  jobs.N = b;
+  jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
+  const int blocks = jobs.blocks0 + tiles[1] * ngroups * splits[1];
+  const int bytes = (int)oz_smem_bytes();
+  BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  oz_kernel<<<blocks, kOzThreads, bytes, s>>>(jobs);
+  BLWS_CHECK_LAUNCH(ctx);
+  for (int t = 0; t < 2; ++t) {
+    const size_t tot = (size_t)Ms[t] * b;
+    oz_reduce<<<std::min(ceil_div((long long)tot, 256), ctx->sms * 8), 256, 0, s>>>(
+        Ms[t], b, npad, splits[t], jobs.job[t].Mpad, jobs.job[t].part, A[t]->e, B[t]->e,
+        P + (t ? m : 0), ldp);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
+  return BLWS_OK;
+}
+
+}  // namespace blws

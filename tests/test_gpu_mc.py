@@ -113,3 +113,31 @@ def test_full_size_config3(ctx, torch_mod):
     assert info["status"] == 0 and info["residual"] <= 1e-4
     assert info["rank"] == 50
     assert factored_relerr(U, th, V, P["ML"], P["MR"]) < 5e-4
+
+
+def test_sparse_product_with_a_prebuilt_mirror(ctx, torch_mod):
+    # the CSC mirror from blws_csc_mirror gives the same product as the mirror
+    # the call builds itself, and both equal the dense product with S
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    P = syn.mc_problem(257, 190, 5, 0.2, seed=4)
+    m, n = 257, 190
+    rp, ci, va = (torch.from_numpy(P["rowptr"]).cuda(), torch.from_numpy(P["cols"]).cuda(),
+                  torch.from_numpy(P["vals"]).cuda())
+    X = blws.colmajor(torch.randn(m + n, 13, dtype=torch.float64, device="cuda"))
+    mirror = ctx.csc_mirror(m, n, rp, ci)
+    P1 = ctx.apply_sparse(m, n, rp, ci, va, X)
+    P2 = ctx.apply_sparse(m, n, rp, ci, va, X, mirror=mirror)
+    torch.cuda.synchronize()
+    assert torch.equal(P1, P2)
+    S = np.zeros((m, n))
+    S[P["rows"], P["cols"]] = P["vals"]
+    Xh = X.cpu().numpy()
+    ref = np.vstack([S @ Xh[m:], S.T @ Xh[:m]])
+    assert np.linalg.norm(P2.cpu().numpy() - ref) / np.linalg.norm(ref) < 1e-13
+    # the mirror itself: columns' rows increasing, perm maps back to the CSR entries
+    cp, ri, pm = (t.cpu().numpy() for t in mirror)
+    for j in range(n):
+        seg = ri[cp[j]:cp[j + 1]]
+        assert np.all(np.diff(seg) > 0)
+        assert np.all(P["cols"][pm[cp[j]:cp[j + 1]]] == j)
