@@ -2,6 +2,8 @@
 #include <stdarg.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <new>
 
@@ -101,6 +103,7 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   if (!ctx) return BLWS_ENOMEM;
   ctx->cfg = c;
   ctx->device = c.device;
+  if (const char* ev = std::getenv("BLWS_EIG")) ctx->eig_route = std::strcmp(ev, "jacobi") == 0 ? 1 : 0;
   blws_status st = bind_device(ctx);
   cudaDeviceProp prop;
   if (st == BLWS_OK && cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) st = BLWS_ECUDA;

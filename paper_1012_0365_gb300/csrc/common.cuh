@@ -65,6 +65,8 @@ enum Buf {
   BUF_TC_X,      // mixed precision: TF32 planes of the block X
   BUF_TC_PART,   // mixed precision: split-K partial sums (FP32)
   BUF_OZ_E,      // FP64-equivalent tensor-core products: scale exponents
+  BUF_TRI,       // eigen-solver: tridiagonal-route scratch (FP32)
+  BUF_EIG_GRP,   // eigen-solver: sorted group ids of the tridiagonal route
   BUF_COUNT_
 };
 
@@ -86,9 +88,13 @@ struct Ctx {
   // kernel (process-wide, per device), not to a context: it only ever grows,
   // under a lock, so that contexts on other threads never lower it under a
   // launch that needs more (defined in capi.cu).
-  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_COUNT_ };
+  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_TRI, ATTR_TRI_INV, ATTR_COUNT_ };
   blws_status smem_limit(SmemAttr which, const void* func, int bytes);
   int jacobi_block_per_sm = 0;  // occupancy of the block Jacobi kernel (queried once)
+  // FP32 eigen stage: 0 the tridiagonal route where it applies, 1 Jacobi only
+  // (environment BLWS_EIG=jacobi at context creation)
+  int eig_route = 0;
+  unsigned long long tri_fallbacks = 0;  // tridiagonal stage results replaced by Jacobi
   template <typename T>
   blws_status get(Buf b, size_t count, T** out) {
     void* p = nullptr;
@@ -109,6 +115,7 @@ enum Slot {
   SLOT_NNZ = 6,        // unsigned long long counter
   SLOT_AUX2 = 7,
   SLOT_TCERR = 8,      // int: a tensor-core kernel's bounded wait ran out
+  SLOT_TRIFAIL = 9,    // int: the tridiagonal route met a group it cannot orthonormalise
   SLOT_MAX = 16
 };
 

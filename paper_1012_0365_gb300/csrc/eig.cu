@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "ops.cuh"
@@ -420,14 +421,17 @@ __global__ void identity_minus(int n, double* R) {
 }
 
 // partial sums (per CTA): [0] sum_{i!=j} S_ij^2, [1] sum R_ij^2, [2] sum T_ij^2
+// Off-diagonal entries inside a group of the FP32 stage (grp, may be null)
+// are left out: the group's columns span its eigenspace without being
+// eigenvectors one by one, and the refinement keeps them as one subspace.
 __global__ void oa_norms_partial(int n, const double* __restrict__ S, const double* __restrict__ R,
-                                 const double* __restrict__ T, double* part) {
+                                 const double* __restrict__ T, const int* __restrict__ grp, double* part) {
   __shared__ double red[3][256];
   double a = 0.0, b = 0.0, c = 0.0;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
        e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
-    if (i != j) a = fma(S[e], S[e], a);
+    if (i != j && !(grp && grp[i] >= 0 && grp[i] == grp[j])) a = fma(S[e], S[e], a);
     b = fma(R[e], R[e], b);
     c = fma(T[e], T[e], c);
   }
@@ -481,14 +485,14 @@ __global__ void oa_lambda(int n, int nparts, const double* __restrict__ S, const
 
 __global__ void oa_correction(int n, const double* __restrict__ S, const double* __restrict__ R,
                               const double* __restrict__ lam, const double* __restrict__ delta,
-                              double* E) {
+                              const int* __restrict__ grp, double* E) {
   const double d = *delta;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
        e += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(e % n), j = (int)(e / n);
     const double rij = R[e];
     double v;
-    if (i == j) {
+    if (i == j || (grp && grp[i] >= 0 && grp[i] == grp[j])) {
       v = 0.5 * rij;
     } else {
       const double gap = lam[j] - lam[i];
@@ -500,7 +504,8 @@ __global__ void oa_correction(int n, const double* __restrict__ S, const double*
 
 // rank of each eigenvalue in decreasing order (ties by index), then scatter
 __global__ void sort_desc(int n, const double* __restrict__ lam_in, const double* __restrict__ X,
-                          double* lam_out, double* Z) {
+                          const int* __restrict__ grp_in, const float* __restrict__ gtop_in, double* lam_out,
+                          double* Z, int* grp_out) {
   for (int i = blockIdx.x; i < n; i += gridDim.x) {
     __shared__ int cnt;
     if (threadIdx.x == 0) cnt = 0;
@@ -514,7 +519,13 @@ __global__ void sort_desc(int n, const double* __restrict__ lam_in, const double
     atomicAdd(&cnt, c);  // integer count: order-independent
     __syncthreads();
     const int rank = cnt;
-    if (threadIdx.x == 0) lam_out[rank] = li;
+    if (threadIdx.x == 0) {
+      lam_out[rank] = li;
+      if (grp_out) {  // group id, then the group's top eigenvalue (n ints, n floats)
+        grp_out[rank] = grp_in ? grp_in[i] : -1;
+        reinterpret_cast<float*>(grp_out + n)[rank] = gtop_in ? gtop_in[i] : 0.0f;
+      }
+    }
     for (int x = threadIdx.x; x < n; x += blockDim.x) Z[x + (size_t)rank * n] = X[x + (size_t)i * n];
     __syncthreads();
   }
@@ -525,8 +536,13 @@ __global__ void sort_desc(int n, const double* __restrict__ lam_in, const double
 // One level: FP32 Jacobi, FP64 refinement, sort.  *delta_dev receives the
 // refinement's cluster width d (pairs closer than d are not resolved).
 blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
-                          double* delta_out, bool sorted = true) {
+                          double* delta_out, bool sorted = true, int* tri_fail = nullptr,
+                          int* grp_sorted = nullptr) {
   if (n <= 0) return BLWS_OK;
+  // FP32 stage: the tridiagonal route (tri_eig.cu) where the packed matrix fits
+  // one CTA; otherwise, and for the block-diagonal second level (whose columns
+  // must stay inside their blocks), Jacobi
+  const bool tri = tri_fail != nullptr && n >= 3 && n <= kTriMaxN;
   const bool small = n + (n & 1) <= kCtaMaxN;
   // padded size: even for the one-CTA solver; an even number of kBS blocks otherwise
   const int N = small ? n + (n & 1) : ceil_div(n, 2 * kBS) * 2 * kBS;
@@ -548,8 +564,13 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
   double* part = lam_u + n;
   double* delta = part + 3 * 1024;
   int* sweeps = reinterpret_cast<int*>(delta + 8);
+  int* grp = reinterpret_cast<int*>(delta + 16);  // groups of the tridiagonal stage (n ints)
+  float* gtop = reinterpret_cast<float*>(grp + n);  // their largest eigenvalues (n floats)
 
-  if (small) {
+  if (tri_fail && !tri) BLWS_TRY_CUDA(ctx, cudaMemsetAsync(tri_fail, 0, sizeof(int), s));
+  if (tri) {
+    BLWS_TRY(tri_stage(ctx, s, n, T, X, grp, gtop, tri_fail));
+  } else if (small) {
     const size_t smem = 2ull * N * N * sizeof(float);
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_JACOBI_CTA, (const void*)jacobi_cta_kernel, (int)smem));
     jacobi_cta_kernel<<<1, 1024, smem, s>>>(n, N, T, V, sweeps);
@@ -576,8 +597,10 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
     ++ctx->launches;
   }
   const int eb = std::min(ceil_div((long long)n * n, 256), ctx->sms * 4);
-  f32_to_f64_block<<<eb, 256, 0, s>>>(n, N, V, X);
-  BLWS_CHECK_LAUNCH(ctx);
+  if (!tri) {
+    f32_to_f64_block<<<eb, 256, 0, s>>>(n, N, V, X);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
   const int nparts = std::min(eb, 1024);
   for (int step = 0; step < kRefineSteps; ++step) {
     BLWS_TRY(gemm(ctx, s, true, false, n, n, n, 1.0, X, n, X, n, 0.0, R, n));
@@ -585,18 +608,19 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
     BLWS_CHECK_LAUNCH(ctx);
     BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, T, n, X, n, 0.0, TX, n));
     BLWS_TRY(gemm(ctx, s, true, false, n, n, n, 1.0, X, n, TX, n, 0.0, S, n));
-    oa_norms_partial<<<nparts, 256, 0, s>>>(n, S, R, T, part);
+    oa_norms_partial<<<nparts, 256, 0, s>>>(n, S, R, T, tri ? grp : nullptr, part);
     BLWS_CHECK_LAUNCH(ctx);
     oa_lambda<<<1, 256, 0, s>>>(n, nparts, S, R, part, lam_u, delta);
     BLWS_CHECK_LAUNCH(ctx);
-    oa_correction<<<eb, 256, 0, s>>>(n, S, R, lam_u, delta, E);
+    oa_correction<<<eb, 256, 0, s>>>(n, S, R, lam_u, delta, tri ? grp : nullptr, E);
     BLWS_CHECK_LAUNCH(ctx);
     BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(X2, X, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, s));
     BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, X, n, E, n, 1.0, X2, n));
     std::swap(X, X2);
   }
   if (sorted) {
-    sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, lam, Z);
+    sort_desc<<<std::min(n, ctx->sms * 4), 128, 0, s>>>(n, lam_u, X, tri ? grp : nullptr, tri ? gtop : nullptr,
+                                                        lam, Z, grp_sorted);
     BLWS_CHECK_LAUNCH(ctx);
   } else {
     BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(lam, lam_u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
@@ -638,7 +662,11 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   if (n <= 0) return BLWS_OK;
   double* scal;
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
-  BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2));
+  const bool tri_enabled = ctx->eig_route != 1;
+  int* dgrp = nullptr;  // sorted group ids and group tops of the tridiagonal stage (n ints, n floats)
+  BLWS_TRY(ctx->get(BUF_EIG_GRP, (size_t)2 * n, &dgrp));
+  BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2, true,
+                         tri_enabled ? reinterpret_cast<int*>(scal + SLOT_TRIFAIL) : nullptr, dgrp));
   // Second level for clusters: eigenvalues closer than the refinement width d
   // are only resolved as a joint subspace, with values accurate to ~d (the
   // FP32 stage's absolute accuracy, ~1e-7 ||T||).  Where that could change
@@ -647,20 +675,45 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   // the same two-stage solver resolves it to ~1e-7 of the cluster's width.
   double* h = ctx->host_pinned;
   std::vector<double> hl(n);
+  std::vector<int> hg(2 * (size_t)n);
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hg.data(), dgrp, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 32, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 33, scal + SLOT_TRIFAIL, sizeof(double), cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  if (tri_enabled && (*reinterpret_cast<const int*>(h + 33) != 0 || !std::isfinite(h[32]))) {
+    // the FP32 tridiagonal stage met a group it could not orthonormalise or a
+    // solve it could not normalise: Jacobi instead
+    ++ctx->tri_fallbacks;
+    BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2, true, nullptr, dgrp));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hg.data(), dgrp, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 32, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  }
   const double d = h[32];
   if (!(d > 0.0)) return BLWS_OK;
-  // clusters (runs of sorted values closer than d) that reach above eps - 3d
+  // Clusters: runs of sorted values closer than d, joined with the groups of
+  // the tridiagonal stage (whose columns are a basis of the group's
+  // eigenspace and whose values are Rayleigh quotients inside the group's
+  // range, so a group is contiguous in sorted order).  A group's values can
+  // sit below its largest eigenvalue: its top from the FP32 stage, widened
+  // by 1e-5 ||T|| (the FP32 stage's accuracy with room to spare), bounds it.
+  // A cluster is solved again when it can reach above eps - 3d.
+  const double tnorm = std::max(std::fabs(hl[0]), std::fabs(hl[n - 1]));
+  const float* htop = reinterpret_cast<const float*>(hg.data() + n);
   struct Cl { int i, j; double mu, scale; };
   std::vector<Cl> cl;
   int n2 = 0;
   for (int i = 0; i < n;) {
     int j = i + 1;
-    while (j < n && hl[j - 1] - hl[j] <= d) ++j;
-    if (j - i >= 2 && hl[i] > eps - 3.0 * d) {
-      cl.push_back({i, j, 0.5 * (hl[i] + hl[j - 1]), 0.5 * (hl[i] - hl[j - 1]) + d});
+    while (j < n && (hl[j - 1] - hl[j] <= d || (hg[j] >= 0 && hg[j] == hg[j - 1]))) ++j;
+    double top = hl[i];
+    for (int t = i; t < j; ++t)
+      if (hg[t] >= 0) top = std::max(top, (double)htop[t] + 1e-5 * tnorm);
+    const double hidden = top - hl[i];
+    if (j - i >= 2 && top > eps - 3.0 * d) {
+      cl.push_back({i, j, 0.5 * (hl[i] + hl[j - 1]), 0.5 * (hl[i] - hl[j - 1]) + d + hidden});
       n2 += j - i;
     }
     i = j;

@@ -29,6 +29,22 @@ blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, i
 blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
                     double eps);
 
+// FP32 eigenvectors of T (n x n FP64, symmetric) by the tridiagonal route
+// (tri_eig.cu): X (n x n FP64, ld n) receives them, columns in increasing
+// order of eigenvalue, with FP32 accuracy.  Eigenvalues closer than
+// kTriGroupTol ||T|| to a neighbour form a group whose columns are an
+// orthonormal basis of the group's joint eigenspace, not eigenvectors one by
+// one: grp[j] (device, n ints) is the group's first column, or -1 for a
+// column alone, and gtop[j] (device, n floats) the group's largest
+// eigenvalue as the FP32 stage found it (within ~1e-6 ||T||).  *fail
+// (device int) is set when a group could not be orthonormalised or a solve
+// normalised (X is then not to be used).  n <= kTriMaxN (the packed lower
+// triangle fills one CTA's shared memory).
+constexpr int kTriMaxN = 336;
+constexpr float kTriGroupTol = 1e-4f;
+blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,
+                      int* fail);
+
 // CholeskyQR2 with column equilibration and deflation: on return X (N x b,
 // ld) holds an orthonormal basis of span(R) with dead columns zeroed and
 // B (b x b upper, ld b) satisfies R = X B (dead rows zero).  R is destroyed.

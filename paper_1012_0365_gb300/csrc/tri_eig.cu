@@ -1,0 +1,760 @@
+// FP32 first stage of the eigen-decomposition of T_k (Algorithm 3, "EVD of
+// T_k") by the tridiagonal route (Golub & Van Loan, Sections 8.3-8.4):
+//   1. Householder tridiagonalisation Q^T T Q = tridiag(d, e): one CTA, the
+//      lower triangle of T packed in shared memory (FP32), one reflector per
+//      column; each step's symmetric rank-2 update is applied in the same
+//      pass over the trailing triangle as the next step's matrix-vector
+//      product;
+//   2. every eigenvalue of the tridiagonal matrix by multisection on Sturm
+//      counts (one warp per eigenvalue, 32 probes per step);
+//   3. eigenvectors by inverse iteration (Wilkinson), each eigenvalue its own
+//      shift, from a hashed random start, two solves (one warp per
+//      eigenvalue, the substitutions in FP64 so that a chain of small
+//      pivots cannot overflow).  Eigenvalues closer than kGroupTol ||T|| form
+//      a group whose vectors are orthonormalised together by CholeskyQR2
+//      after each solve, so a tight cluster still comes out as an
+//      orthonormal basis of its joint eigenspace;
+//   4. back-transformation Z = Q Y with the reflectors gathered eight at a
+//      time in compact WY form (Schreiber & Van Loan), written out in FP64.
+// The result has FP32 accuracy (residual and orthogonality ~1e-6) and is the
+// starting point of the FP64 Ogita-Aishima refinement in eig.cu.  Every
+// reduction has a fixed order: the stage is deterministic.
+#include <algorithm>
+
+#include "ops.cuh"
+
+namespace blws {
+
+namespace {
+
+constexpr int kTriThreads = 1024;
+constexpr int kQrThreads = 512;
+constexpr float kGroupTol = kTriGroupTol;
+constexpr float kInvPert = 1.2e-7f;  // inverse iteration: pivots kept >= this x ||T||
+constexpr int kQrSmemFloats = 56 * 1024;  // group kernel: shared-memory budget (floats)
+constexpr float kPivMin = 1e-30f;    // Sturm counts: pivots kept away from zero by this (T scaled to <= 1)
+
+// packed lower triangle, column-major: element (i, j), i >= j
+__device__ __forceinline__ int pk(int n, int i, int j) { return j * n - (j * (j - 1)) / 2 + (i - j); }
+
+// sum over the CTA, returned to every thread (fixed order)
+__device__ float block_sum(float v, float* red) {
+  __syncthreads();  // red may still be read from the previous call
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float s = 0.0f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;
+}
+
+// ------------------------------------------------- 1. tridiagonalisation --
+// T (n x n FP64, ld n, symmetric; its lower triangle is read) is scaled by a
+// power of two to max |T_ij| in [0.5, 1).  Reflector k, H_k = I - tau_k v v^T
+// with v_{k+1} = 1, is stored in V(:, k) (zeros above row k + 1).
+//
+// Step k: (1) column k receives the rank-2 update left pending by step k-1
+// (one warp), which gives alpha, sigma and the diagonal; (2) the reflector;
+// (3) one pass over the trailing triangle (rows and columns > k) applies the
+// pending update to every element and forms p = A22 v in the same loads, in
+// items of 32 columns x 64 rows (one warp each): lane i holds two rows; for
+// each column it adds A(r, c) v_c to its rows' sums (the part left of the
+// diagonal) and A(r, c) v_r to a per-column sum (the part on and below it),
+// which a 31-shuffle reduce-scatter hands to lane c.  Lanes read consecutive
+// rows of one column: no bank conflicts.  The partial sums go to a small
+// global scratch (L1-resident) and are added per row in a fixed order;
+// (4) K = tau p^T v / 2 and w = p - K v become the next pending update.
+constexpr int kItemCols = 32, kItemRows = 64;
+constexpr int kMaxGroups = (kTriMaxN + kItemCols - 1) / kItemCols;
+constexpr int kMaxChunks = (kTriMaxN + kItemRows - 1) / kItemRows;
+
+__global__ void __launch_bounds__(kTriThreads)
+tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
+                  float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ part,
+                  float* __restrict__ tscale) {
+  extern __shared__ float sm[];
+  __shared__ float red[32];
+  __shared__ double redd[32];
+  __shared__ float col[3];  // alpha, sigma and the diagonal entry of the current column
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int np = n * (n + 1) / 2;
+  float* A = sm;        // packed lower triangle
+  float* pv = A + np;   // pending update A -= pv pw^T + pw pv^T (global row index)
+  float* pw = pv + n;
+  float* vk = pw + n;   // this step's reflector (global row index)
+  float* Lp = part;                     // [group][row]: sums left of the diagonal
+  float* Up = part + kMaxGroups * n;    // [chunk][column]: sums on and below the diagonal
+  // scale: largest |T_ij| over the lower triangle (a warp per column)
+  double mx = 0.0;
+  for (int j = wid; j < n; j += nw) {
+#pragma unroll 4
+    for (int i = j + lane; i < n; i += 32) mx = fmax(mx, fabs(T[i + (size_t)j * n]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) redd[wid] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < nw; ++w) mx = fmax(mx, redd[w]);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  const double scale = ldexp(1.0, -ex);
+  if (tid == 0) *tscale = (float)ldexp(1.0, ex);  // T = 2^ex x the scaled matrix
+  for (int j = wid; j < n; j += nw) {
+    const int base = pk(n, j, j) - j;
+#pragma unroll 4
+    for (int i = j + lane; i < n; i += 32) A[base + i] = (float)(T[i + (size_t)j * n] * scale);
+  }
+  for (int t = tid; t < n; t += nt) {
+    pv[t] = 0.0f;
+    pw[t] = 0.0f;
+  }
+  __syncthreads();
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // trailing rows k+1 .. n-1 (local 0 .. m-1)
+    // (1) column k
+    if (wid == 0) {
+      const int base = pk(n, k, k) - k;  // + r: A(r, k), r >= k
+      const float pvk = pv[k], pwk = pw[k];
+      float ssq = 0.0f;
+      for (int r = k + lane; r < n; r += 32) {
+        const float a = A[base + r] - fmaf(pv[r], pwk, pw[r] * pvk);
+        A[base + r] = a;
+        if (r >= k + 2) ssq = fmaf(a, a, ssq);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+      __syncwarp();
+      if (lane == 0) {
+        col[0] = A[base + k + 1];
+        col[1] = ssq;
+        col[2] = A[base + k];
+      }
+    }
+    __syncthreads();
+    // (2) reflector: H x = beta e_1 (same scalars in every thread)
+    const float alpha = col[0], sigma = col[1];
+    float tau = 0.0f, beta = alpha, vscale = 0.0f;
+    if (sigma > 0.0f) {
+      const float nrm = sqrtf(fmaf(alpha, alpha, sigma));
+      beta = alpha >= 0.0f ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      vscale = 1.0f / (alpha - beta);
+    }
+    if (tid == 0) {
+      dv[k] = col[2];
+      ev[k] = beta;
+      tauv[k] = tau;
+    }
+    const int c0 = pk(n, k + 1, k);  // A(k+1, k)
+    for (int t = tid; t < n; t += nt) {
+      float v = 0.0f;
+      if (t == k + 1) v = 1.0f;
+      else if (t > k + 1 && tau != 0.0f) v = A[c0 + (t - k - 1)] * vscale;
+      V[t + (size_t)k * n] = v;
+      vk[t] = v;
+    }
+    __syncthreads();
+    // (3) pending update and product, one pass
+    const int G = (m + kItemCols - 1) / kItemCols, H = (m + kItemRows - 1) / kItemRows;
+    for (int it = wid; it < G * H; it += nw) {
+      const int g = it % G, h = it / G;
+      const int cb = g * kItemCols, rb = h * kItemRows;
+      if (rb + kItemRows - 1 < cb) continue;  // above the diagonal
+      const int r0 = rb + lane, r1 = r0 + 32;
+      const int R0 = k + 1 + r0, R1 = k + 1 + r1;
+      const float pv0 = r0 < m ? pv[R0] : 0.0f, pw0 = r0 < m ? pw[R0] : 0.0f, v0 = r0 < m ? vk[R0] : 0.0f;
+      const float pv1 = r1 < m ? pv[R1] : 0.0f, pw1 = r1 < m ? pw[R1] : 0.0f, v1 = r1 < m ? vk[R1] : 0.0f;
+      float l0 = 0.0f, l1 = 0.0f, acc[32];
+      int base = pk(n, k + 1 + cb, k + 1 + cb) - cb;  // + r: A(k+1+r, k+1+c)
+      if (rb >= cb + kItemCols && rb + kItemRows <= m && cb + kItemCols <= m) {
+        // every element present and left of the diagonal
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int C = k + 1 + cb + j;
+          const float pvc = pv[C], pwc = pw[C], vc = vk[C];
+          const float a0 = fmaf(-pw0, pvc, fmaf(-pv0, pwc, A[base + r0]));
+          const float a1 = fmaf(-pw1, pvc, fmaf(-pv1, pwc, A[base + r1]));
+          A[base + r0] = a0;
+          A[base + r1] = a1;
+          l0 = fmaf(a0, vc, l0);
+          l1 = fmaf(a1, vc, l1);
+          acc[j] = fmaf(a0, v0, a1 * v1);
+          base += n - C - 1;
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = cb + j, C = k + 1 + c;
+          float a0 = 0.0f, a1 = 0.0f, vc = 0.0f;
+          if (c < m) {
+            const float pvc = pv[C], pwc = pw[C];
+            vc = vk[C];
+            if (r0 >= c && r0 < m) {
+              a0 = fmaf(-pw0, pvc, fmaf(-pv0, pwc, A[base + r0]));
+              A[base + r0] = a0;
+            }
+            if (r1 >= c && r1 < m) {
+              a1 = fmaf(-pw1, pvc, fmaf(-pv1, pwc, A[base + r1]));
+              A[base + r1] = a1;
+            }
+          }
+          if (r0 > c) l0 = fmaf(a0, vc, l0);
+          if (r1 > c) l1 = fmaf(a1, vc, l1);
+          acc[j] = fmaf(a0, v0, a1 * v1);
+          base += n - C - 1;
+        }
+      }
+      // reduce-scatter over the lanes: lane j ends with the sum of acc[j]
+#pragma unroll
+      for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool up = (lane & sft) != 0;
+#pragma unroll
+        for (int q = 0; q < sft; ++q) {
+          const float send = up ? acc[q] : acc[q + sft];
+          const float keep = up ? acc[q + sft] : acc[q];
+          acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+        }
+      }
+      if (cb + lane < m) Up[h * n + cb + lane] = acc[0];
+      if (r0 < m) Lp[g * n + r0] = l0;
+      if (r1 < m) Lp[g * n + r1] = l1;
+    }
+    __syncthreads();
+    // (4) p = tau A22 v, K, w: the next pending update
+    float p = 0.0f, pvv = 0.0f;
+    if (tid < m) {
+      const int r = tid, gr = r / kItemCols;
+      float lv[kMaxGroups], uv[kMaxChunks];  // independent loads, then a fixed-order sum
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g) lv[g] = g <= gr ? Lp[g * n + r] : 0.0f;
+#pragma unroll
+      for (int h = 0; h < kMaxChunks; ++h)
+        uv[h] = (h < H && h * kItemRows + kItemRows - 1 >= gr * kItemCols) ? Up[h * n + r] : 0.0f;
+      float sl = 0.0f, su = 0.0f;
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g) sl += lv[g];
+#pragma unroll
+      for (int h = 0; h < kMaxChunks; ++h) su += uv[h];
+      p = tau * (sl + su);
+      pvv = p * vk[k + 1 + r];
+    }
+    const float K = 0.5f * tau * block_sum(pvv, red);
+    if (tid < m) {
+      const int R = k + 1 + tid;
+      pw[R] = p - K * vk[R];
+      pv[R] = vk[R];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (n >= 2) {  // the last 2 x 2 block receives the last pending update
+      const int a = n - 2, b = n - 1;
+      const float daa = A[pk(n, a, a)] - 2.0f * pv[a] * pw[a];
+      const float dba = A[pk(n, b, a)] - fmaf(pv[b], pw[a], pw[b] * pv[a]);
+      const float dbb = A[pk(n, b, b)] - 2.0f * pv[b] * pw[b];
+      dv[a] = daa;
+      ev[a] = dba;
+      dv[b] = dbb;
+      tauv[a] = 0.0f;
+    } else {
+      dv[0] = A[0];
+    }
+  }
+}
+
+// ------------------------------------------------------ 2. eigenvalues --
+// lam[j] = the (j+1)-th smallest eigenvalue of tridiag(d, e), one warp each.
+__device__ __forceinline__ int sturm_count(int n, const float* sd, const float* se2, float x) {
+  float q = sd[0] - x;
+  if (fabsf(q) <= kPivMin) q = -kPivMin;
+  int c = q < 0.0f;
+  for (int i = 1; i < n; ++i) {
+    q = (sd[i] - x) - __fdividef(se2[i - 1], q);
+    if (fabsf(q) <= kPivMin) q = -kPivMin;
+    c += q < 0.0f;
+  }
+  return c;
+}
+
+__global__ void __launch_bounds__(256)
+tri_bisect_kernel(int n, const float* __restrict__ dv, const float* __restrict__ ev, float* __restrict__ lam) {
+  __shared__ float sd[kTriMaxN], se2[kTriMaxN];
+  __shared__ float rlo[8], rhi[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  float lo = 3.0e38f, hi = -3.0e38f;
+  for (int i = tid; i < n; i += blockDim.x) {
+    const float d = dv[i];
+    const float el = i > 0 ? fabsf(ev[i - 1]) : 0.0f, er = i + 1 < n ? fabsf(ev[i]) : 0.0f;
+    sd[i] = d;
+    if (i + 1 < n) se2[i] = ev[i] * ev[i];
+    lo = fminf(lo, d - el - er);
+    hi = fmaxf(hi, d + el + er);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (lane == 0) {
+    rlo[wid] = lo;
+    rhi[wid] = hi;
+  }
+  __syncthreads();
+  lo = rlo[0];
+  hi = rhi[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+    lo = fminf(lo, rlo[w]);
+    hi = fmaxf(hi, rhi[w]);
+  }
+  const float tn = fmaxf(fabsf(lo), fabsf(hi));
+  const float tol = 2.4e-7f * tn + kPivMin;
+  lo -= 1e-6f * tn + kPivMin;  // count(lo) = 0 and count(hi) = n
+  hi += 1e-6f * tn + kPivMin;
+  const int j = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (j >= n) return;
+  for (int it = 0; it < 12 && hi - lo > tol; ++it) {
+    const float x = lo + (hi - lo) * (float)(lane + 1) * (1.0f / 33.0f);
+    const unsigned below = __ballot_sync(0xffffffffu, sturm_count(n, sd, se2, x) <= j);
+    const int f = __ffs(~below) - 1;  // first probe with more than j eigenvalues below it (-1: none)
+    const float xl = __shfl_sync(0xffffffffu, x, f > 0 ? f - 1 : 31);
+    const float xh = __shfl_sync(0xffffffffu, x, f >= 0 ? f : 31);
+    if (f != 0) lo = xl;           // lanes before f all have count <= j
+    if (f >= 0) hi = xh;
+  }
+  if (lane == 0) lam[j] = 0.5f * (lo + hi);
+}
+
+// ----------------------------------------------- 3. inverse iteration --
+__device__ __forceinline__ float hash_uniform(uint32_t col, uint32_t row) {
+  // integer hash (xorshift-multiply finaliser) of (col, row) to [-1, 1)
+  uint32_t x = col * 0x9E3779B1u ^ (row + 0x632BE5ABu) * 0x85EBCA77u;
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return (float)(x >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+
+// One warp per eigenvalue g.  First call: the group of g (grp[g]: its first
+// column for groups of two or more, else -1; gtop[g]: the group's largest
+// eigenvalue from the multisection, in T's units), the LU factorisation with
+// partial pivoting of tridiag(d, e) - lam_g I (F, kept for the second call)
+// and a hashed random start; second call: F and the start from Y.  Lane 0
+// runs the substitutions from shared memory.  A chain of small pivots can
+// grow the solution past the FP32 range: whenever an entry exceeds 2^100 the
+// running values are scaled by 2^-100 and the row is recorded, and the
+// entries computed before it are scaled down with the normalisation.  Y(r, g)
+// at r * n + g receives the normalised solution; a solution that cannot be
+// normalised (too many rescalings, a non-finite entry, zero) sets *fail.
+constexpr int kMaxRescale = 8;
+constexpr float kRescaleAt = 1.2676506e30f;  // 2^100
+constexpr float kRescaleBy = 7.888609e-31f;  // 2^-100
+
+template <bool kFirst>
+__global__ void __launch_bounds__(32)
+tri_solve_kernel(int n, const float* __restrict__ dv, const float* __restrict__ ev,
+                 const float* __restrict__ lam, const float* __restrict__ tscale, float4* __restrict__ F,
+                 float* __restrict__ Y, int* __restrict__ grp, float* __restrict__ gtop, int* fail) {
+  extern __shared__ float4 smf[];
+  float4* sF = smf;                                // n
+  float* sy = reinterpret_cast<float*>(sF + n);    // right-hand side, then solution (n)
+  float* sb = sy + n;                              // after the forward elimination (n)
+  float* sd = sb + n;                              // d, e (first call)
+  float* se = sd + n;
+  __shared__ int nres, rrow[kMaxRescale];
+  const int g = blockIdx.x, lane = threadIdx.x;
+  const float tn = fmaxf(fabsf(lam[0]), fabsf(lam[n - 1]));
+  const float pmin = fmaxf(kInvPert * tn, kPivMin);
+  if (kFirst) {
+#pragma unroll 4
+    for (int r = lane; r < n; r += 32) {
+      sd[r] = dv[r];
+      se[r] = r + 1 < n ? ev[r] : 0.0f;
+      sy[r] = hash_uniform((uint32_t)g, (uint32_t)r);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const float gtol = kGroupTol * tn;
+      int i = g, j = g + 1;
+      while (i > 0 && lam[i] - lam[i - 1] < gtol) --i;
+      while (j < n && lam[j] - lam[j - 1] < gtol) ++j;
+      grp[g] = j - i >= 2 ? i : -1;
+      gtop[g] = lam[j - 1] * *tscale;  // largest eigenvalue of the group (FP32 estimate, T's units)
+      const float x = lam[g];
+      float al = sd[0] - x, be = se[0];  // pending row k: (k, k) and (k, k+1)
+      for (int k = 0; k + 1 < n; ++k) {
+        const float ck = se[k], ak1 = sd[k + 1] - x, bk1 = se[k + 1];
+        float u1, u2, u3, lk;
+        uint32_t sw;
+        if (fabsf(al) >= fabsf(ck)) {  // keep row k
+          u1 = al; u2 = be; u3 = 0.0f; sw = 0u;
+          if (fabsf(u1) < pmin) u1 = u1 < 0.0f ? -pmin : pmin;
+          const float ru = __frcp_rn(u1);
+          lk = ck * ru;
+          al = fmaf(-lk, be, ak1);
+          be = bk1;
+          u1 = ru;
+        } else {                       // interchange rows k and k+1
+          u2 = ak1; u3 = bk1; sw = 1u;
+          const float rc = __frcp_rn(ck);
+          lk = al * rc;
+          al = fmaf(-lk, ak1, be);
+          be = -lk * bk1;
+          u1 = fabsf(ck) < pmin ? __frcp_rn(ck < 0.0f ? -pmin : pmin) : rc;
+        }
+        // stored: 1/U(k,k), U(k,k+1), U(k,k+2), multiplier whose last mantissa
+        // bit carries the interchange (a one-ulp change, immaterial here)
+        sF[k] = make_float4(u1, u2, u3, __uint_as_float((__float_as_uint(lk) & ~1u) | sw));
+      }
+      if (fabsf(al) < pmin) al = al < 0.0f ? -pmin : pmin;
+      sF[n - 1] = make_float4(__frcp_rn(al), 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp();
+    for (int k = lane; k < n; k += 32) F[(size_t)k * n + g] = sF[k];
+  } else {
+    if (*fail) return;
+#pragma unroll 4
+    for (int k = lane; k < n; k += 32) {
+      sF[k] = F[(size_t)k * n + g];
+      sy[k] = Y[(size_t)k * n + g];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    float yk = sy[0];
+    for (int k = 0; k + 1 < n; ++k) {  // L^{-1} P y
+      const float4 f = sF[k];
+      float yk1 = sy[k + 1];
+      if (__float_as_uint(f.w) & 1u) {
+        const float t = yk;
+        yk = yk1;
+        yk1 = t;
+      }
+      yk1 = fmaf(-f.w, yk, yk1);
+      sb[k] = yk;
+      yk = yk1;
+    }
+    int nr = 0;
+    float x1 = yk * sF[n - 1].x, x2 = 0.0f;  // U x = y
+    if (fabsf(x1) > kRescaleAt) {
+      x1 *= kRescaleBy;  // nothing computed before it
+    }
+    sy[n - 1] = x1;
+    for (int k = n - 2; k >= 0; --k) {
+      const float4 f = sF[k];
+      float xk = fmaf(-f.z, x2, fmaf(-f.y, x1, sb[k])) * f.x;
+      if (fabsf(xk) > kRescaleAt) {
+        xk *= kRescaleBy;
+        x1 *= kRescaleBy;
+        x2 *= kRescaleBy;
+        if (nr < kMaxRescale) rrow[nr] = k;
+        ++nr;
+      }
+      sy[k] = xk;
+      x2 = x1;
+      x1 = xk;
+    }
+    nres = nr;
+  }
+  __syncwarp();
+  const int nr = nres;
+  // entries above a rescaled row were computed before it: scale them down
+  float mx = 0.0f;
+  for (int r = lane; r < n; r += 32) {
+    float v = sy[r];
+    for (int e = 0; e < min(nr, kMaxRescale); ++e)
+      if (r > rrow[e]) v *= kRescaleBy;
+    sy[r] = v;
+    mx = fmaxf(mx, fabsf(v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __syncwarp();
+  const bool ok = nr <= kMaxRescale && mx > 0.0f && mx <= 3.0e38f;
+  const float rm = ok ? 1.0f / mx : 0.0f;
+  float ss = 0.0f;
+  for (int r = lane; r < n; r += 32) {
+    const float v = sy[r] * rm;
+    ss = fmaf(v, v, ss);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+  const float inv = ok ? rm * rsqrtf(ss) : 0.0f;
+  if (!ok && lane == 0) *fail = 1;
+  for (int r = lane; r < n; r += 32) Y[(size_t)r * n + g] = sy[r] * inv;
+}
+
+// CholeskyQR2 (FP32) of each group's n x c block of Y, one CTA per group
+// (the CTA of the group's first column; the others return at once).  The
+// block and its Gram matrix are staged in shared memory (sm_floats), the
+// block with an odd leading dimension so that warps reading down a column
+// and threads walking a row both hit distinct banks.  A group too wide for
+// that sets *fail (the matrix then goes to Jacobi).
+__global__ void __launch_bounds__(kQrThreads)
+tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __restrict__ Y, int* fail) {
+  extern __shared__ float smq[];
+  __shared__ float ssc;
+  const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  if (grp[i] != i || *fail) return;
+  int j = i + 1;
+  while (j < n && grp[j] == i) ++j;
+  const int c = j - i;
+  const int lds = c | 1;
+  if ((long long)n * lds + (long long)c * c > sm_floats) {
+    // too wide to stage: the caller falls back to Jacobi for this matrix
+    if (tid == 0) *fail = 1;
+    return;
+  }
+  float* Yb = smq;  // block element (r, a) at Yb[r * lds + a]
+  float* G = smq + (size_t)n * lds;
+  const int ldb = lds;
+  for (int r = wid; r < n; r += nw)
+    for (int a = lane; a < c; a += 32) Yb[r * ldb + a] = Y[(size_t)r * n + i + a];
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    // Gram matrix in 4 x 4 tiles (upper triangle of tiles), a warp per tile,
+    // lanes over rows; mirrored
+    const int t4 = (c + 3) / 4, ntile = t4 * (t4 + 1) / 2;
+    for (int e = wid; e < ntile; e += nw) {
+      int ta = 0, rem = e;  // unrank e -> (ta, tb), ta <= tb
+      while (rem >= t4 - ta) {
+        rem -= t4 - ta;
+        ++ta;
+      }
+      const int tb = ta + rem;
+      float acc[4][4] = {};
+      for (int r = lane; r < n; r += 32) {
+        const float* yr = Yb + (size_t)r * ldb;
+        float ya[4], yb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ya[u] = 4 * ta + u < c ? yr[4 * ta + u] : 0.0f;
+          yb[u] = 4 * tb + u < c ? yr[4 * tb + u] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][q] = fmaf(ya[u], yb[q], acc[u][q]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int a = 4 * ta + u, b = 4 * tb + q;
+            if (a < c && b < c) {
+              G[a + b * c] = acc[u][q];
+              G[b + a * c] = acc[u][q];
+            }
+          }
+      }
+    }
+    __syncthreads();
+    // G = L L^T in place (lower triangle), column by column
+    for (int kk = 0; kk < c; ++kk) {
+      if (tid == 0) {
+        float p = G[kk + kk * c];
+        if (!(p > 1e-8f)) {  // too ill-conditioned for CholeskyQR2 in FP32
+          *fail = 1;
+          p = 1.0f;
+        }
+        const float r = sqrtf(p);
+        G[kk + kk * c] = r;
+        ssc = 1.0f / r;
+      }
+      __syncthreads();
+      const float ri = ssc;
+      for (int a = kk + 1 + tid; a < c; a += nt) G[a + kk * c] *= ri;
+      __syncthreads();
+      // trailing update of the lower triangle: a warp per column, lanes over rows
+      for (int b = kk + 1 + wid; b < c; b += nw) {
+        const float gb = G[b + kk * c];
+        for (int a = b + lane; a < c; a += 32) G[a + b * c] = fmaf(-G[a + kk * c], gb, G[a + b * c]);
+      }
+      __syncthreads();
+    }
+    // Y <- Y L^{-T}, one row per thread
+    for (int r = tid; r < n; r += nt) {
+      float* yr = Yb + (size_t)r * ldb;
+      for (int a = 0; a < c; ++a) {
+        float acc = yr[a];
+        for (int b = 0; b < a; ++b) acc = fmaf(-yr[b], G[a + b * c], acc);
+        yr[a] = acc / G[a + a * c];
+      }
+    }
+    __syncthreads();
+  }
+  for (int r = wid; r < n; r += nw)
+    for (int a = lane; a < c; a += 32) Y[(size_t)r * n + i + a] = Yb[r * ldb + a];
+}
+
+// ------------------------------------------------- 4. back-transformation --
+// Reflectors k0 .. k0+7 (block b, k0 = 8 b) compose as H_k0 ... H_k0+7 =
+// I - Vb Tb Vb^T with Tb upper triangular (forward, columnwise accumulation):
+// Tb(j, j) = tau_j, Tb(0:j, j) = -tau_j Tb(0:j, 0:j) (Vb(:, 0:j)^T v_j).
+constexpr int kWY = 8;
+
+__global__ void __launch_bounds__(64)
+tri_wy_kernel(int n, const float* __restrict__ V, const float* __restrict__ tauv, float* __restrict__ Tw) {
+  __shared__ float gv[kWY][kWY];
+  const int b = blockIdx.x, k0 = b * kWY, nref = n - 2;
+  const int cnt = min(kWY, nref - k0);
+  const int tid = threadIdx.x;
+  if (tid < kWY * kWY) {
+    const int a = tid % kWY, c = tid / kWY;
+    float acc = 0.0f;
+    if (a < c && c < cnt) {
+      const float* va = V + (size_t)(k0 + a) * n;
+      const float* vc = V + (size_t)(k0 + c) * n;
+      for (int r = 0; r < n; ++r) acc = fmaf(va[r], vc[r], acc);
+    }
+    gv[a][c] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    float t[kWY][kWY] = {};
+    for (int c = 0; c < cnt; ++c) {
+      const float tc = tauv[k0 + c];
+      for (int a = 0; a < c; ++a) {
+        float s = 0.0f;
+        for (int l = a; l < c; ++l) s = fmaf(t[a][l], gv[l][c], s);
+        t[a][c] = -tc * s;
+      }
+      t[c][c] = tc;
+    }
+    for (int e = 0; e < kWY * kWY; ++e) Tw[(size_t)b * kWY * kWY + e] = t[e % kWY][e / kWY];
+  }
+}
+
+// X(:, col) = H_0 H_1 ... H_{n-3} Y(:, col) in FP64, one warp per column; the
+// CTA stages kBackStage WY blocks at a time in shared memory.
+constexpr int kBackRows = (kTriMaxN + 31) / 32;
+constexpr int kBackWarps = 8;
+constexpr int kBackStage = 4;
+
+__global__ void __launch_bounds__(kBackWarps * 32)
+tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw, const float* __restrict__ Y,
+                double* __restrict__ X) {
+  __shared__ float sv[kBackStage * kWY][kBackRows * 32];
+  __shared__ float st[kBackStage][kWY * kWY];
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * kBackWarps + (threadIdx.x >> 5);
+  const int nref = n - 2, nblk = nref > 0 ? (nref + kWY - 1) / kWY : 0;
+  float z[kBackRows];
+#pragma unroll
+  for (int t = 0; t < kBackRows; ++t) {
+    const int r = lane + 32 * t;
+    z[t] = (col < n && r < n) ? Y[(size_t)r * n + col] : 0.0f;
+  }
+  for (int bt = nblk - 1; bt >= 0; bt -= kBackStage) {
+    const int b0 = max(bt - kBackStage + 1, 0), nb = bt - b0 + 1;  // blocks b0 .. bt
+    __syncthreads();
+#pragma unroll 8
+    for (int e = threadIdx.x; e < nb * kWY * kBackRows * 32; e += blockDim.x) {
+      const int r = e % (kBackRows * 32), q = e / (kBackRows * 32);  // q: reflector within the stage
+      const int k = b0 * kWY + q;
+      sv[q][r] = (r < n && k < nref) ? V[r + (size_t)k * n] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < nb * kWY * kWY; e += blockDim.x)
+      st[e / (kWY * kWY)][e % (kWY * kWY)] = Tw[(size_t)b0 * kWY * kWY + e];
+    __syncthreads();
+    for (int q = nb - 1; q >= 0; --q) {
+      // y = Vb^T z, u = Tb y, z -= Vb u
+      float y[kWY];
+#pragma unroll
+      for (int a = 0; a < kWY; ++a) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < kBackRows; ++t) acc = fmaf(sv[q * kWY + a][lane + 32 * t], z[t], acc);
+        y[a] = acc;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int a = 0; a < kWY; ++a) y[a] += __shfl_xor_sync(0xffffffffu, y[a], o);
+      float u[kWY];
+#pragma unroll
+      for (int a = 0; a < kWY; ++a) {
+        float s = 0.0f;
+#pragma unroll
+        for (int c = a; c < kWY; ++c) s = fmaf(st[q][a + c * kWY], y[c], s);
+        u[a] = s;
+      }
+#pragma unroll
+      for (int t = 0; t < kBackRows; ++t) {
+        float zt = z[t];
+#pragma unroll
+        for (int a = 0; a < kWY; ++a) zt = fmaf(-sv[q * kWY + a][lane + 32 * t], u[a], zt);
+        z[t] = zt;
+      }
+    }
+  }
+  if (col >= n) return;
+#pragma unroll
+  for (int t = 0; t < kBackRows; ++t) {
+    const int r = lane + 32 * t;
+    if (r < n) X[r + (size_t)col * n] = (double)z[t];
+  }
+}
+
+}  // namespace
+
+blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,
+                      int* fail) {
+  if (n < 1 || n > kTriMaxN) return ctx->fail(BLWS_EINVAL, "tri_stage: n = %d", n);
+  const size_t nn = (size_t)n * n;
+  const int nblk = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
+  // F (4 nn, first: 16-byte aligned), V, Y, reduction partial sums, WY factors, d, e, tau, lam, scale
+  const size_t parts = (size_t)(kMaxGroups + kMaxChunks) * n;
+  float* f = nullptr;
+  BLWS_TRY(ctx->get(BUF_TRI, (nn * 6 + parts + (size_t)nblk * kWY * kWY + (size_t)n * 4 + 64) * sizeof(float),
+                    (void**)&f));
+  float4* F = reinterpret_cast<float4*>(f);
+  float* V = f + 4 * nn;
+  float* Y = V + nn;
+  float* part = Y + nn;
+  float* Tw = part + parts;
+  float* dv = Tw + (size_t)nblk * kWY * kWY;
+  float* ev = dv + n;
+  float* tauv = ev + n;
+  float* lam = tauv + n;
+  float* tscale = lam + n;
+  const int smem = (n * (n + 1) / 2 + 3 * n) * (int)sizeof(float);
+  BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
+  // the group kernel's shared memory: the largest staged block n x (c|1) plus c x c, capped
+  const int qr_floats = std::min((int)(((size_t)n * (n | 1) + nn)), kQrSmemFloats);
+  const int gsmem = qr_floats * (int)sizeof(float);
+  BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_INV, (const void*)tri_group_qr_kernel, gsmem));
+  const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
+  tri_reduce_kernel<<<1, kTriThreads, smem, s>>>(n, T, V, dv, ev, tauv, part, tscale);
+  BLWS_CHECK_LAUNCH(ctx);
+  tri_bisect_kernel<<<ceil_div(n, 8), 256, 0, s>>>(n, dv, ev, lam);
+  BLWS_CHECK_LAUNCH(ctx);
+  tri_solve_kernel<true><<<n, 32, ssmem, s>>>(n, dv, ev, lam, tscale, F, Y, grp, gtop, fail);
+  BLWS_CHECK_LAUNCH(ctx);
+  tri_group_qr_kernel<<<n, kQrThreads, gsmem, s>>>(n, qr_floats, grp, Y, fail);
+  BLWS_CHECK_LAUNCH(ctx);
+  tri_solve_kernel<false><<<n, 32, ssmem, s>>>(n, dv, ev, lam, tscale, F, Y, grp, gtop, fail);
+  BLWS_CHECK_LAUNCH(ctx);
+  tri_group_qr_kernel<<<n, kQrThreads, gsmem, s>>>(n, qr_floats, grp, Y, fail);
+  BLWS_CHECK_LAUNCH(ctx);
+  if (nblk > 0) {
+    tri_wy_kernel<<<nblk, 64, 0, s>>>(n, V, tauv, Tw);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
+  tri_back_kernel<<<ceil_div(n, kBackWarps), kBackWarps * 32, 0, s>>>(n, V, Tw, Y, X);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+}  // namespace blws
