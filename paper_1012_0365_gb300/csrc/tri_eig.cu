@@ -37,15 +37,18 @@ constexpr float kPivMin = 1e-30f;    // Sturm counts: pivots kept away from zero
 // packed lower triangle, column-major: element (i, j), i >= j
 __device__ __forceinline__ int pk(int n, int i, int j) { return j * n - (j * (j - 1)) / 2 + (i - j); }
 
-// sum over the CTA, returned to every thread (fixed order)
+// sum over the CTA, returned to every thread (fixed order: each warp reduces
+// the per-warp partials with the same shuffle tree)
 __device__ float block_sum(float v, float* red) {
   __syncthreads();  // red may still be read from the previous call
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  float s = 0.0f;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  float s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
@@ -79,10 +82,10 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
   __shared__ float col[3];  // alpha, sigma and the diagonal entry of the current column
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int np = n * (n + 1) / 2;
-  float* A = sm;        // packed lower triangle
-  float* pv = A + np;   // pending update A -= pv pw^T + pw pv^T (global row index)
-  float* pw = pv + n;
-  float* vk = pw + n;   // this step's reflector (global row index)
+  float* A = sm;  // packed lower triangle
+  // per row (global index): x, y the pending update A -= pv pw^T + pw pv^T,
+  // z this step's reflector: one 16-byte load per column in the items
+  float4* cv = reinterpret_cast<float4*>(A + np + ((4 - (np & 3)) & 3));
   float* Lp = part;                     // [group][row]: sums left of the diagonal
   float* Up = part + kMaxGroups * n;    // [chunk][column]: sums on and below the diagonal
   // scale: largest |T_ij| over the lower triangle (a warp per column)
@@ -106,20 +109,18 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
 #pragma unroll 4
     for (int i = j + lane; i < n; i += 32) A[base + i] = (float)(T[i + (size_t)j * n] * scale);
   }
-  for (int t = tid; t < n; t += nt) {
-    pv[t] = 0.0f;
-    pw[t] = 0.0f;
-  }
+  for (int t = tid; t < n; t += nt) cv[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   __syncthreads();
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // trailing rows k+1 .. n-1 (local 0 .. m-1)
     // (1) column k
     if (wid == 0) {
       const int base = pk(n, k, k) - k;  // + r: A(r, k), r >= k
-      const float pvk = pv[k], pwk = pw[k];
+      const float pvk = cv[k].x, pwk = cv[k].y;
       float ssq = 0.0f;
       for (int r = k + lane; r < n; r += 32) {
-        const float a = A[base + r] - fmaf(pv[r], pwk, pw[r] * pvk);
+        const float4 q = cv[r];
+        const float a = A[base + r] - fmaf(q.x, pwk, q.y * pvk);
         A[base + r] = a;
         if (r >= k + 2) ssq = fmaf(a, a, ssq);
       }
@@ -153,7 +154,7 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
       if (t == k + 1) v = 1.0f;
       else if (t > k + 1 && tau != 0.0f) v = A[c0 + (t - k - 1)] * vscale;
       V[t + (size_t)k * n] = v;
-      vk[t] = v;
+      cv[t].z = v;
     }
     __syncthreads();
     // (3) pending update and product, one pass
@@ -163,9 +164,9 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
       const int cb = g * kItemCols, rb = h * kItemRows;
       if (rb + kItemRows - 1 < cb) continue;  // above the diagonal
       const int r0 = rb + lane, r1 = r0 + 32;
-      const int R0 = k + 1 + r0, R1 = k + 1 + r1;
-      const float pv0 = r0 < m ? pv[R0] : 0.0f, pw0 = r0 < m ? pw[R0] : 0.0f, v0 = r0 < m ? vk[R0] : 0.0f;
-      const float pv1 = r1 < m ? pv[R1] : 0.0f, pw1 = r1 < m ? pw[R1] : 0.0f, v1 = r1 < m ? vk[R1] : 0.0f;
+      const float4 q0 = r0 < m ? cv[k + 1 + r0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float4 q1 = r1 < m ? cv[k + 1 + r1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float pv0 = q0.x, pw0 = q0.y, v0 = q0.z, pv1 = q1.x, pw1 = q1.y, v1 = q1.z;
       float l0 = 0.0f, l1 = 0.0f, acc[32];
       int base = pk(n, k + 1 + cb, k + 1 + cb) - cb;  // + r: A(k+1+r, k+1+c)
       if (rb >= cb + kItemCols && rb + kItemRows <= m && cb + kItemCols <= m) {
@@ -173,7 +174,8 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int C = k + 1 + cb + j;
-          const float pvc = pv[C], pwc = pw[C], vc = vk[C];
+          const float4 q = cv[C];
+          const float pvc = q.x, pwc = q.y, vc = q.z;
           const float a0 = fmaf(-pw0, pvc, fmaf(-pv0, pwc, A[base + r0]));
           const float a1 = fmaf(-pw1, pvc, fmaf(-pv1, pwc, A[base + r1]));
           A[base + r0] = a0;
@@ -189,8 +191,9 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
           const int c = cb + j, C = k + 1 + c;
           float a0 = 0.0f, a1 = 0.0f, vc = 0.0f;
           if (c < m) {
-            const float pvc = pv[C], pwc = pw[C];
-            vc = vk[C];
+            const float4 q = cv[C];
+            const float pvc = q.x, pwc = q.y;
+            vc = q.z;
             if (r0 >= c && r0 < m) {
               a0 = fmaf(-pw0, pvc, fmaf(-pv0, pwc, A[base + r0]));
               A[base + r0] = a0;
@@ -238,22 +241,24 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
 #pragma unroll
       for (int h = 0; h < kMaxChunks; ++h) su += uv[h];
       p = tau * (sl + su);
-      pvv = p * vk[k + 1 + r];
+      pvv = p * cv[k + 1 + r].z;
     }
     const float K = 0.5f * tau * block_sum(pvv, red);
     if (tid < m) {
-      const int R = k + 1 + tid;
-      pw[R] = p - K * vk[R];
-      pv[R] = vk[R];
+      float4 q = cv[k + 1 + tid];
+      q.y = p - K * q.z;
+      q.x = q.z;
+      cv[k + 1 + tid] = q;
     }
     __syncthreads();
   }
   if (tid == 0) {
     if (n >= 2) {  // the last 2 x 2 block receives the last pending update
       const int a = n - 2, b = n - 1;
-      const float daa = A[pk(n, a, a)] - 2.0f * pv[a] * pw[a];
-      const float dba = A[pk(n, b, a)] - fmaf(pv[b], pw[a], pw[b] * pv[a]);
-      const float dbb = A[pk(n, b, b)] - 2.0f * pv[b] * pw[b];
+      const float4 qa = cv[a], qb = cv[b];
+      const float daa = A[pk(n, a, a)] - 2.0f * qa.x * qa.y;
+      const float dba = A[pk(n, b, a)] - fmaf(qb.x, qa.y, qb.y * qa.x);
+      const float dbb = A[pk(n, b, b)] - 2.0f * qb.x * qb.y;
       dv[a] = daa;
       ev[a] = dba;
       dv[b] = dbb;
@@ -728,7 +733,7 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   float* tauv = ev + n;
   float* lam = tauv + n;
   float* tscale = lam + n;
-  const int smem = (n * (n + 1) / 2 + 3 * n) * (int)sizeof(float);
+  const int smem = (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float);
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
   // the group kernel's shared memory: the largest staged block n x (c|1) plus c x c, capped
   const int qr_floats = std::min((int)(((size_t)n * (n | 1) + nn)), kQrSmemFloats);
