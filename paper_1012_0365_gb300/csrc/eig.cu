@@ -542,7 +542,7 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
   // FP32 stage: the tridiagonal route (tri_eig.cu) where the packed matrix fits
   // one CTA; otherwise, and for the block-diagonal second level (whose columns
   // must stay inside their blocks), Jacobi
-  const bool tri = tri_fail != nullptr && n >= 3 && n <= kTriMaxN;
+  const bool tri = tri_fail != nullptr && n >= 3 && tri_fits(ctx, n);
   const bool small = n + (n & 1) <= kCtaMaxN;
   // padded size: even for the one-CTA solver; an even number of kBS blocks otherwise
   const int N = small ? n + (n & 1) : ceil_div(n, 2 * kBS) * 2 * kBS;

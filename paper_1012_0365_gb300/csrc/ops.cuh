@@ -38,9 +38,13 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
 // column alone, and gtop[j] (device, n floats) the group's largest
 // eigenvalue as the FP32 stage found it (within ~1e-6 ||T||).  *fail
 // (device int) is set when a group could not be orthonormalised or a solve
-// normalised (X is then not to be used).  n <= kTriMaxN (the packed lower
-// triangle fills one CTA's shared memory).
-constexpr int kTriMaxN = 336;
+// normalised (X is then not to be used).  n <= kTriMaxN: up to
+// kTriOneCtaMaxN the packed lower triangle fits one CTA's shared memory;
+// larger matrices are reduced on a thread-block cluster (tri_fits tells
+// whether this GPU's shared memory holds a cluster's share).
+constexpr int kTriOneCtaMaxN = 336;
+constexpr int kTriMaxN = 576;
+bool tri_fits(Ctx* ctx, int n);
 constexpr float kTriGroupTol = 1e-4f;
 blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,
                       int* fail);

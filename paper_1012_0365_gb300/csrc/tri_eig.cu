@@ -19,9 +19,14 @@
 // The result has FP32 accuracy (residual and orthogonality ~1e-6) and is the
 // starting point of the FP64 Ogita-Aishima refinement in eig.cu.  Every
 // reduction has a fixed order: the stage is deterministic.
+#include <cooperative_groups.h>
+
 #include <algorithm>
+#include <climits>
 
 #include "ops.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace blws {
 
@@ -69,8 +74,8 @@ __device__ float block_sum(float v, float* red) {
 // global scratch (L1-resident) and are added per row in a fixed order;
 // (4) K = tau p^T v / 2 and w = p - K v become the next pending update.
 constexpr int kItemCols = 32, kItemRows = 64;
-constexpr int kMaxGroups = (kTriMaxN + kItemCols - 1) / kItemCols;
-constexpr int kMaxChunks = (kTriMaxN + kItemRows - 1) / kItemRows;
+constexpr int kMaxGroups = (kTriOneCtaMaxN + kItemCols - 1) / kItemCols;
+constexpr int kMaxChunks = (kTriOneCtaMaxN + kItemRows - 1) / kItemRows;
 
 __global__ void __launch_bounds__(kTriThreads)
 tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
@@ -267,6 +272,265 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
       dv[0] = A[0];
     }
   }
+}
+
+// ------------------------------------ 1b. tridiagonalisation on a cluster --
+// The same reduction spread over a cluster of kTriCl CTAs, for matrices
+// whose packed triangle does not fit one CTA (kTriOneCtaMaxN < n <=
+// kTriMaxN).  (For smaller n the single CTA is faster: three cluster barriers
+// and the distributed-shared-memory broadcasts per step cost more than the
+// divided item work saves.)  Column groups of 32 are owned round-robin
+// (group g by CTA g mod kTriCl); a CTA keeps all rows of its columns, packed,
+// in its own shared memory, and a full copy of the per-row vectors (the
+// pending update and the reflector).  Step k:
+//   (A) the owner of column k applies the pending update to it, forms the
+//       reflector and writes it into every CTA's vectors (distributed shared
+//       memory); cluster barrier;
+//   (B) every CTA runs the fused update-and-product items over its columns:
+//       column sums are complete inside the owner, row sums are partial;
+//       each CTA writes its row partials and its columns' sums to CTA 0;
+//       cluster barrier;
+//   (C) CTA 0 adds them up in a fixed order, forms p, K and w and writes the
+//       next pending update into every CTA; cluster barrier.
+constexpr int kTriCl = 4;
+constexpr int kTriClusterMinN = kTriOneCtaMaxN;
+constexpr int kClGroups = (kTriMaxN / kItemCols + kTriCl - 1) / kTriCl;   // groups per CTA
+constexpr int kClChunks = (kTriMaxN + kItemRows - 1) / kItemRows;
+
+__host__ __device__ inline int cl_owner(int j) { return (j / kItemCols) % kTriCl; }
+
+// words of packed columns the CTA of `rank` holds
+__host__ __device__ inline int cl_words(int n, int rank) {
+  int w = 0;
+  for (int j = 0; j < n; ++j)
+    if (cl_owner(j) == rank) w += n - j;
+  return w;
+}
+
+__global__ void __cluster_dims__(kTriCl, 1, 1) __launch_bounds__(kTriThreads)
+tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
+                          float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ part,
+                          float* __restrict__ tscale) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  extern __shared__ float4 smc[];
+  float4* cv = smc;                                        // x, y: pending update; z: reflector
+  float* rowpart = reinterpret_cast<float*>(cv + n);      // [kTriCl][n], filled in CTA 0
+  float* ucol = rowpart + (size_t)kTriCl * n;             // [n], filled in CTA 0
+  int* colstart = reinterpret_cast<int*>(ucol + n);       // A(r, j) at A[colstart[j] + r], own j
+  float* A = reinterpret_cast<float*>(colstart + n);
+  __shared__ float red[32];
+  __shared__ double redd[32];
+  __shared__ double cmax[kTriCl];
+  __shared__ float s_tau, s_col[3];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  float* Lp = part + (size_t)rank * (kClGroups + kClChunks) * n;  // [local group][row]
+  float* Up = Lp + (size_t)kClGroups * n;                         // [chunk][column]
+  if (tid == 0) {
+    int off = 0;
+    for (int j = 0; j < n; ++j) {
+      colstart[j] = INT_MIN / 2;
+      if (cl_owner(j) == rank) {
+        colstart[j] = off - j;
+        off += n - j;
+      }
+    }
+  }
+  // scale: the largest |T_ij| over the whole lower triangle
+  double mx = 0.0;
+  for (int j = wid; j < n; j += nw) {
+    if (cl_owner(j) != rank) continue;
+#pragma unroll 4
+    for (int i = j + lane; i < n; i += 32) mx = fmax(mx, fabs(T[i + (size_t)j * n]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) redd[wid] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double bm = 0.0;
+    for (int w = 0; w < nw; ++w) bm = fmax(bm, redd[w]);
+    for (int q = 0; q < kTriCl; ++q) *cl.map_shared_rank(&cmax[rank], q) = bm;
+  }
+  cl.sync();
+  mx = 0.0;
+  for (int q = 0; q < kTriCl; ++q) mx = fmax(mx, cmax[q]);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  const double scale = ldexp(1.0, -ex);
+  if (rank == 0 && tid == 0) *tscale = (float)ldexp(1.0, ex);
+  for (int j = wid; j < n; j += nw) {
+    if (cl_owner(j) != rank) continue;
+    const int base = colstart[j];
+#pragma unroll 4
+    for (int i = j + lane; i < n; i += 32) A[base + i] = (float)(T[i + (size_t)j * n] * scale);
+  }
+  for (int t = tid; t < n; t += nt) cv[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  cl.sync();
+  const int ngr = (n + kItemCols - 1) / kItemCols, H = (n + kItemRows - 1) / kItemRows;
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    // (A) column k at its owner
+    if (rank == cl_owner(k)) {
+      const int base = colstart[k];
+      if (wid == 0) {
+        const float pvk = cv[k].x, pwk = cv[k].y;
+        float ssq = 0.0f;
+        for (int r = k + lane; r < n; r += 32) {
+          const float4 q = cv[r];
+          const float a = A[base + r] - fmaf(q.x, pwk, q.y * pvk);
+          A[base + r] = a;
+          if (r >= k + 2) ssq = fmaf(a, a, ssq);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+        __syncwarp();
+        if (lane == 0) {
+          s_col[0] = A[base + k + 1];
+          s_col[1] = ssq;
+          s_col[2] = A[base + k];
+        }
+      }
+      __syncthreads();
+      const float alpha = s_col[0], sigma = s_col[1];
+      float tau = 0.0f, beta = alpha, vscale = 0.0f;
+      if (sigma > 0.0f) {
+        const float nrm = sqrtf(fmaf(alpha, alpha, sigma));
+        beta = alpha >= 0.0f ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        vscale = 1.0f / (alpha - beta);
+      }
+      if (tid == 0) {
+        dv[k] = s_col[2];
+        ev[k] = beta;
+        tauv[k] = tau;
+        for (int q = 0; q < kTriCl; ++q) *cl.map_shared_rank(&s_tau, q) = tau;
+      }
+      for (int t = tid; t < n; t += nt) {
+        float v = 0.0f;
+        if (t == k + 1) v = 1.0f;
+        else if (t > k + 1 && tau != 0.0f) v = A[base + t] * vscale;
+        V[t + (size_t)k * n] = v;
+        if (t > k)
+          for (int q = 0; q < kTriCl; ++q) cl.map_shared_rank(cv, q)[t].z = v;
+      }
+    }
+    cl.sync();
+    const float tau = s_tau;
+    // (B) items over my column groups in the trailing block
+    int nit = 0;
+    for (int g = rank; g < ngr; g += kTriCl)
+      if (kItemCols * g + kItemCols - 1 >= k + 1) nit += H - max(kItemCols * g, k + 1) / kItemRows;
+    for (int it = wid; it < nit; it += nw) {
+      int g = rank, rem = it, h = 0;
+      for (;; g += kTriCl) {
+        if (kItemCols * g + kItemCols - 1 < k + 1) continue;
+        const int h0 = max(kItemCols * g, k + 1) / kItemRows;
+        if (rem < H - h0) {
+          h = h0 + rem;
+          break;
+        }
+        rem -= H - h0;
+      }
+      const int cb = kItemCols * g, rb = kItemRows * h, gl = g / kTriCl;
+      const int r0 = rb + lane, r1 = r0 + 32;
+      const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      const float4 q0 = (r0 > k && r0 < n) ? cv[r0] : z4, q1 = (r1 > k && r1 < n) ? cv[r1] : z4;
+      float l0 = 0.0f, l1 = 0.0f, acc[32];
+      const bool full = cb >= k + 1 && cb + kItemCols <= n && rb >= cb + kItemCols && rb + kItemRows <= n;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = cb + j;
+        const bool cin = full || (c > k && c < n);
+        const float4 qc = cin ? cv[c] : z4;
+        const int base = cin ? colstart[c] : 0;
+        const bool in0 = full || (cin && r0 >= c && r0 < n), in1 = full || (cin && r1 >= c && r1 < n);
+        float a0 = 0.0f, a1 = 0.0f;
+        if (in0) {
+          a0 = fmaf(-q0.y, qc.x, fmaf(-q0.x, qc.y, A[base + r0]));
+          A[base + r0] = a0;
+        }
+        if (in1) {
+          a1 = fmaf(-q1.y, qc.x, fmaf(-q1.x, qc.y, A[base + r1]));
+          A[base + r1] = a1;
+        }
+        if (r0 > c) l0 = fmaf(a0, qc.z, l0);
+        if (r1 > c) l1 = fmaf(a1, qc.z, l1);
+        acc[j] = fmaf(a0, q0.z, a1 * q1.z);
+      }
+#pragma unroll
+      for (int sft = 16; sft >= 1; sft >>= 1) {
+        const bool up = (lane & sft) != 0;
+#pragma unroll
+        for (int q = 0; q < sft; ++q) {
+          const float send = up ? acc[q] : acc[q + sft];
+          const float keep = up ? acc[q + sft] : acc[q];
+          acc[q] = keep + __shfl_xor_sync(0xffffffffu, send, sft);
+        }
+      }
+      if (cb + lane > k && cb + lane < n) Up[(size_t)h * n + cb + lane] = acc[0];
+      if (r0 > k && r0 < n) Lp[(size_t)gl * n + r0] = l0;
+      if (r1 > k && r1 < n) Lp[(size_t)gl * n + r1] = l1;
+    }
+    __syncthreads();
+    {
+      float* rp0 = cl.map_shared_rank(rowpart, 0);
+      float* uc0 = cl.map_shared_rank(ucol, 0);
+      for (int r = k + 1 + tid; r < n; r += nt) {
+        float sl = 0.0f;
+        for (int g = rank; g < ngr && kItemCols * g < r; g += kTriCl)
+          if (kItemCols * g + kItemCols - 1 >= k + 1) sl += Lp[(size_t)(g / kTriCl) * n + r];
+        rp0[(size_t)rank * n + r] = sl;
+        if (cl_owner(r) == rank) {
+          const int g = r / kItemCols;
+          float su = 0.0f;
+          for (int h = max(kItemCols * g, k + 1) / kItemRows; h < H; ++h) su += Up[(size_t)h * n + r];
+          uc0[r] = su;
+        }
+      }
+    }
+    cl.sync();
+    // (C) CTA 0: p = tau (row sums + column sums), K, w; the next pending update everywhere
+    if (rank == 0) {
+      float p = 0.0f, pvv = 0.0f, v = 0.0f;
+      const int r = k + 1 + tid;
+      if (tid < m) {
+        float sum = ucol[r];
+#pragma unroll
+        for (int q = 0; q < kTriCl; ++q) sum += rowpart[(size_t)q * n + r];
+        p = tau * sum;
+        v = cv[r].z;
+        pvv = p * v;
+      }
+      const float K = 0.5f * tau * block_sum(pvv, red);
+      if (tid < m) {
+        const float w = p - K * v;
+        for (int q = 0; q < kTriCl; ++q) {
+          float4* rc = cl.map_shared_rank(cv, q);
+          rc[r].x = v;
+          rc[r].y = w;
+        }
+      }
+    }
+    cl.sync();
+  }
+  if (tid == 0 && n >= 2) {  // the last 2 x 2 block receives the last pending update
+    const int a = n - 2, b = n - 1;
+    const float4 qa = cv[a], qb = cv[b];
+    if (rank == cl_owner(a)) {
+      dv[a] = A[colstart[a] + a] - 2.0f * qa.x * qa.y;
+      ev[a] = A[colstart[a] + b] - fmaf(qb.x, qa.y, qb.y * qa.x);
+      tauv[a] = 0.0f;
+    }
+    if (rank == cl_owner(b)) dv[b] = A[colstart[b] + b] - 2.0f * qb.x * qb.y;
+  }
+}
+
+int cl_smem_bytes(int n) {
+  int w = 0;
+  for (int r = 0; r < kTriCl; ++r) w = std::max(w, cl_words(n, r));
+  return n * (int)sizeof(float4) + (kTriCl + 1) * n * (int)sizeof(float) + n * (int)sizeof(int) +
+         w * (int)sizeof(float);
 }
 
 // ------------------------------------------------------ 2. eigenvalues --
@@ -644,7 +908,7 @@ tri_wy_kernel(int n, const float* __restrict__ V, const float* __restrict__ tauv
 // CTA stages kBackStage WY blocks at a time in shared memory.
 constexpr int kBackRows = (kTriMaxN + 31) / 32;
 constexpr int kBackWarps = 8;
-constexpr int kBackStage = 4;
+constexpr int kBackStage = 2;
 
 __global__ void __launch_bounds__(kBackWarps * 32)
 tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw, const float* __restrict__ Y,
@@ -713,13 +977,19 @@ tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw
 
 }  // namespace
 
+bool tri_fits(Ctx* ctx, int n) {
+  if (n <= kTriOneCtaMaxN) return true;
+  return n <= kTriMaxN && (size_t)cl_smem_bytes(n) + 1024 <= ctx->smem_optin;
+}
+
 blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,
                       int* fail) {
-  if (n < 1 || n > kTriMaxN) return ctx->fail(BLWS_EINVAL, "tri_stage: n = %d", n);
+  if (n < 1 || !tri_fits(ctx, n)) return ctx->fail(BLWS_EINVAL, "tri_stage: n = %d", n);
+  const bool on_cluster = n > kTriClusterMinN;
   const size_t nn = (size_t)n * n;
   const int nblk = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
   // F (4 nn, first: 16-byte aligned), V, Y, reduction partial sums, WY factors, d, e, tau, lam, scale
-  const size_t parts = (size_t)(kMaxGroups + kMaxChunks) * n;
+  const size_t parts = (size_t)std::max(kMaxGroups + kMaxChunks, kTriCl * (kClGroups + kClChunks)) * n;
   float* f = nullptr;
   BLWS_TRY(ctx->get(BUF_TRI, (nn * 6 + parts + (size_t)nblk * kWY * kWY + (size_t)n * 4 + 64) * sizeof(float),
                     (void**)&f));
@@ -733,15 +1003,24 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   float* tauv = ev + n;
   float* lam = tauv + n;
   float* tscale = lam + n;
-  const int smem = (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float);
-  BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
+  if (on_cluster) {
+    const int csmem = cl_smem_bytes(n);
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL, (const void*)tri_reduce_cluster_kernel, csmem));
+  } else {
+    const int smem = (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float);
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
+  }
   // the group kernel's shared memory: the largest staged block n x (c|1) plus c x c, capped
   const int qr_floats = std::min((int)(((size_t)n * (n | 1) + nn)), kQrSmemFloats);
   const int gsmem = qr_floats * (int)sizeof(float);
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_INV, (const void*)tri_group_qr_kernel, gsmem));
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
-  tri_reduce_kernel<<<1, kTriThreads, smem, s>>>(n, T, V, dv, ev, tauv, part, tscale);
+  if (on_cluster)
+    tri_reduce_cluster_kernel<<<kTriCl, kTriThreads, cl_smem_bytes(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
+  else
+    tri_reduce_kernel<<<1, kTriThreads, (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float), s>>>(
+        n, T, V, dv, ev, tauv, part, tscale);
   BLWS_CHECK_LAUNCH(ctx);
   tri_bisect_kernel<<<ceil_div(n, 8), 256, 0, s>>>(n, dv, ev, lam);
   BLWS_CHECK_LAUNCH(ctx);
