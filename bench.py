@@ -179,6 +179,12 @@ def run_mc(args):
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     max_rank = 4 * r
+    if args.profile_solve:  # one untimed solve, for a profiler's launch list
+        l0 = ctx.launches
+        U, th, V, info = ctx.mc_solve(m, n, rowptr, cols, vals, max_rank=max_rank)
+        torch.cuda.synchronize()
+        return {"profile": "solve", "workload": args.workload, "iters": info["iters"],
+                "launches": ctx.launches - l0}
     for _ in range(args.warmup):
         U, th, V, info = ctx.mc_solve(m, n, rowptr, cols, vals, max_rank=max_rank)
     ms = []

@@ -142,7 +142,8 @@ __global__ void spmm_rows(int rows, int b, const int* __restrict__ ptr, const in
 #pragma unroll
   for (int c = 0; c < CPL; ++c) acc[c] = 0.0;
   const int lo = ptr[warp], hi = ptr[warp + 1];
-  for (int e = lo; e < hi; ++e) {
+#pragma unroll 4
+  for (int e = lo; e < hi; ++e) {  // unrolled: several rows of Xt in flight
     const double v = val[PERM ? perm[e] : e];
     const double* x = Xt + (size_t)idx[e] * b;
 #pragma unroll
@@ -177,48 +178,52 @@ __global__ void scale_rows(int r, int b, const double* __restrict__ sl, double* 
     C[e] *= sl[e % r];
 }
 
-// SDDMM on Omega, one warp per row of the pattern, lanes over the rank:
-// x = sum_t Ut[i, t] th_t Vt[j, t]  (Ut, Vt row-major with stride c).
+// SDDMM on Omega, one warp per row i of the pattern, one lane per observed
+// entry (i, j): the row's scaled u = Ut[i, :] th sits in shared memory and
+// each lane walks its own row of Vt, so a warp has 32 independent gathers in
+// flight and no per-entry reduction:
+//   x = sum_t Ut[i, t] th_t Vt[j, t]  (Ut, Vt row-major with stride c),
 //   mode 0 (SVT):  r = m - x;  y += delta r;            acc r^2
 //   mode 1 (PROX): r = m - x;  y = delta r (next sparse values);  acc r^2
-template <int CPL>
-__global__ void sddmm_update(int rows, int c, const int* __restrict__ rowptr,
-                             const int* __restrict__ colidx, const double* __restrict__ mval,
-                             const double* __restrict__ Ut, const double* __restrict__ th,
-                             const double* __restrict__ Vt, double delta, int mode, double* y,
-                             double* part) {
-  __shared__ double red[8];
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+constexpr int kSddWarps = 8;
+
+__global__ void __launch_bounds__(kSddWarps * 32)
+sddmm_update(int rows, int c, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+             const double* __restrict__ mval, const double* __restrict__ Ut, const double* __restrict__ th,
+             const double* __restrict__ Vt, double delta, int mode, double* y, double* part) {
+  extern __shared__ double su[];  // [kSddWarps][c]
+  __shared__ double red[kSddWarps];
+  const int wib = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int warp = blockIdx.x * kSddWarps + wib;
+  double* u = su + (size_t)wib * c;
   double acc2 = 0.0;
   if (warp < rows) {
-    double u[CPL];
-#pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-      const int t = lane + 32 * q;
-      u[q] = t < c ? Ut[(size_t)warp * c + t] * th[t] : 0.0;
-    }
-    for (int e = rowptr[warp]; e < rowptr[warp + 1]; ++e) {
+    for (int t = lane; t < c; t += 32) u[t] = Ut[(size_t)warp * c + t] * th[t];
+    __syncwarp();
+    const int e1 = rowptr[warp + 1];
+    for (int e = rowptr[warp] + lane; e < e1; e += 32) {
       const double* v = Vt + (size_t)colidx[e] * c;
-      double x = 0.0;
-#pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const int t = lane + 32 * q;
-        if (t < c) x = fma(u[q], v[t], x);
+      double x0 = 0.0, x1 = 0.0, x2 = 0.0, x3 = 0.0;
+      int t = 0;
+      for (; t + 3 < c; t += 4) {
+        x0 = fma(u[t], v[t], x0);
+        x1 = fma(u[t + 1], v[t + 1], x1);
+        x2 = fma(u[t + 2], v[t + 2], x2);
+        x3 = fma(u[t + 3], v[t + 3], x3);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      const double r = mval[e] - x;
-      if (lane == 0) {
-        acc2 = fma(r, r, acc2);
-        y[e] = mode == 0 ? fma(delta, r, y[e]) : delta * r;
-      }
+      for (; t < c; ++t) x0 = fma(u[t], v[t], x0);
+      const double r = mval[e] - ((x0 + x1) + (x2 + x3));
+      acc2 = fma(r, r, acc2);
+      y[e] = mode == 0 ? fma(delta, r, y[e]) : delta * r;
     }
   }
-  if (lane == 0) red[threadIdx.x / 32] = acc2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  if (lane == 0) red[wib] = acc2;
   __syncthreads();
   if (threadIdx.x == 0) {
     double sacc = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; ++w) sacc += red[w];
+    for (int w = 0; w < kSddWarps; ++w) sacc += red[w];
     part[blockIdx.x] = sacc;
   }
 }
@@ -303,15 +308,11 @@ blws_status sddmm(Ctx* ctx, cudaStream_t s, int m, int n, int c, const int* rowp
     BLWS_CHECK_LAUNCH(ctx);
   }
   double* part = nullptr;
-  const int blocks = ceil_div((long long)m * 32, 256);
+  const int blocks = ceil_div((long long)m, kSddWarps);
   BLWS_TRY(ctx->get(BUF_RED, (size_t)std::max(blocks, ctx->sms * 8), &part));
-  const int cc = std::max(c, 1);
-  if (cc <= 32) sddmm_update<1><<<blocks, 256, 0, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
-  else if (cc <= 64) sddmm_update<2><<<blocks, 256, 0, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
-  else if (cc <= 128) sddmm_update<4><<<blocks, 256, 0, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
-  else if (cc <= 256) sddmm_update<8><<<blocks, 256, 0, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
-  else if (cc <= 512) sddmm_update<16><<<blocks, 256, 0, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
-  else return ctx->fail(BLWS_EINVAL, "rank %d > 512", c);
+  if (c > 512) return ctx->fail(BLWS_EINVAL, "rank %d > 512", c);
+  const int ssm = kSddWarps * std::max(c, 1) * (int)sizeof(double);
+  sddmm_update<<<blocks, kSddWarps * 32, ssm, s>>>(m, c, rowptr, colidx, mval, Ut, th, Vt, delta, mode, y, part);
   BLWS_CHECK_LAUNCH(ctx);
   sum_parts<<<1, 256, 0, s>>>(blocks, part, sumsq_out);
   BLWS_CHECK_LAUNCH(ctx);
