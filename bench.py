@@ -197,13 +197,13 @@ def run_mc(args):
         e1.record(stream)
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
-    # relerr of the factored X against the planted M = ML MR^T, from the factors
-    Un, thn, Vn = U.cpu().numpy(), th.cpu().numpy(), V.cpu().numpy()
-    ML, MR = P["ML"], P["MR"]
-    xx = float(np.sum(thn ** 2))
-    mm = float(np.trace((ML.T @ ML) @ (MR.T @ MR)))
-    xm = float(np.trace((thn[:, None] * (Un.T @ ML)) @ (MR.T @ Vn)))
-    rel = math.sqrt(max(xx + mm - 2 * xm, 0.0) / mm)
+    # relerr of X = U diag(th) V^T against the planted M = ML MR^T, both formed on the device
+    # (the expansion ||X||^2 + ||M||^2 - 2 <X, M> cancels to rounding noise at 1e-4)
+    with torch.no_grad():
+        Mg = torch.from_numpy(P["ML"]).cuda() @ torch.from_numpy(P["MR"]).cuda().t()
+        Xg = (U * th) @ V.t()
+        rel = float(torch.linalg.norm(Xg - Mg) / torch.linalg.norm(Mg))
+        del Mg, Xg
     # the sparse product [S X_v; S^T X_u] at b = rank + 1, with the CSC mirror built once
     b = r + 1
     mirror = ctx.csc_mirror(m, n, rowptr, cols)

@@ -92,25 +92,39 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
   }
 }
 
-__global__ void splitk_reduce(int M, int N, int splits, double alpha, const double* __restrict__ part,
+// C = alpha (sum of the split-K partials) + beta C.  Each output is summed by
+// a group of G lanes (G a power of two up to 32, chosen so that small outputs
+// with many splits still fill the GPU): lane q of the group adds partials q,
+// q + G, ... in order (loads issued 8 at a time), then the group adds its lanes
+// with a fixed shuffle tree -- a fixed order for given M, N, splits.
+__global__ void splitk_reduce(int M, int N, int splits, int G, double alpha, const double* __restrict__ part,
                               double beta, double* C, int ldc) {
   const size_t total = (size_t)M * N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    // loads issued 8 at a time (independent), summed in split order
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  const int q = (int)(tid % G);
+  // every lane of a warp runs the same number of iterations (the shuffles need them all)
+  const size_t span = (total * G + nth - 1) / nth * nth;
+  for (size_t t = tid; t < span; t += nth) {
+    const size_t e = t / G;
     double acc = 0.0;
-    int z = 0;
-    for (; z + 8 <= splits; z += 8) {
-      double v[8];
+    if (e < total) {
+      int z = q;
+      for (; z + 7 * G < splits; z += 8 * G) {
+        double v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(z + u) * total + e];
+        for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(z + u * G) * total + e];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc += v[u];
+        for (int u = 0; u < 8; ++u) acc += v[u];
+      }
+      for (; z < splits; z += G) acc += part[(size_t)z * total + e];
     }
-    for (; z < splits; ++z) acc += part[(size_t)z * total + e];
-    const int i = (int)(e % M), j = (int)(e / M);
-    double* c = C + i + (size_t)j * ldc;
-    *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (q == 0 && e < total) {
+      const int i = (int)(e % M), j = (int)(e / M);
+      double* c = C + i + (size_t)j * ldc;
+      *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+    }
   }
 }
 
@@ -145,8 +159,11 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
   BLWS_CHECK_LAUNCH(ctx);
   if (splits > 1) {
     const size_t total = (size_t)M * N;
-    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)ctx->sms * 8);
-    splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, alpha, part, beta, C, ldc);
+    // lanes per output: enough to fill ~8 x 256 threads per SM, at most 32 and the split count
+    int G = 1;
+    while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)ctx->sms * 8 * 256) G *= 2;
+    const int blocks = (int)std::min<size_t>((total * G + 255) / 256, (size_t)ctx->sms * 8);
+    splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, alpha, part, beta, C, ldc);
     BLWS_CHECK_LAUNCH(ctx);
   }
   return BLWS_OK;
@@ -365,8 +382,10 @@ cudaError_t noalloc_gemm(cudaStream_t s, int sms, double* scratch, int M, int N,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const size_t total = (size_t)M * N;
-  const int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)sms * 8);
-  splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, 1.0, part, 0.0, C, ldc);
+  int G = 1;  // the same lane-group rule as the context path
+  while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)sms * 8 * 256) G *= 2;
+  const int blocks = (int)std::min<size_t>((total * G + 255) / 256, (size_t)sms * 8);
+  splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, 1.0, part, 0.0, C, ldc);
   return cudaGetLastError();
 }
 

@@ -43,11 +43,14 @@ def run(ctx, torch, P, **kw):
 
 
 def factored_relerr(U, th, V, ML, MR):
-    # ||U diag(th) V^T - ML MR^T||_F / ||ML MR^T||_F from the factors
-    xx = np.sum(th ** 2) if U.shape[1] else 0.0
-    mm = np.trace((ML.T @ ML) @ (MR.T @ MR))
-    xm = np.trace((th[:, None] * (U.T @ ML)) @ (MR.T @ V)) if U.shape[1] else 0.0
-    return np.sqrt(max(xx + mm - 2 * xm, 0.0) / mm)
+    # ||U diag(th) V^T - ML MR^T||_F / ||ML MR^T||_F from the factors: with
+    # A = [U diag(th), -ML] = Qa Ra and B = [V, MR] = Qb Rb, the difference is
+    # Qa (Ra Rb^T) Qb^T, so its norm is that of the small Ra Rb^T (no
+    # cancellation between ||X||^2 and ||M||^2)
+    Ra = np.linalg.qr(np.hstack([U * th, -ML]), mode="r")
+    Rb = np.linalg.qr(np.hstack([V, MR]), mode="r")
+    Rm = np.linalg.qr(ML, mode="r") @ np.linalg.qr(MR, mode="r").T
+    return np.linalg.norm(Ra @ Rb.T) / np.linalg.norm(Rm)
 
 
 @pytest.mark.parametrize("m,n,r,sdr,seed", [(300, 300, 10, 6, 0), (257, 190, 5, 5, 1)])
