@@ -633,14 +633,19 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
 
 namespace {
 
-// K = blockdiag over clusters of (S - mu_c I) / scale_c; cross-cluster entries 0
+// K = blockdiag over clusters of (sym(S) - mu_c I) / scale_c; cross-cluster
+// entries 0.  S = X^T (T X) from two GEMMs is symmetric only up to rounding,
+// and for an exactly degenerate cluster S - mu I is nothing but that rounding:
+// without the symmetrisation K would be a non-symmetric noise matrix and its
+// "eigenvectors" would not be orthogonal.
 __global__ void cluster_blocks(int n2, const double* __restrict__ S, const int* __restrict__ blk,
                                const double* __restrict__ mu, const double* __restrict__ inv_scale,
                                double* K) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * n2; e += gridDim.x * blockDim.x) {
     const int a = e % n2, b = e / n2;
     double v = 0.0;
-    if (blk[a] == blk[b]) v = (S[e] - (a == b ? mu[a] : 0.0)) * inv_scale[a];
+    if (blk[a] == blk[b])
+      v = (0.5 * (S[e] + S[b + (size_t)a * n2]) - (a == b ? mu[a] : 0.0)) * inv_scale[a];
     K[e] = v;
   }
 }

@@ -136,11 +136,7 @@ def test_whole_space_krylov_is_exact(blws, torch_mod):
     assert rel(recon(U.cpu().numpy(), V.cpu().numpy(), sig.cpu().numpy(), 0.7), A3) < 1e-10
 
 
-@pytest.mark.parametrize("mult,eps", [
-    pytest.param(12, 7.0, marks=pytest.mark.xfail(
-        reason="a 12-fold singular value straddling eps: U loses orthogonality at 3e-4 inside the "
-               "cluster (both eigen-solver routes; the oracle's BLWS is exact): open", strict=False)),
-    (12, 11.0), (40, 3.0), (4, 7.0)])
+@pytest.mark.parametrize("mult,eps", [(12, 7.0), (11, 7.0), (16, 7.0), (12, 11.0), (40, 3.0), (4, 7.0)])
 def test_repeated_singular_values(blws, torch_mod, mult, eps):
     # a singular value of multiplicity `mult` gives T_k a cluster of equal
     # eigenvalues: the eigen-solver resolves it as a joint eigenspace (and
