@@ -272,6 +272,9 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
   }
+  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)M * N * K >= kOzGemmMin &&
+      std::min(M, N) >= 16 && K >= 64)
+    return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   if (fp32) {
     if (!ta && !tb) return gemm_t<float, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     if (ta && !tb) return gemm_t<float, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);

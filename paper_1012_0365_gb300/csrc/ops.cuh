@@ -11,9 +11,15 @@ namespace blws {
 // inner size K.  beta == 0 never reads C.  Split-K partial sums are reduced
 // in a fixed order (deterministic).  fp32: products and in-CTA sums in FP32
 // (at most 256 terms each), FP64 in and out (mixed-precision mode).
+// In a BLWS_PREC_FP64_TC context the FP64 products of at least kOzGemmMin
+// multiply-adds go to oz_gemm (FP64-equivalent digit products on the tensor
+// cores); smaller ones stay on the FP64 pipe.
 blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
                  double alpha, const double* A, int lda, const double* B, int ldb,
                  double beta, double* C, int ldc, bool fp32 = false);
+blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
+constexpr double kOzGemmMin = 8.0e6;
 
 // sum of squares of an M x N matrix (ld) into *out (device), deterministic
 blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld, double* out);

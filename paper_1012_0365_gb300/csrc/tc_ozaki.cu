@@ -347,10 +347,10 @@ oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __rest
 
 // transposed digit planes of the m x n column-major A: plane t, (i, j) = A[i + j lda],
 // split with the scale of row i
-__global__ void oz_planes_rows(int m, int n, int ld, const double* __restrict__ A, int lda,
+__global__ void oz_planes_rows(int m, int n, int ld, int plane_rows, const double* __restrict__ A, int lda,
                                const int* __restrict__ E, __nv_bfloat16* planes) {
   __shared__ double tile[32][33];
-  const size_t plane = (size_t)m * ld;
+  const size_t plane = (size_t)plane_rows * ld;
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int jj = ty; jj < 32; jj += 8) {
@@ -373,7 +373,7 @@ __global__ void oz_planes_rows(int m, int n, int ld, const double* __restrict__ 
 // P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64, split order
 __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const float2* __restrict__ part,
                           const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ P,
-                          int ldp) {
+                          int ldp, double alpha = 1.0, double beta = 0.0) {
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -383,7 +383,9 @@ __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const fl
       const float2 v = part[((size_t)z * npad + j) * Mpad + r];
       acc += (double)v.x + (double)v.y;
     }
-    P[r + (size_t)j * ldp] = ldexp(acc, ea[r] + eb[j]);
+    const double v = ldexp(acc, ea[r] + eb[j]);
+    double* c = P + r + (size_t)j * ldp;
+    *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
   }
 }
 
@@ -448,7 +450,7 @@ blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int l
   oz_row_scales<<<dim3(ceil_div(m, 32), ceil_div(n, 32)), 256, 0, s>>>(m, n, A, lda, out.e);
   BLWS_CHECK_LAUNCH(ctx);
   dim3 grid(ceil_div(m, 32), ceil_div(out.ld, 32));
-  oz_planes_rows<<<grid, 256, 0, s>>>(m, n, out.ld, A, lda, out.e, out.d);
+  oz_planes_rows<<<grid, 256, 0, s>>>(m, n, out.ld, out.rows, A, lda, out.e, out.d);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
@@ -533,6 +535,77 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
         P + (t ? m : 0), ldp);
     BLWS_CHECK_LAUNCH(ctx);
   }
+  return BLWS_OK;
+}
+
+// C (M x N, ldc) = alpha op(A) op(B) + beta C with FP64-equivalent digit
+// products (op(A) is M x K, op(B) K x N; column-major, op = transpose when
+// ta / tb).  The rows of op(A) and the columns of op(B) are scaled and split
+// into digit planes (from the contiguous side when the operand is transposed,
+// by the tiled transpose otherwise), one job of the digit kernel covers the
+// product, split along K to fill the GPU, and the FP64 reduction applies the
+// scales, alpha and beta.
+blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+  BLWS_TRY(oz_encoder(ctx));
+  const int ngroups = ceil_div(N, kOzBN), npad = ngroups * kOzBN, ldk = oz_ld(K);
+  const size_t pa = (size_t)kOzS * M * ldk, pb = (size_t)kOzS * npad * ldk;
+  uint8_t* base = nullptr;
+  const size_t bytes = (pa + pb) * sizeof(__nv_bfloat16) + ((size_t)M + npad + 64) * sizeof(int);
+  BLWS_TRY(ctx->get(BUF_OZ_G, bytes, (void**)&base));
+  __nv_bfloat16* da = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* db = da + pa;
+  int* ea = reinterpret_cast<int*>(base + (pa + pb) * sizeof(__nv_bfloat16));
+  int* eb = ea + M;
+  const OzPlanes Ap{da, ea, M, K, ldk};
+  const OzPlanes Bp{db, eb, npad, K, ldk};
+  // op(B) columns beyond N stay zero digits with exponent 0
+  if (npad > N) {
+    BLWS_TRY_CUDA(ctx, cudaMemsetAsync(db, 0, pb * sizeof(__nv_bfloat16), s));
+    BLWS_TRY_CUDA(ctx, cudaMemsetAsync(eb, 0, sizeof(int) * npad, s));
+  }
+  if (ta) BLWS_TRY(oz_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
+  else BLWS_TRY(oz_planes_from_rows(ctx, s, A, lda, M, K, Ap));
+  if (!tb) BLWS_TRY(oz_planes_from_cols(ctx, s, B, ldb, 0, K, N, Bp));
+  else BLWS_TRY(oz_planes_from_rows(ctx, s, B, ldb, N, K, OzPlanes{db, eb, npad, K, ldk}));
+  const int tiles = ceil_div(M, kOzBM);
+  const int kchunks = ceil_div(K, kOzChunk);
+  const int per = ceil_div(ctx->sms, std::max(1, tiles * ngroups));
+  const int sp = std::max(1, std::min(per, kchunks));
+  const int kchunk = ceil_div(kchunks, sp) * kOzChunk;
+  const int splits = ceil_div(K, kchunk);
+  float2* part = nullptr;
+  BLWS_TRY(ctx->get(BUF_TC_PART, (size_t)splits * npad * tiles * kOzBM * sizeof(float2), (void**)&part));
+  OzJobs jobs;
+  memset(&jobs, 0, sizeof(jobs));
+  OzJob& J = jobs.job[0];
+  BLWS_TRY(oz_encode(ctx, &J.a, da, M, K, ldk, kOzBM));
+  BLWS_TRY(oz_encode(ctx, &J.b, db, npad, K, ldk, kOzBN));
+  J.ea = ea;
+  J.eb = eb;
+  J.part = part;
+  J.M = M;
+  J.K = K;
+  J.tiles = tiles;
+  J.ngroups = ngroups;
+  J.splits = splits;
+  J.kchunk = kchunk;
+  J.Mpad = tiles * kOzBM;
+  J.npad = npad;
+  jobs.job[1] = J;  // unused: every block belongs to job 0
+  double* scal = nullptr;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  jobs.blocks0 = tiles * ngroups * splits;
+  jobs.N = N;
+  jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
+  const int smem = (int)oz_smem_bytes();
+  BLWS_TRY(ctx->smem_limit(Ctx::ATTR_OZ, (const void*)oz_kernel, smem));
+  oz_kernel<<<jobs.blocks0, kOzThreads, smem, s>>>(jobs);
+  BLWS_CHECK_LAUNCH(ctx);
+  const size_t tot = (size_t)M * N;
+  oz_reduce<<<std::min(ceil_div((long long)tot, 256), ctx->sms * 8), 256, 0, s>>>(
+      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta);
+  BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
 
