@@ -240,6 +240,146 @@ def run_mc(args):
                                  "the row-major copy of X)"}}
 
 
+def run_ablation(args):
+    """Variants of the method (its own JSON line): on the 2000x2000 rank-100 RPCA
+    workload, the number of Lanczos blocks k, the mixed start [U;V]/sqrt2 against
+    the standard start [U;0] (Section 4.1), and warm starts against a cold
+    (random-start) block Lanczos in every outer iteration; then the paper's size
+    sweeps as GPU reruns: RPCA m = n in {500, 1000, 2000, 3000}, rank 10%, 10%
+    corrupted, against full-SVD SVT on the same GPU (Table 1 pattern), and MC
+    m = n from 5000 to 30000 at the (rank, samples per degree of freedom) pairs
+    of the Table 2 pattern; and BL_EVD of a symmetric matrix (evd_sequence)."""
+    import torch
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+
+    def rpca_case(m, rank, ctx_kw, steps, max_iter=1000, amp=50.0):
+        D, L0, _ = syn.rpca_problem(m, m, rank, 0.10, amp=amp, seed=0)
+        Dg = blws.colmajor(torch.from_numpy(D))
+        ctx = blws.Context(**ctx_kw)
+        A = blws.empty_colmajor(m, m)
+        E = blws.empty_colmajor(m, m)
+        kw = dict(tol=1e-7, A=A, E=E, max_iter=max_iter, allow_noconv=True)
+        _, _, info = ctx.rpca_solve(Dg, **kw)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, info = ctx.rpca_solve(Dg, **kw)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        L0g = torch.from_numpy(L0).cuda()
+        rel = float(torch.linalg.norm(A - L0g) / torch.linalg.norm(L0g))
+        out = {"ms_per_solve": float(np.mean(ms)), "iters": info["iters"], "rank": info["rank"],
+               "status": info["status"], "residual": info["residual"], "relerr_vs_planted": rel}
+        return out, Dg, info
+
+    res = {"metric": "ablation", "unit": "ms/solve", "n_gpus": 1, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "rpca_2000x2000_r100 variants; size sweeps", "tol_rpca": 1e-7}}
+    base = {"precision": 0}
+    res["k_sweep"] = {str(k): rpca_case(2000, 100, dict(base, k=k), 2)[0] for k in (2, 3, 4)}
+    res["start"] = {"mixed [U;V]/sqrt2": rpca_case(2000, 100, dict(base, start=0), 2)[0],
+                    "standard [U;0]": rpca_case(2000, 100, dict(base, start=1), 2)[0]}
+    # a cold (seeded Gaussian) block Lanczos of k_cold blocks in every outer iteration,
+    # capped at 100 iterations: status -4 with the residual reached when it stalls
+    res["warm"] = {"warm (BLWS), k=3": rpca_case(2000, 100, dict(base, warm=1), 2)[0],
+                   "cold every iteration, k_cold=4": rpca_case(2000, 100, dict(base, warm=0), 1, max_iter=100)[0],
+                   "cold every iteration, k_cold=8": rpca_case(2000, 100, dict(base, warm=0, k_cold=8), 1,
+                                                               max_iter=100)[0]}
+    # Table 1 pattern: rank 10% of m, 10% of the entries corrupted, values in [-500, 500]
+    sweep = []
+    for m in (500, 1000, 2000, 3000):
+        r = max(1, int(round(0.10 * m)))
+        out, Dg, info = rpca_case(m, r, base, 2, amp=500.0)
+        full = fullsvd_gpu_sample(torch, Dg, 1.0 / math.sqrt(m), info["iters"])
+        out.update({"m": m, "rank": r, "fullsvd_ms_per_solve": 1e3 / full["value"],
+                    "speedup": 1e3 / full["value"] / out["ms_per_solve"]})
+        sweep.append(out)
+    res["rpca_size_sweep"] = sweep
+    # Table 2 pattern: (m, r, samples per degree of freedom s / d_r)
+    mcs = []
+    for m, r, spd in ((5000, 10, 6), (5000, 50, 5), (5000, 100, 4), (10000, 10, 6), (10000, 50, 5),
+                      (20000, 10, 6), (30000, 10, 6)):
+        frac = spd * r * (2 * m - r) / (m * m)
+        P = syn.mc_problem(m, m, r, frac, seed=0)
+        ctx = blws.Context(precision=0)
+        rp, cc, vv = (torch.from_numpy(P[x]).cuda() for x in ("rowptr", "cols", "vals"))
+        # early SVT iterates can carry many more values above tau than the rank
+        cap = min(m, max(4 * r, 200))
+        try:
+            U, th, V, info = ctx.mc_solve(m, m, rp, cc, vv, max_rank=cap)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            U, th, V, info = ctx.mc_solve(m, m, rp, cc, vv, max_rank=cap)
+            e1.record()
+            e1.synchronize()
+        except blws.BlwsError as e:  # reported, not hidden: the sweep goes on
+            mcs.append({"m": m, "rank": r, "s_per_dof": spd, "observed": frac, "error": str(e)})
+            continue
+        # ||U diag(th) V^T - ML MR^T||_F from the QR factors of [U th, -ML] and [V, MR]
+        with torch.no_grad():
+            ML, MR = torch.from_numpy(P["ML"]).cuda(), torch.from_numpy(P["MR"]).cuda()
+            _, R1 = torch.linalg.qr(torch.cat([U * th, -ML], 1))
+            _, R2 = torch.linalg.qr(torch.cat([V, MR], 1))
+            _, R3 = torch.linalg.qr(ML)
+            _, R4 = torch.linalg.qr(MR)
+            rel = float(torch.linalg.norm(R1 @ R2.t()) / torch.linalg.norm(R3 @ R4.t()))
+        mcs.append({"m": m, "rank": r, "s_per_dof": spd, "observed": frac, "ms_per_solve": e0.elapsed_time(e1),
+                    "iters": info["iters"], "status": info["status"], "relerr_vs_planted": rel})
+    res["mc_size_sweep"] = mcs
+    res["bl_evd"] = evd_sequence(torch, blws, syn)
+    return res
+
+
+def evd_sequence(torch, blws, syn, m=4000, rank=150, r=100, calls=6, delta=1e-3):
+    """BL_EVD on a symmetric W (Section 4's BLWS definition applied to a partial
+    EVD): a sequence W_i = W + i delta E of nearby symmetric matrices, the
+    leading r = 100 eigenpairs of each, warm-started from the previous call's
+    (k = 3), against a cold block Lanczos per call (k_cold = 4) and a full FP64
+    EVD by the library (torch.linalg.eigh, cuSOLVER) on the same GPU.  The
+    accuracy is the largest error of the eigenvalues above eps against the
+    library's, relative to the largest eigenvalue."""
+    W0, npos = syn.symmetric_problem(m, rank, seed=0)
+    G = syn.gaussian_block(m, m, seed=1)
+    W0g = blws.colmajor(torch.from_numpy(W0))
+    Eg = blws.colmajor(torch.from_numpy((G + G.T) / 2))
+    lam_ref = torch.linalg.eigvalsh(W0g).flip(0)
+    eps = float(0.5 * (lam_ref[npos - 1] + lam_ref[npos]))
+    seq = [blws.colmajor(W0g + (i * delta) * Eg) for i in range(calls)]
+    ctx = blws.Context(k=3)
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        e1.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    U, lam, c = ctx.blws_evd(seq[0], eps, r)          # the first call is cold
+    warm_ms, cold_ms, lib_ms, err_w, err_c = [], [], [], 0.0, 0.0
+    for Wi in seq[1:]:
+        ref, t = timed(lambda: torch.linalg.eigvalsh(Wi))
+        lib_ms.append(t)
+        ref = ref.flip(0)
+        (U, lam, c), t = timed(lambda: ctx.blws_evd(Wi, eps, r, U))
+        warm_ms.append(t)
+        scale = float(ref.abs().max())
+        err_w = max(err_w, float((lam[:c] - ref[:c]).abs().max()) / scale)
+        (_, lamc, cc), t = timed(lambda: ctx.blws_evd(Wi, eps, r))
+        cold_ms.append(t)
+        err_c = max(err_c, float((lamc[:cc] - ref[:cc]).abs().max()) / scale)
+    return {"m": m, "r": r, "count_above_eps": c, "calls": calls - 1, "delta": delta,
+            "warm_k3_ms": float(np.mean(warm_ms)), "warm_max_relerr": err_w,
+            "cold_k4_ms": float(np.mean(cold_ms)), "cold_max_relerr": err_c,
+            "library_full_evd_ms": float(np.mean(lib_ms))}
+
+
 def run_batch(args):
     """Uneven instances (m, n ~ U{100..1000}, rank 5% of min(m, n), 5-10%
     corruption) solved by the library's server: all submitted at once, solved
@@ -434,6 +574,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="uneven batch through the server (own JSON line)")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve", action="store_true", help="Poisson serving sweep (own JSON line)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="variants of the method and the paper's size sweeps (own JSON line)")
     ap.add_argument("--pool", type=int, default=12)
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5])
@@ -451,10 +593,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         print(json.dumps(run_mc(args)))
         return
-    if args.batch or args.serve:
+    if args.batch or args.serve or args.ablation:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        print(json.dumps(run_batch(args) if args.batch else run_serve(args)))
+        print(json.dumps(run_ablation(args) if args.ablation else run_batch(args) if args.batch else run_serve(args)))
         return
 
     import torch

@@ -77,6 +77,16 @@ typedef struct {
   uint64_t seed;  /* seed of the counter-based generator (Philox4x32-10) that
                      draws extra start columns.  Default 0x5eed. */
   int device;     /* CUDA device ordinal the context binds to.  Default 0. */
+  int start;      /* warm-start block of blws_svt, rpca_solve and mc_solve
+                     (Section 4.1):
+                     0 (default) the mixed start [U; V]/sqrt(2), 1 the
+                     standard start [U; 0] the paper compares it with. */
+  int warm;       /* 1 (default): every outer iteration of rpca_solve /
+                     mc_solve restarts from the previous iteration's singular
+                     subspaces (BLWS); 0: every call is a cold start (k_cold
+                     blocks from a seeded Gaussian block, full
+                     reorthogonalisation), the random-start block Lanczos the
+                     paper compares against.  Variants for ablations. */
 } blws_config;
 
 /* Fill *cfg with the defaults above.  Never fails for a non-NULL cfg. */
@@ -152,6 +162,32 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r,
                      const double* G, int g,
                      double* U, double* V, double* sigma, int* count,
                      void* stream);
+
+/* Partial EVD of a symmetric W by block Lanczos with warm start: the BLWS
+ * definition of Section 4, (U_i, Lambda_i) = BL_EVD(W_i, U_{i-1}, k), i.e.
+ * Algorithms 2 and 3 run on W itself rather than on the augmented matrix.
+ *   W       m x m symmetric, dense FP64 column-major, ld ldw >= m (device);
+ *           the products read all of W (P = W X), so both triangles must
+ *           hold the matrix.
+ *   eps     finite; count = #{lambda_t > eps} (the eigenvalues an
+ *           eigenvalue thresholding at eps keeps).
+ *   r       Ritz pairs to output, 1 <= r <= m: the r largest (algebraic).
+ *   U0, w   warm start: the previous principal eigen-subspace, m x w (ld m);
+ *           w = 0 means cold start (k_cold blocks, full reorthogonalisation).
+ *   G, g    optional extra start columns, m x g (ld m), after the warm ones;
+ *           when G == NULL and r > w the library draws them.  The block
+ *           width is b = max(r, w + g).
+ *   U       out: m x r (ld m) Ritz vectors, orthonormal columns.
+ *   lam     out: the r leading Ritz values, decreasing.
+ *   count   out (host).
+ *   Requires k*b <= m.  The context's precision applies as for blws_svt
+ *   (digit-plane tensor-core products for large ones in the FP64-equivalent
+ *   mode; FP32 tall products in the mixed mode).  The call synchronises
+ *   `stream`.  Errors: BLWS_EINVAL for bad sizes or missing pointers (nothing
+ *   launched), BLWS_ECUDA for a failed launch or copy. */
+blws_status blws_evd(blws_ctx* ctx, const double* W, int m, int ldw, double eps, int r,
+                     const double* U0, int w, const double* G, int g,
+                     double* U, double* lam, int* count, void* stream);
 
 /* Step a2 alone: P = W~ X for the augmented matrix without forming it
  * (Section 4, end): P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m].

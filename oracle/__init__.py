@@ -18,7 +18,8 @@ Modules
 svt      Eq. (3)-(4): the shrinkage operator and SVT by full SVD.
 lanczos  Algorithm 1: the single-vector Lanczos procedure (b = 1 pin).
 blws     Eq. (7)-(13), Algorithms 2 and 3, Theorem 1, Section 4: block
-         Lanczos on the augmented matrix with the mixed warm start.
+         Lanczos on the augmented matrix with the mixed warm start, and
+         BL_EVD of a symmetric matrix with a warm start.
 rpca     Section 5 host: inexact ALM Robust PCA with full-SVD SVT.
 mc       Section 5 host: SVT matrix completion, and the proximal (FPC-type)
          variant whose W is a sparse residual plus a low-rank term.
@@ -29,6 +30,6 @@ from .svt import theta, svt_full, svt_factored  # noqa: F401
 from .lanczos import lanczos_alg1  # noqa: F401
 from .blws import (augmented, apply_augmented, block_lanczos, assemble_T,  # noqa: F401
                    bl_evd, blws_svt_ref, cold_svt_ref, warm_start_block,
-                   qr_deflate)
+                   qr_deflate, blws_evd_ref)
 from .rpca import rpca_ialm_full, rpca_ialm_blws, rank_predict  # noqa: F401
 from .mc import mc_svt_full, mc_prox_full  # noqa: F401

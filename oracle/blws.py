@@ -199,3 +199,26 @@ def blws_svt_ref(W, eps, U0, V0, k, r, G=None):
     X1 = warm_start_block(U0, V0, G)
     Y, lam = bl_evd(lambda X: apply_augmented(W, X), X1, k, r)
     return _svt_from_ritz(Y, lam, eps, m)
+
+
+def blws_evd_ref(W, eps, U0, k, r, G=None):
+    """BL_EVD of a symmetric W warm-started from its previous principal
+    eigen-subspace: the BLWS definition of Section 4,
+    (U_i, Lambda_i) = BL_EVD(W_i, U_{i-1}, k_i), with Algorithms 2 and 3 run on
+    W itself.
+
+    U0 is m x w (w may be 0: a cold start, which then needs G); G is an
+    optional m x e block of extra start columns after the warm ones.  The
+    start block is qr([U0 | G]).  A cold start (w = 0) reorthogonalises fully,
+    as for the SVD.  Returns ``lam`` (r, decreasing algebraically), ``U``
+    (m x r) and ``c = #{lam > eps}``.
+    """
+    W = np.asarray(W, dtype=np.float64)
+    m = W.shape[0]
+    blocks = [np.asarray(U0, float).reshape(m, -1)] if U0 is not None else []
+    if G is not None and G.shape[1] > 0:
+        blocks.append(np.asarray(G, float))
+    X1, _ = np.linalg.qr(np.hstack(blocks), mode="reduced")
+    cold = U0 is None or np.asarray(U0).size == 0
+    U, lam = bl_evd(lambda X: W @ X, X1, k, r, full_reorth=cold)
+    return {"lam": lam, "U": U, "c": int(np.count_nonzero(lam > eps))}

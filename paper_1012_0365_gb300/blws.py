@@ -18,7 +18,7 @@ PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
            "blws_last_error", "blws_launch_count", "blws_apply", "blws_apply_noalloc",
-           "blws_svt", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
+           "blws_svt", "blws_evd", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
            "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
            "blws_csc_mirror")
@@ -26,7 +26,8 @@ EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_st
 
 class BlwsConfig(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("k_cold", ctypes.c_int), ("precision", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("device", ctypes.c_int)]
+                ("seed", ctypes.c_uint64), ("device", ctypes.c_int), ("start", ctypes.c_int),
+                ("warm", ctypes.c_int)]
 
 
 class BlwsOp(ctypes.Structure):
@@ -108,6 +109,7 @@ def load():
     lib.blws_last_error.restype = ctypes.c_char_p
     lib.blws_svt.argtypes = [vp, ctypes.POINTER(BlwsOp), cd, ci, vp, vp, ci, vp, ci, vp, vp, vp,
                              ctypes.POINTER(ci), vp]
+    lib.blws_evd.argtypes = [vp, vp, ci, ci, cd, ci, vp, ci, vp, ci, vp, vp, ctypes.POINTER(ci), vp]
     lib.blws_apply.argtypes = [vp, ctypes.POINTER(BlwsOp), vp, ci, ci, vp, ci, vp]
     lib.blws_apply_noalloc.argtypes = [vp, ci, ci, ci, vp, ci, ci, vp, ci, vp]
     lib.rpca_params_default.argtypes = [ctypes.POINTER(RpcaParams)]
@@ -191,12 +193,12 @@ def apply_noalloc(W, X, P, stream=None):
 class Context:
     """Owns a blws_ctx (workspace, generator state) bound to one device."""
 
-    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0):
+    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0, start=0, warm=1):
         lib = load()
         cfg = BlwsConfig()
         lib.blws_config_default(ctypes.byref(cfg))
         cfg.k, cfg.k_cold, cfg.seed, cfg.device = k, k_cold, seed, device
-        cfg.precision = precision
+        cfg.precision, cfg.start, cfg.warm = precision, start, warm
         h = ctypes.c_void_p()
         st = lib.blws_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:
@@ -224,6 +226,28 @@ class Context:
         raise BlwsError(st, "%s: %s" % (what, load().blws_last_error(self._h).decode()))
 
     # ------------------------------------------------------------------ SVT --
+    def blws_evd(self, W, eps, r, U0=None, G=None, stream=None):
+        """Partial EVD of a symmetric W (column-major (m, m) FP64 CUDA tensor)
+        by block Lanczos warm-started from U0 (m, w).  Returns (U (m, r),
+        lam (r,) decreasing, count = #{lam > eps})."""
+        torch = _torch()
+        m = W.shape[0]
+        _check_colmajor(W, m, m, "W")
+        w = 0 if U0 is None else U0.shape[1]
+        if w:
+            _check_colmajor(U0, m, w, "U0")
+        g = 0 if G is None else G.shape[1]
+        if g:
+            _check_colmajor(G, m, g, "G")
+        U = empty_colmajor(m, r)
+        lam = torch.empty(r, dtype=torch.float64, device="cuda")
+        cnt = ctypes.c_int(0)
+        st = load().blws_evd(self._h, _ptr(W), m, m, float(eps), int(r), _ptr(U0), w, _ptr(G), g,
+                             _ptr(U), _ptr(lam), ctypes.byref(cnt), _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_evd")
+        return U, lam, cnt.value
+
     def blws_svt(self, W, eps, r, U0=None, V0=None, G=None, stream=None, sparse=None):
         """One SVT evaluation by BLWS.  W: column-major (m, n) FP64 CUDA tensor,
         or None with sparse=(m, n, rowptr, colidx, val[, Ul, sl, Vl]).

@@ -11,6 +11,9 @@
 //     error along X_l), or against every block on a cold start;
 //   * T_k assembled as in Eq. (11), its EVD in decreasing order (Algorithm 3);
 //   * Ritz lift U = sqrt2 Q_u Z(:, 1:r), V = sqrt2 Q_v Z(:, 1:r) (Theorem 1).
+// For a symmetric W (Operator::sym) the same procedure runs on W itself: the
+// start block is [U_{i-1} | extra columns], P_l = W X_l, and the Ritz vectors
+// are Q Z(:, 1:r) -- BL_EVD(W_i, U_{i-1}, k) of Section 4 (Algorithm 3).
 #include <math.h>
 
 #include <algorithm>
@@ -24,10 +27,12 @@ namespace {
 constexpr double kDeflTol = 1e-12;
 constexpr double kDeflTolMixed = 1e-6;  // FP32 products resolve columns down to ~1e-6
 
+// standard != 0: the warm columns are [U0; 0] (the one-sided start Section
+// 4.1 compares the mixed start with) instead of [U0; V0] / sqrt(2)
 __global__ void build_start(int m, int n, int w, const double* __restrict__ U0, int ldu0,
                             const double* __restrict__ V0, int ldv0, const double* __restrict__ G,
-                            int ldg, int g, int b, uint64_t seed, uint32_t stream_id, double* X,
-                            int ldx) {
+                            int ldg, int g, int b, uint64_t seed, uint32_t stream_id, int standard,
+                            double* X, int ldx) {
   const int N = m + n;
   const double r2 = 0.70710678118654752440;
   const size_t total = (size_t)N * b;
@@ -36,7 +41,7 @@ __global__ void build_start(int m, int n, int w, const double* __restrict__ U0, 
     const int i = (int)(e % N), j = (int)(e / N);
     double v;
     if (j < w) {
-      v = (i < m ? U0[i + (size_t)j * ldu0] : V0[(i - m) + (size_t)j * ldv0]) * r2;
+      v = i < m ? U0[i + (size_t)j * ldu0] * r2 : (standard ? 0.0 : V0[(i - m) + (size_t)j * ldv0] * r2);
     } else if (j - w < g) {
       v = G[i + (size_t)(j - w) * ldg];
     } else {
@@ -86,6 +91,7 @@ __global__ void ritz_values(int r, const double* __restrict__ lam, double eps, d
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
                      double* P, int ldp) {
   const int m = op.m, n = op.n;
+  if (op.sym) return gemm(ctx, s, false, false, m, b, m, 1.0, op.W, op.ldw, X, ldx, 0.0, P, ldp);
   if (op.W && op.Or && op.Oc) return oz_dual_apply(ctx, s, *op.Or, *op.Oc, m, n, X, ldx, b, P, ldp);
   if (op.W && op.Wr && op.Wc && tc_npad(b) > 0)
     return tc_dual_apply(ctx, s, *op.Wr, *op.Wc, m, n, X, ldx, b, P, ldp);
@@ -119,7 +125,7 @@ blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax) {
 
 blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a,
                      double* U, int ldu, double* V, int ldv, double* sigma, int* count_dev) {
-  const int m = op.m, n = op.n, N = m + n;
+  const int m = op.m, n = op.sym ? 0 : op.n, N = m + n;
   const int w = a.w, g = a.G ? a.g : 0;
   const int b = std::max(a.r, w + g);
   const int k = a.k;
@@ -144,7 +150,7 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(T, 0, sizeof(double) * kb * kb, s));
   const int eb = std::min(ceil_div((long long)N * b, 256), ctx->sms * 8);
   build_start<<<eb, 256, 0, s>>>(m, n, w, a.U0, a.ldu0, a.V0, a.ldv0, a.G, a.ldg, g, b,
-                                 ctx->cfg.seed, a.draw, P, N);
+                                 ctx->cfg.seed, a.draw, a.standard ? 1 : 0, P, N);
   BLWS_CHECK_LAUNCH(ctx);
   // orthonormalise the start block: deflation scale = its largest column norm
   BLWS_TRY(col_norms(ctx, s, N, b, P, N, lam, scal + SLOT_AUX));
@@ -179,9 +185,13 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
     BLWS_CHECK_LAUNCH(ctx);
   }
   BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z, a.eps));
-  const double r2 = 1.41421356237309504880;
-  BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu, f32));
-  BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv, f32));
+  if (op.sym) {
+    BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, 1.0, Q, N, Z, kb, 0.0, U, ldu, f32));
+  } else {
+    const double r2 = 1.41421356237309504880;
+    BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu, f32));
+    BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv, f32));
+  }
   ritz_values<<<1, 256, 0, s>>>(a.r, lam, a.eps, sigma, count_dev);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;

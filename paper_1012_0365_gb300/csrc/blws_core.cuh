@@ -5,9 +5,12 @@
 namespace blws {
 
 // W (m x n): dense FP64 column-major, or CSR (+ CSC mirror) plus an optional
-// low-rank term Ul diag(sl) Vl^T.
+// low-rank term Ul diag(sl) Vl^T.  sym: W is a dense symmetric m x m matrix
+// and the procedure runs on W itself (BL_EVD, Algorithm 3) instead of the
+// augmented matrix; n is unused.
 struct Operator {
   int m = 0, n = 0;
+  bool sym = false;
   const double* W = nullptr;
   int ldw = 0;
   // sparse part
@@ -48,9 +51,10 @@ struct BlwsArgs {
   uint32_t draw = 0;         // generator stream of the extra columns (per call)
   bool mixed = false;        // tall products in FP32 arithmetic (eigen-solver and
                              // Cholesky factorisations stay FP64)
+  bool standard = false;     // warm columns [U0; 0] instead of [U0; V0] / sqrt(2)
 };
 
-// P = W~ X: P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m]
+// P = W~ X: P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m]  (sym: P = W X, m rows)
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
                      double* P, int ldp);
 blws_status apply_sparse(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx,
@@ -60,7 +64,8 @@ blws_status apply_sparse(Ctx* ctx, cudaStream_t s, const Operator& op, const dou
 blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax);
 
 // One BLWS evaluation: writes U (m x r), V (n x r), sigma (r) and the count
-// #{sigma > eps} to count_dev (device int).
+// #{sigma > eps} to count_dev (device int).  With op.sym: U (m x r) holds the
+// Ritz vectors of W itself, sigma its r largest Ritz values, V is not written.
 blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a, double* U,
                      int ldu, double* V, int ldv, double* sigma, int* count_dev);
 

@@ -2,6 +2,7 @@
 #include <stdarg.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -87,6 +88,8 @@ blws_status blws_config_default(blws_config* cfg) {
   cfg->precision = BLWS_PREC_FP64;
   cfg->seed = 0x5eedull;
   cfg->device = 0;
+  cfg->start = 0;
+  cfg->warm = 1;
   return BLWS_OK;
 }
 
@@ -97,7 +100,8 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   blws_config_default(&c);
   if (cfg) c = *cfg;
   if (c.k < 1 || c.k_cold < 1 ||
-      (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED && c.precision != BLWS_PREC_FP64_TC))
+      (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED && c.precision != BLWS_PREC_FP64_TC) ||
+      (c.start != 0 && c.start != 1) || (c.warm != 0 && c.warm != 1))
     return BLWS_EINVAL;
   blws_ctx* ctx = new (std::nothrow) blws_ctx();
   if (!ctx) return BLWS_ENOMEM;
@@ -284,6 +288,7 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
   a.ldg = m + n;
   a.g = g;
   a.cold = (w == 0);
+  a.standard = ctx->cfg.start == 1;
   a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
   blws::TcPlanes Wr, Wc;
   blws::OzPlanes Or, Oc;
@@ -293,6 +298,46 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
   BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
   int* cdev = reinterpret_cast<int*>(scal + blws::SLOT_COUNT);
   BLWS_TRY(blws::blws_run(ctx, s, op, a, U, m, V, n, sigma, cdev));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  *count = *reinterpret_cast<int*>(ctx->host_pinned + blws::SLOT_COUNT);
+  return BLWS_OK;
+}
+
+blws_status blws_evd(blws_ctx* ctx, const double* W, int m, int ldw, double eps, int r,
+                     const double* U0, int w, const double* G, int g, double* U, double* lam,
+                     int* count, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!W || !U || !lam || !count) return ctx->fail(BLWS_EINVAL, "blws_evd: null argument");
+  if (m < 1 || ldw < m) return ctx->fail(BLWS_EINVAL, "blws_evd: need m >= 1, ldw >= m (m=%d ldw=%d)", m, ldw);
+  if (!std::isfinite(eps) || r < 1 || r > m || w < 0 || g < 0)
+    return ctx->fail(BLWS_EINVAL, "blws_evd: need finite eps, 1 <= r <= m, w, g >= 0");
+  if (w > 0 && !dev_ptr_ok(U0)) return ctx->fail(BLWS_EINVAL, "blws_evd: warm start pointer missing");
+  if (g > 0 && !G) return ctx->fail(BLWS_EINVAL, "blws_evd: g > 0 but G is NULL");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  blws::Operator op;
+  op.m = op.n = m;
+  op.sym = true;
+  op.W = W;
+  op.ldw = ldw;
+  blws::BlwsArgs a;
+  a.eps = eps;
+  a.r = r;
+  a.U0 = U0;
+  a.ldu0 = m;
+  a.w = w;
+  a.G = g > 0 ? G : nullptr;
+  a.ldg = m;
+  a.g = g;
+  a.cold = (w == 0);
+  a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
+  a.mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
+  double* scal;
+  BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
+  int* cdev = reinterpret_cast<int*>(scal + blws::SLOT_COUNT);
+  BLWS_TRY(blws::blws_run(ctx, s, op, a, U, m, nullptr, 0, lam, cdev));
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
                                      cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));

@@ -153,7 +153,8 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
       a.r = sk;
       a.mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
       a.draw = (uint32_t)(it * 64 + (sk - r_prev));
-      if (w == 0) {
+      a.standard = ctx->cfg.start == 1;
+      if (w == 0 || !ctx->cfg.warm) {
         a.cold = true;
         a.k = std::max(1, std::min(k_cold, N / sk));
       } else {

@@ -348,7 +348,8 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     a.eps = eps;
     a.r = sv;
     a.draw = (uint32_t)it;  // extra columns depend on the iteration only
-    if (w == 0) {
+    a.standard = ctx->cfg.start == 1;
+    if (w == 0 || !ctx->cfg.warm) {
       a.cold = true;
       a.k = std::max(1, std::min(k_cold, N / sv));
     } else {

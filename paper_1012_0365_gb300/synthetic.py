@@ -10,6 +10,7 @@ Recipes (NumPy PCG64, one seed per instance):
     since Gaussian factors have Haar-distributed singular vectors; S0 has
     round(frac * m * n) entries at positions drawn without replacement, values
     uniform in [-amp, amp]; D = L0 + S0.
+  * BL_EVD of a symmetric matrix (Section 4): see symmetric_problem.
   * MC (Section 5, Table 2 pattern): M = M_L M_R^T with i.i.d. N(0, 1) factors;
     Omega = round(frac * m * n) positions drawn uniformly without replacement,
     returned sorted by (row, col) with CSR row pointers (int32).
@@ -48,6 +49,20 @@ def mc_problem(m, n, rank, frac, seed=0):
     np.cumsum(np.bincount(rows, minlength=m), out=rowptr[1:])
     return {"rows": rows, "cols": cols, "vals": vals, "rowptr": rowptr,
             "ML": ML, "MR": MR, "nnz": nnz, "m": m, "n": n}
+
+
+def symmetric_problem(m, rank, noise=0.05, seed=0):
+    """A symmetric indefinite m x m matrix for BL_EVD: W = X diag(d) X^T / m
+    plus noise * sqrt(m) * (E + E^T) / 2, with X (m x rank) and E i.i.d.
+    N(0, 1) and |d_i| ~ U[m, 2m], every third d_i negative.  Returns (W, npos)
+    with npos the number of positive d_i (the eigenvalues that stand above
+    the noise edge)."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, rank))
+    d = np.where(np.arange(rank) % 3 == 2, -1.0, 1.0) * rng.uniform(1.0, 2.0, rank) * m
+    E = rng.standard_normal((m, m))
+    W = (X * d) @ X.T / m + noise * math.sqrt(m) * (E + E.T) / 2
+    return W, int(np.count_nonzero(d > 0))
 
 
 def gaussian_block(rows, cols, seed=0):

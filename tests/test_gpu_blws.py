@@ -229,3 +229,120 @@ def test_argument_errors(blws, torch_mod):
         ctx.blws_svt(W, 1.0, 11)           # r > min(m, n)
     with pytest.raises(blws.BlwsError):
         ctx.blws_svt(W, 1.0, 10)           # k * b = 30 > m + n
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_standard_start_matches_oracle(blws, torch_mod, k):
+    # start = 1: the one-sided start block [U0; 0] of Section 4.1; the oracle
+    # takes it as the mixed start of (sqrt2 U0, 0)
+    torch = torch_mod
+    m, n, rank, w, r = 120, 90, 6, 6, 8
+    W = structured(m, n, rank, seed=21)
+    s = np.linalg.svd(W, compute_uv=False)
+    eps = 0.5 * (s[rank - 1] + s[rank])
+    Up, _, Vpt = np.linalg.svd(W + 0.01 * syn.gaussian_block(m, n, seed=22), full_matrices=False)
+    U0, V0 = Up[:, :w], Vpt[:w].T
+    G = syn.gaussian_block(m + n, r - w, seed=23)
+    ref = oracle.blws_svt_ref(W, eps, U0 * np.sqrt(2.0), 0.0 * V0, k, r, G)
+    ctx = blws.Context(k=k, start=1)
+    U, V, sig, c = ctx.blws_svt(gpu(blws, torch, W), eps, r, gpu(blws, torch, U0),
+                                gpu(blws, torch, V0), gpu(blws, torch, G))
+    assert c == ref["c"]
+    np.testing.assert_allclose(sig.cpu().numpy(), ref["sigma"], rtol=0, atol=SIG_TOL * s[0])
+    assert rel(recon(U.cpu().numpy(), V.cpu().numpy(), sig.cpu().numpy(), eps), ref["A"]) < A_TOL
+    # and the mixed start of the same subspaces is closer to the exact SVT (Section 4.1)
+    A_exact, _ = oracle.svt_full(W, eps)
+    mixed = oracle.blws_svt_ref(W, eps, U0, V0, k, r, G)
+    assert np.linalg.norm(mixed["A"] - A_exact) <= np.linalg.norm(ref["A"] - A_exact)
+
+
+def sym_structured(m, rank, seed, noise=0.05):
+    """Symmetric indefinite: a rank-`rank` part with eigenvalues of both signs
+    plus symmetric noise, so the top of the spectrum is separated.  Returns
+    (W, eps) with eps between the positive signal eigenvalues and the rest."""
+    W, npos = syn.symmetric_problem(m, rank, noise, seed)
+    lam_all = np.sort(np.linalg.eigvalsh(W))[::-1]
+    return W, 0.5 * (lam_all[npos - 1] + lam_all[npos])
+
+
+EVD_CASES = [
+    # m, rank, w (0: cold), r, k
+    (40, 4, 4, 5, 2),
+    (200, 10, 11, 12, 3),
+    (129, 12, 9, 14, 3),      # r > w: extra columns
+    (513, 30, 33, 33, 3),
+    (37, 3, 0, 6, 4),         # cold start, full reorthogonalisation
+    (5, 2, 0, 5, 1),          # r = m: one block is the whole space
+]
+
+
+@pytest.mark.parametrize("m,rank,w,r,k", EVD_CASES)
+def test_blws_evd_matches_oracle(blws, torch_mod, m, rank, w, r, k):
+    torch = torch_mod
+    W, eps = sym_structured(m, rank, seed=m + 3 * rank)
+    lam_all = np.sort(np.linalg.eigvalsh(W))[::-1]
+    U0 = None
+    if w:
+        E = syn.gaussian_block(m, m, seed=7)
+        _, Qp = np.linalg.eigh(W + 0.005 * (E + E.T))
+        U0 = Qp[:, ::-1][:, :w].copy()
+    b = max(r, w)
+    G = syn.gaussian_block(m, b - w, seed=8) if b > w else None
+    ref = oracle.blws_evd_ref(W, eps, U0, k, r, G)
+    ctx = blws.Context(k=k, k_cold=k)
+    U, lam, c = ctx.blws_evd(gpu(blws, torch, W), eps, r, None if U0 is None else gpu(blws, torch, U0),
+                             None if G is None else gpu(blws, torch, G))
+    U, lam = U.cpu().numpy(), lam.cpu().numpy()
+    scale = np.max(np.abs(lam_all))
+    assert c == ref["c"]
+    np.testing.assert_allclose(lam, ref["lam"], rtol=0, atol=SIG_TOL * scale)
+    # the thresholded part U diag(max(lam - eps, 0)) U^T (unique where the
+    # eigenvector signs and bases of near-equal values are not)
+    th = np.maximum(lam - eps, 0.0)
+    thr = np.maximum(ref["lam"] - eps, 0.0)
+    assert rel((U * th) @ U.T, (ref["U"] * thr) @ ref["U"].T) < A_TOL
+    np.testing.assert_allclose(U.T @ U, np.eye(r), atol=1e-10)
+
+
+def test_blws_evd_full_size(blws, torch_mod):
+    # m = 3000, 100 pairs.  (1) One warm call from the exact eigenvectors of a
+    # nearby matrix matches the oracle's BL_EVD on the same inputs.  (2)
+    # Repeated warm calls on one W converge: the residual of the pairs above
+    # eps falls each call to the FP64 level, and those Ritz values match
+    # LAPACK's eigenvalues.
+    torch = torch_mod
+    m, rank, r = 3000, 100, 100
+    W, eps = sym_structured(m, rank, seed=11)
+    lam_all = np.sort(np.linalg.eigvalsh(W))[::-1]
+    scale = np.max(np.abs(lam_all))
+    E = syn.gaussian_block(m, m, seed=12)
+    _, Qp = np.linalg.eigh(W + 1e-3 * (E + E.T))
+    U0 = Qp[:, ::-1][:, :r].copy()
+    ref = oracle.blws_evd_ref(W, eps, U0, 3, r)
+    Wg = gpu(blws, torch, W)
+    ctx = blws.Context(k=3)
+    U, lam, c = ctx.blws_evd(Wg, eps, r, gpu(blws, torch, U0))
+    assert c == ref["c"] == int(np.count_nonzero(lam_all > eps))
+    lh, Uh = lam.cpu().numpy(), U.cpu().numpy()
+    np.testing.assert_allclose(lh, ref["lam"], rtol=0, atol=SIG_TOL * scale)
+    th, thr = np.maximum(lh - eps, 0.0), np.maximum(ref["lam"] - eps, 0.0)
+    assert rel((Uh * th) @ Uh.T, (ref["U"] * thr) @ ref["U"].T) < A_TOL
+    res = []
+    for _ in range(4):
+        U, lam, c = ctx.blws_evd(Wg, eps, r, U)
+        Rz = Wg @ U[:, :c] - U[:, :c] * lam[:c]
+        res.append(float(torch.linalg.matrix_norm(Rz, ord=2)) / scale)
+    assert res[1] < res[0] and res[-1] < 1e-9
+    np.testing.assert_allclose(lam[:c].cpu().numpy(), lam_all[:c], rtol=0, atol=1e-12 * scale)
+
+
+def test_blws_evd_argument_errors(blws, torch_mod):
+    torch = torch_mod
+    W = gpu(blws, torch, sym_structured(20, 2, seed=1)[0])
+    ctx = blws.Context(k=3)
+    with pytest.raises(blws.BlwsError):
+        ctx.blws_evd(W, 0.0, 21)                 # r > m
+    with pytest.raises(blws.BlwsError):
+        ctx.blws_evd(W, 0.0, 8)                  # cold k_cold * b = 32 > m
+    with pytest.raises(blws.BlwsError):
+        ctx.blws_evd(W, float("nan"), 2)

@@ -187,3 +187,66 @@ def test_blws_adm_stable_far_past_convergence():
     out = oracle.rpca_ialm_blws(D, lambda r, c: rng.standard_normal((r, c)), tol=1e-15, max_iter=45)
     assert max(h[1] for h in out["history"][10:]) == 3
     assert min(h[0] for h in out["history"]) < 1e-12
+
+
+def _sym_with_spectrum(lam, seed):
+    Q = syn.orthonormal(len(lam), len(lam), seed=seed)
+    return (Q * np.asarray(lam, float)) @ Q.T, Q
+
+
+def test_evd_whole_space_is_exact_and_algebraic():
+    # BL_EVD on a symmetric indefinite W: once k*b = m the Krylov space is the
+    # whole space, so the Ritz pairs are W's eigenpairs, ordered algebraically
+    # (-12 has the largest magnitude but is not among the top four).
+    lam = [9.0, 7.0, 4.0, 1.0, -0.5, -3.0, -12.0, 0.25, 2.5, -6.0, 5.5, -1.5]
+    W, Q = _sym_with_spectrum(lam, seed=40)
+    G = syn.gaussian_block(12, 4, seed=41)
+    out = oracle.blws_evd_ref(W, 2.0, None, 3, 4, G)
+    np.testing.assert_allclose(out["lam"], [9.0, 7.0, 5.5, 4.0], atol=1e-12)
+    assert out["c"] == 4
+    want = Q[:, [0, 1, 10, 2]]
+    np.testing.assert_allclose(np.abs(np.sum(out["U"] * want, axis=0)), 1.0, atol=1e-10)
+    np.testing.assert_allclose(W @ out["U"], out["U"] * out["lam"], atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_evd_exact_warm_start_is_exact(k):
+    # an invariant start block (the exact leading eigenvectors) gives R_1 = 0:
+    # the leading eigenpairs come out exactly for any k
+    lam = np.array([10.0, 6.0, 3.0, -1.0, -2.0, 0.5, 1.5, -8.0, 2.0, 0.0])
+    W, Q = _sym_with_spectrum(lam, seed=42)
+    out = oracle.blws_evd_ref(W, 0.0, Q[:, :3], k, 3)
+    np.testing.assert_allclose(out["lam"], [10.0, 6.0, 3.0], atol=1e-12)
+    np.testing.assert_allclose(np.abs(np.sum(out["U"] * Q[:, :3], axis=0)), 1.0, atol=1e-12)
+
+
+def test_evd_warm_start_error_shrinks_with_perturbation():
+    # Section 4.1's argument for BL_EVD: warm-started from the eigenvectors of
+    # a nearby W_{i-1}, a small k recovers W_i's leading pairs with an error
+    # that falls with the distance between the two
+    lam = np.concatenate([[20.0, 15.0, 12.0, 10.0], np.linspace(-1.0, 1.0, 56)])
+    W0, Q = _sym_with_spectrum(lam, seed=43)
+    E = syn.gaussian_block(60, 60, seed=44)
+    E = (E + E.T) / 2
+    errs = {1: [], 2: [], 3: []}
+    for delta in (1e-1, 1e-2, 1e-3):
+        W = W0 + delta * E
+        ref = np.sort(np.linalg.eigvalsh(W))[::-1][:4]
+        for k in errs:
+            out = oracle.blws_evd_ref(W, 5.0, Q[:, :4], k, 4)
+            errs[k].append(np.max(np.abs(out["lam"] - ref)))
+    for k, e in errs.items():
+        assert e[0] > e[1] > e[2]          # falls with the distance
+    for i in range(3):
+        assert errs[1][i] > errs[2][i] > errs[3][i]   # and with more blocks
+    assert errs[2][2] < 1e-7 and errs[3][2] < 1e-9
+
+
+def test_evd_of_augmented_matrix_gives_singular_values():
+    # Theorem 1 link: BL_EVD on the explicit W~ from the mixed start is the
+    # SVD-side procedure, so its Ritz values are the singular-value estimates
+    W = syn.gaussian_block(9, 7, seed=45)
+    U, s, Vt = np.linalg.svd(W)
+    X0 = np.vstack([U[:, :3], Vt[:3].T]) / np.sqrt(2.0)
+    out = oracle.blws_evd_ref(augmented(W), 0.5, X0, 2, 3)
+    np.testing.assert_allclose(out["lam"], s[:3], atol=1e-12)
