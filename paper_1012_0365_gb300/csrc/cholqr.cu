@@ -37,6 +37,58 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
 
 constexpr double kPivMin = 1e-10;
 constexpr double kPivMinF32 = 1e-6;
+constexpr double kNearIdErr = 2e-16;  // error allowed in L, elementwise
+
+// Near-identity shortcut.  When the equilibrated Gram matrix is I + E with
+// every off-diagonal |E_ij| <= e_b = sqrt(kNearIdErr / b) (about 1.4e-9 at
+// b = 101: the columns are already orthonormal to that level, as after a
+// first CholeskyQR pass), its Cholesky factor is L = I + tril(E) and
+// L^-1 = I - tril(E), each to within b e_b^2 = kNearIdErr elementwise
+// (L L^T = I + E + tril(E) tril(E)^T), so S and B follow without a
+// factorisation.  The pivots are then 1 to that accuracy;
+// a live column whose scale is within a factor 1 + 1e-6 of the deflation
+// threshold takes the full path, so both paths deflate the same columns.
+// The test reads the lower triangle only, like the factorisation, and a
+// non-finite entry sends the matrix to the full path.  Every thread of the
+// block calls it (it ends in a block-wide vote).
+__device__ bool near_identity(int b, const double* __restrict__ G, const double* d,
+                              const double* dinv, const int* dead, double thr) {
+  const double eb = sqrt(kNearIdErr / b);
+  int slow = 0;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int i = e % b, j = e / b;
+    if (i < j) continue;
+    if (i == j) {
+      if (!dead[j] && !(d[j] > thr * (1.0 + 1e-6))) slow = 1;
+    } else if (!dead[i] && !dead[j] && !(fabs(G[e]) * dinv[i] * dinv[j] <= eb)) {
+      slow = 1;
+    }
+  }
+  return __syncthreads_or(slow) == 0;
+}
+
+// S(c, j) = L^-1(j, c) / d_c and B(c, j) = L(j, c) d_j from the shortcut,
+// for the elements e = first, first + stride, ... of the b x b outputs.
+__device__ void near_identity_write(int b, const double* __restrict__ G, const double* d,
+                                    const double* dinv, const int* dead, double* __restrict__ S,
+                                    double* __restrict__ Bout, int first, int stride) {
+  for (int e = first; e < b * b; e += stride) {
+    const int c = e % b, j = e / b;
+    double sv = 0.0, bv = 0.0;
+    if (j >= c && !dead[c]) {
+      if (j == c) {
+        sv = dinv[c];
+        bv = d[c];
+      } else if (!dead[j]) {
+        const double f = G[j + (size_t)c * b] * dinv[j] * dinv[c];  // E(j, c), lower triangle
+        sv = -f * dinv[c];
+        bv = f * d[j];
+      }
+    }
+    S[e] = sv;
+    Bout[e] = bv;
+  }
+}
 
 // One CTA: equilibrated Cholesky of G (b x b, ld b) with deflation, then
 // S = D^-1 L^-T (upper, X = R S) and B = L^T D (upper, R = X B).
@@ -65,6 +117,10 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
     dinv[j] = dz ? 1.0 : 1.0 / dj;
   }
   __syncthreads();
+  if (near_identity(b, G, d, dinv, dead, thr)) {
+    near_identity_write(b, G, d, dinv, dead, S, Bout, tid, nt);
+    return;
+  }
   // equilibrated lower triangle (upper ignored)
   for (int e = tid; e < b * b; e += nt) {
     const int i = e % b, j = e / b;
@@ -233,6 +289,12 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
     dinv[j] = dz ? 1.0 : 1.0 / dj;
   }
   __syncthreads();
+  // every CTA takes the same decision from the same data; none has touched
+  // another's shared memory yet, so all may leave here
+  if (near_identity(b, G, d, dinv, dead, thr)) {
+    near_identity_write(b, G, d, dinv, dead, S, Bout, rank * kCThreads + tid, kCC * kCThreads);
+    return;
+  }
   // my tiles of the equilibrated lower triangle; padding rows and columns
   // (index >= b) are identity, dead columns unit vectors
   for (int lin = rank; lin < lay.ntiles; lin += kCC) {
