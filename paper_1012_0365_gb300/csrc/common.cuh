@@ -89,7 +89,7 @@ struct Ctx {
   // kernel (process-wide, per device), not to a context: it only ever grows,
   // under a lock, so that contexts on other threads never lower it under a
   // launch that needs more (defined in capi.cu).
-  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_TRI, ATTR_TRI_INV, ATTR_TRI_CL, ATTR_OZ, ATTR_COUNT_ };
+  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_TRI, ATTR_TRI_INV, ATTR_TRI_CL, ATTR_TRI_CL8, ATTR_OZ, ATTR_COUNT_ };
   blws_status smem_limit(SmemAttr which, const void* func, int bytes);
   int jacobi_block_per_sm = 0;  // occupancy of the block Jacobi kernel (queried once)
   // FP32 eigen stage: 0 the tridiagonal route where it applies, 1 Jacobi only

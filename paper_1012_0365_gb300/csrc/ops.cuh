@@ -46,10 +46,10 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
 // (device int) is set when a group could not be orthonormalised or a solve
 // normalised (X is then not to be used).  n <= kTriMaxN: up to
 // kTriOneCtaMaxN the packed lower triangle fits one CTA's shared memory;
-// larger matrices are reduced on a thread-block cluster (tri_fits tells
-// whether this GPU's shared memory holds a cluster's share).
+// larger matrices are reduced on a thread-block cluster of 4 or 8 CTAs
+// (tri_fits tells whether this GPU's shared memory holds a cluster's share).
 constexpr int kTriOneCtaMaxN = 336;
-constexpr int kTriMaxN = 576;
+constexpr int kTriMaxN = 736;
 bool tri_fits(Ctx* ctx, int n);
 constexpr float kTriGroupTol = 1e-4f;
 blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,

@@ -275,12 +275,12 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
 }
 
 // ------------------------------------ 1b. tridiagonalisation on a cluster --
-// The same reduction spread over a cluster of kTriCl CTAs, for matrices
+// The same reduction spread over a cluster of kCl CTAs, for matrices
 // whose packed triangle does not fit one CTA (kTriOneCtaMaxN < n <=
 // kTriMaxN).  (For smaller n the single CTA is faster: three cluster barriers
 // and the distributed-shared-memory broadcasts per step cost more than the
 // divided item work saves.)  Column groups of 32 are owned round-robin
-// (group g by CTA g mod kTriCl); a CTA keeps all rows of its columns, packed,
+// (group g by CTA g mod kCl); a CTA keeps all rows of its columns, packed,
 // in its own shared memory, and a full copy of the per-row vectors (the
 // pending update and the reflector).  Step k:
 //   (A) the owner of column k applies the pending update to it, forms the
@@ -292,36 +292,43 @@ tri_reduce_kernel(int n, const double* __restrict__ T, float* __restrict__ V, fl
 //       cluster barrier;
 //   (C) CTA 0 adds them up in a fixed order, forms p, K and w and writes the
 //       next pending update into every CTA; cluster barrier.
-constexpr int kTriCl = 4;
-constexpr int kTriClusterMinN = kTriOneCtaMaxN;
-constexpr int kClGroups = (kTriMaxN / kItemCols + kTriCl - 1) / kTriCl;   // groups per CTA
+// Two cluster sizes: 4 CTAs up to kTriCl4MaxN (a quarter of the packed
+// triangle per CTA fits shared memory), 8 CTAs (the portable maximum) above,
+// up to kTriMaxN.
+constexpr int kTriCl4MaxN = 576;
+template <int kCl>
+__host__ __device__ constexpr int cl_groups() { return (kTriMaxN / kItemCols + kCl - 1) / kCl; }  // groups per CTA
 constexpr int kClChunks = (kTriMaxN + kItemRows - 1) / kItemRows;
 
-__host__ __device__ inline int cl_owner(int j) { return (j / kItemCols) % kTriCl; }
+template <int kCl>
+__host__ __device__ inline int cl_owner(int j) { return (j / kItemCols) % kCl; }
 
 // words of packed columns the CTA of `rank` holds
+template <int kCl>
 __host__ __device__ inline int cl_words(int n, int rank) {
   int w = 0;
   for (int j = 0; j < n; ++j)
-    if (cl_owner(j) == rank) w += n - j;
+    if (cl_owner<kCl>(j) == rank) w += n - j;
   return w;
 }
 
-__global__ void __cluster_dims__(kTriCl, 1, 1) __launch_bounds__(kTriThreads)
+template <int kCl>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTriThreads)
 tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
                           float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ part,
                           float* __restrict__ tscale) {
+  constexpr int kClGroups = cl_groups<kCl>();
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   extern __shared__ float4 smc[];
   float4* cv = smc;                                        // x, y: pending update; z: reflector
-  float* rowpart = reinterpret_cast<float*>(cv + n);      // [kTriCl][n], filled in CTA 0
-  float* ucol = rowpart + (size_t)kTriCl * n;             // [n], filled in CTA 0
+  float* rowpart = reinterpret_cast<float*>(cv + n);      // [kCl][n], filled in CTA 0
+  float* ucol = rowpart + (size_t)kCl * n;             // [n], filled in CTA 0
   int* colstart = reinterpret_cast<int*>(ucol + n);       // A(r, j) at A[colstart[j] + r], own j
   float* A = reinterpret_cast<float*>(colstart + n);
   __shared__ float red[32];
   __shared__ double redd[32];
-  __shared__ double cmax[kTriCl];
+  __shared__ double cmax[kCl];
   __shared__ float s_tau, s_col[3];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   float* Lp = part + (size_t)rank * (kClGroups + kClChunks) * n;  // [local group][row]
@@ -330,7 +337,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
     int off = 0;
     for (int j = 0; j < n; ++j) {
       colstart[j] = INT_MIN / 2;
-      if (cl_owner(j) == rank) {
+      if (cl_owner<kCl>(j) == rank) {
         colstart[j] = off - j;
         off += n - j;
       }
@@ -339,7 +346,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
   // scale: the largest |T_ij| over the whole lower triangle
   double mx = 0.0;
   for (int j = wid; j < n; j += nw) {
-    if (cl_owner(j) != rank) continue;
+    if (cl_owner<kCl>(j) != rank) continue;
 #pragma unroll 4
     for (int i = j + lane; i < n; i += 32) mx = fmax(mx, fabs(T[i + (size_t)j * n]));
   }
@@ -350,17 +357,17 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
   if (tid == 0) {
     double bm = 0.0;
     for (int w = 0; w < nw; ++w) bm = fmax(bm, redd[w]);
-    for (int q = 0; q < kTriCl; ++q) *cl.map_shared_rank(&cmax[rank], q) = bm;
+    for (int q = 0; q < kCl; ++q) *cl.map_shared_rank(&cmax[rank], q) = bm;
   }
   cl.sync();
   mx = 0.0;
-  for (int q = 0; q < kTriCl; ++q) mx = fmax(mx, cmax[q]);
+  for (int q = 0; q < kCl; ++q) mx = fmax(mx, cmax[q]);
   int ex = 0;
   if (mx > 0.0) frexp(mx, &ex);
   const double scale = ldexp(1.0, -ex);
   if (rank == 0 && tid == 0) *tscale = (float)ldexp(1.0, ex);
   for (int j = wid; j < n; j += nw) {
-    if (cl_owner(j) != rank) continue;
+    if (cl_owner<kCl>(j) != rank) continue;
     const int base = colstart[j];
 #pragma unroll 4
     for (int i = j + lane; i < n; i += 32) A[base + i] = (float)(T[i + (size_t)j * n] * scale);
@@ -371,7 +378,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
     // (A) column k at its owner
-    if (rank == cl_owner(k)) {
+    if (rank == cl_owner<kCl>(k)) {
       const int base = colstart[k];
       if (wid == 0) {
         const float pvk = cv[k].x, pwk = cv[k].y;
@@ -404,7 +411,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
         dv[k] = s_col[2];
         ev[k] = beta;
         tauv[k] = tau;
-        for (int q = 0; q < kTriCl; ++q) *cl.map_shared_rank(&s_tau, q) = tau;
+        for (int q = 0; q < kCl; ++q) *cl.map_shared_rank(&s_tau, q) = tau;
       }
       for (int t = tid; t < n; t += nt) {
         float v = 0.0f;
@@ -412,18 +419,18 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
         else if (t > k + 1 && tau != 0.0f) v = A[base + t] * vscale;
         V[t + (size_t)k * n] = v;
         if (t > k)
-          for (int q = 0; q < kTriCl; ++q) cl.map_shared_rank(cv, q)[t].z = v;
+          for (int q = 0; q < kCl; ++q) cl.map_shared_rank(cv, q)[t].z = v;
       }
     }
     cl.sync();
     const float tau = s_tau;
     // (B) items over my column groups in the trailing block
     int nit = 0;
-    for (int g = rank; g < ngr; g += kTriCl)
+    for (int g = rank; g < ngr; g += kCl)
       if (kItemCols * g + kItemCols - 1 >= k + 1) nit += H - max(kItemCols * g, k + 1) / kItemRows;
     for (int it = wid; it < nit; it += nw) {
       int g = rank, rem = it, h = 0;
-      for (;; g += kTriCl) {
+      for (;; g += kCl) {
         if (kItemCols * g + kItemCols - 1 < k + 1) continue;
         const int h0 = max(kItemCols * g, k + 1) / kItemRows;
         if (rem < H - h0) {
@@ -432,7 +439,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
         }
         rem -= H - h0;
       }
-      const int cb = kItemCols * g, rb = kItemRows * h, gl = g / kTriCl;
+      const int cb = kItemCols * g, rb = kItemRows * h, gl = g / kCl;
       const int r0 = rb + lane, r1 = r0 + 32;
       const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       const float4 q0 = (r0 > k && r0 < n) ? cv[r0] : z4, q1 = (r1 > k && r1 < n) ? cv[r1] : z4;
@@ -478,10 +485,10 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
       float* uc0 = cl.map_shared_rank(ucol, 0);
       for (int r = k + 1 + tid; r < n; r += nt) {
         float sl = 0.0f;
-        for (int g = rank; g < ngr && kItemCols * g < r; g += kTriCl)
-          if (kItemCols * g + kItemCols - 1 >= k + 1) sl += Lp[(size_t)(g / kTriCl) * n + r];
+        for (int g = rank; g < ngr && kItemCols * g < r; g += kCl)
+          if (kItemCols * g + kItemCols - 1 >= k + 1) sl += Lp[(size_t)(g / kCl) * n + r];
         rp0[(size_t)rank * n + r] = sl;
-        if (cl_owner(r) == rank) {
+        if (cl_owner<kCl>(r) == rank) {
           const int g = r / kItemCols;
           float su = 0.0f;
           for (int h = max(kItemCols * g, k + 1) / kItemRows; h < H; ++h) su += Up[(size_t)h * n + r];
@@ -497,7 +504,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
       if (tid < m) {
         float sum = ucol[r];
 #pragma unroll
-        for (int q = 0; q < kTriCl; ++q) sum += rowpart[(size_t)q * n + r];
+        for (int q = 0; q < kCl; ++q) sum += rowpart[(size_t)q * n + r];
         p = tau * sum;
         v = cv[r].z;
         pvv = p * v;
@@ -505,7 +512,7 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
       const float K = 0.5f * tau * block_sum(pvv, red);
       if (tid < m) {
         const float w = p - K * v;
-        for (int q = 0; q < kTriCl; ++q) {
+        for (int q = 0; q < kCl; ++q) {
           float4* rc = cl.map_shared_rank(cv, q);
           rc[r].x = v;
           rc[r].y = w;
@@ -517,19 +524,20 @@ tri_reduce_cluster_kernel(int n, const double* __restrict__ T, float* __restrict
   if (tid == 0 && n >= 2) {  // the last 2 x 2 block receives the last pending update
     const int a = n - 2, b = n - 1;
     const float4 qa = cv[a], qb = cv[b];
-    if (rank == cl_owner(a)) {
+    if (rank == cl_owner<kCl>(a)) {
       dv[a] = A[colstart[a] + a] - 2.0f * qa.x * qa.y;
       ev[a] = A[colstart[a] + b] - fmaf(qb.x, qa.y, qb.y * qa.x);
       tauv[a] = 0.0f;
     }
-    if (rank == cl_owner(b)) dv[b] = A[colstart[b] + b] - 2.0f * qb.x * qb.y;
+    if (rank == cl_owner<kCl>(b)) dv[b] = A[colstart[b] + b] - 2.0f * qb.x * qb.y;
   }
 }
 
+template <int kCl>
 int cl_smem_bytes(int n) {
   int w = 0;
-  for (int r = 0; r < kTriCl; ++r) w = std::max(w, cl_words(n, r));
-  return n * (int)sizeof(float4) + (kTriCl + 1) * n * (int)sizeof(float) + n * (int)sizeof(int) +
+  for (int r = 0; r < kCl; ++r) w = std::max(w, cl_words<kCl>(n, r));
+  return n * (int)sizeof(float4) + (kCl + 1) * n * (int)sizeof(float) + n * (int)sizeof(int) +
          w * (int)sizeof(float);
 }
 
@@ -979,17 +987,21 @@ tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw
 
 bool tri_fits(Ctx* ctx, int n) {
   if (n <= kTriOneCtaMaxN) return true;
-  return n <= kTriMaxN && (size_t)cl_smem_bytes(n) + 1024 <= ctx->smem_optin;
+  if (n > kTriMaxN) return false;
+  const int bytes = n <= kTriCl4MaxN ? cl_smem_bytes<4>(n) : cl_smem_bytes<8>(n);
+  return (size_t)bytes + 1024 <= ctx->smem_optin;
 }
 
 blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* X, int* grp, float* gtop,
                       int* fail) {
   if (n < 1 || !tri_fits(ctx, n)) return ctx->fail(BLWS_EINVAL, "tri_stage: n = %d", n);
-  const bool on_cluster = n > kTriClusterMinN;
+  const bool on_cluster = n > kTriOneCtaMaxN;
+  const bool cl8 = n > kTriCl4MaxN;
   const size_t nn = (size_t)n * n;
   const int nblk = n > 2 ? (n - 2 + kWY - 1) / kWY : 0;
   // F (4 nn, first: 16-byte aligned), V, Y, reduction partial sums, WY factors, d, e, tau, lam, scale
-  const size_t parts = (size_t)std::max(kMaxGroups + kMaxChunks, kTriCl * (kClGroups + kClChunks)) * n;
+  const size_t parts = (size_t)std::max({kMaxGroups + kMaxChunks, 4 * (cl_groups<4>() + kClChunks),
+                                         8 * (cl_groups<8>() + kClChunks)}) * n;
   float* f = nullptr;
   BLWS_TRY(ctx->get(BUF_TRI, (nn * 6 + parts + (size_t)nblk * kWY * kWY + (size_t)n * 4 + 64) * sizeof(float),
                     (void**)&f));
@@ -1003,9 +1015,10 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   float* tauv = ev + n;
   float* lam = tauv + n;
   float* tscale = lam + n;
-  if (on_cluster) {
-    const int csmem = cl_smem_bytes(n);
-    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL, (const void*)tri_reduce_cluster_kernel, csmem));
+  if (on_cluster && cl8) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL8, (const void*)tri_reduce_cluster_kernel<8>, cl_smem_bytes<8>(n)));
+  } else if (on_cluster) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL, (const void*)tri_reduce_cluster_kernel<4>, cl_smem_bytes<4>(n)));
   } else {
     const int smem = (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float);
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
@@ -1016,8 +1029,10 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_INV, (const void*)tri_group_qr_kernel, gsmem));
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
-  if (on_cluster)
-    tri_reduce_cluster_kernel<<<kTriCl, kTriThreads, cl_smem_bytes(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
+  if (on_cluster && cl8)
+    tri_reduce_cluster_kernel<8><<<8, kTriThreads, cl_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
+  else if (on_cluster)
+    tri_reduce_cluster_kernel<4><<<4, kTriThreads, cl_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
   else
     tri_reduce_kernel<<<1, kTriThreads, (n * (n + 1) / 2 + 4 * n + 4) * (int)sizeof(float), s>>>(
         n, T, V, dv, ev, tauv, part, tscale);
