@@ -68,6 +68,7 @@ enum Buf {
   BUF_TRI,       // eigen-solver: tridiagonal-route scratch (FP32)
   BUF_EIG_GRP,   // eigen-solver: sorted group ids of the tridiagonal route
   BUF_OZ_G,      // FP64-equivalent general products: digit planes of both operands
+  BUF_RPCA_A,    // RPCA, FP64-equivalent mode: A = U diag(theta) V^T as a product (m x n)
   BUF_COUNT_
 };
 

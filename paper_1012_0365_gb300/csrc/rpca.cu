@@ -9,7 +9,10 @@
 // One fused pass over HBM per iteration (rpca_epilogue): with A kept
 // factored as U diag(theta) V^T it rebuilds each a_ij in registers (rank-c
 // tile product), forms Z, updates Y, shrinks the next E and writes the next
-// SVT input W.  Reads D, E, Y; writes E', Y, W.
+// SVT input W.  Reads D, E, Y; writes E', Y, W.  In the FP64-equivalent mode
+// the rank-c product is an FP64 ALU bound of its own (2c flops per element),
+// so there A = (U diag(theta)) V^T is formed first as a digit-plane
+// tensor-core product and the pass reads it (EP_PRE).
 #include <math.h>
 
 #include <algorithm>
@@ -29,7 +32,7 @@ __device__ inline double shrink(double x, double t) {
   return ax > 0.0 ? copysign(ax, x) : 0.0;
 }
 
-enum EpMode { EP_ITER = 0, EP_FINAL = 1 };
+enum EpMode { EP_ITER = 0, EP_FINAL = 1, EP_PRE = 2 };  // EP_PRE: as EP_ITER, A read from Aout
 
 // Rank-c tile reconstruction a = U[i,:] diag(th) V[j,:]^T plus the host update.
 // CT: arithmetic of the rank-c reconstruction (double, or float in the
@@ -53,7 +56,7 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
   for (int p = 0; p < 4; ++p)
 #pragma unroll
     for (int q = 0; q < 4; ++q) a[p][q] = CT(0);
-  for (int t0 = 0; t0 < c; t0 += kEpBK) {
+  for (int t0 = 0; MODE != EP_PRE && t0 < c; t0 += kEpBK) {
     for (int e = threadIdx.x; e < kEpBM * kEpBK; e += 256) {
       const int i = e % kEpBM, t = e / kEpBM;
       const int gi = i0 + i, gt = t0 + t;
@@ -91,7 +94,7 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
       const int gi = i0 + tx + 16 * p;
       if (gi >= m) continue;
       const size_t o = gi + (size_t)gj * ld;
-      const double av = (double)a[p][q];
+      const double av = MODE == EP_PRE ? Aout[o] : (double)a[p][q];
       if (MODE == EP_FINAL) {
         Aout[o] = av;
       } else {
@@ -106,7 +109,7 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
       }
     }
   }
-  if (MODE == EP_ITER) {
+  if (MODE != EP_FINAL) {
     red[threadIdx.x] = z2;
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
@@ -197,6 +200,14 @@ __global__ void count_nonzero(int m, int n, int ld, const double* __restrict__ E
     __syncthreads();
   }
   if (threadIdx.x == 0) atomicAdd(out, red[0]);  // integer sum: order-independent
+}
+
+// Us(:, t) = U(:, t) th_t, m x r
+__global__ void scale_columns(int m, int r, const double* __restrict__ U, const double* __restrict__ th,
+                              double* __restrict__ Us) {
+  const size_t total = (size_t)m * r;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    Us[e] = U[e] * th[e / m];
 }
 
 __global__ void thresholds(int r, const double* __restrict__ sigma, double eps, double* th) {
@@ -327,7 +338,11 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   int mixed_iters = 0;
   TcPlanes Wr{}, Wc{};
   OzPlanes Or{}, Oc{};
-  if (fp64tc) BLWS_TRY(oz_alloc(ctx, m, n, &Or, &Oc));
+  double* Apre = nullptr;
+  if (fp64tc) {
+    BLWS_TRY(oz_alloc(ctx, m, n, &Or, &Oc));
+    BLWS_TRY(ctx->get(BUF_RPCA_A, (size_t)ld * n, &Apre));
+  }
   if (mixed) {
     const int ldr = tc_ld(n), ldc = tc_ld(m);
     float* wp = nullptr;
@@ -380,7 +395,20 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     thresholds<<<1, 256, 0, s>>>(sv, sig, eps, th);
     BLWS_CHECK_LAUNCH(ctx);
     const double mu_next = std::min(mu * p.rho, mu_bar);
-    if (mixed)
+    // FP64-equivalent mode: A = (U diag(theta)) V^T over the sv computed pairs
+    // (theta is zero past the count) as a digit-plane product, when it is
+    // large enough for gemm to route it there
+    if (fp64tc && sv >= 64) {
+      double* Us = nullptr;
+      BLWS_TRY(ctx->get(BUF_P2, (size_t)m * sv, &Us));  // CholeskyQR scratch, free here
+      scale_columns<<<std::min(ceil_div((long long)m * sv, 256), ctx->sms * 8), 256, 0, s>>>(
+          m, sv, Uw, th, Us);
+      BLWS_CHECK_LAUNCH(ctx);
+      BLWS_TRY(gemm(ctx, s, false, true, m, n, sv, 1.0, Us, m, Vw, n, 0.0, Apre, ld));
+      rpca_epilogue<EP_PRE, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                          Ecur, Enext, Y, W, Apre, mu, mu_next,
+                                                          lam, zpart);
+    } else if (mixed)
       rpca_epilogue<EP_ITER, float><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
                                                           Ecur, Enext, Y, W, nullptr, mu, mu_next,
                                                           lam, zpart);

@@ -69,7 +69,8 @@ size_t rpca_bytes(int m, int n, int ld, int k, int k_cold, int sv0, int precisio
   b += 3 * kb * kb * 8 + 9 * kb * kb * 4;  // T_k, eigen-solver scratch
   b += (m + n) * best * 8;                 // warm-start factors
   if (precision == BLWS_PREC_MIXED) b += (size_t)16 * m * n + 4 * N * best * 4;  // TF32 planes
-  if (precision == BLWS_PREC_FP64_TC) b += (size_t)28 * m * n + 28 * N * 128;      // BF16 digit planes
+  if (precision == BLWS_PREC_FP64_TC)  // BF16 digit planes; A as a product
+    b += (size_t)28 * m * n + 28 * N * 128 + (size_t)ld * n * 8;
   return b;
 }
 
