@@ -26,10 +26,14 @@ __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __restrict__ A,
                 int lda, const double* __restrict__ B, int ldb, double beta, double* C, int ldc,
                 double* __restrict__ part) {
-  constexpr int TM = BM / 16, TN = BN / 16;
+  // TX x TY threads over the tile, TM x TN outputs each: 16 x 16 threads, or
+  // for tiles narrower than 16 columns 256 / BN threads down the rows
+  constexpr int TX = BN >= 16 ? 16 : kThreads / BN, TY = kThreads / TX;
+  constexpr int TM = BM / TX, TN = BN / TY;
+  static_assert(TM >= 1 && TN >= 1 && TM * TX == BM && TN * TY == BN, "tile shape");
   __shared__ CT As[kBK][BM + 1];
   __shared__ CT Bs[kBK][BN + 1];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
@@ -63,9 +67,9 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
     for (int kk = 0; kk < kBK; ++kk) {
       CT a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + TX * i];
 #pragma unroll
-      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + TY * j];
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -75,11 +79,11 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
   }
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
-    const int gi = m0 + tx + 16 * i;
+    const int gi = m0 + tx + TX * i;
     if (gi >= M) continue;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
-      const int gj = n0 + ty + 16 * j;
+      const int gj = n0 + ty + TY * j;
       if (gj >= N) continue;
       const double av = (double)acc[i][j];
       if (part) {
@@ -170,14 +174,16 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
 }
 
 // The tile shape that wastes the fewest FMAs on padding (the DFMA pipe, not
-// shared-memory traffic, bounds every shape here); ties go to the larger tile.
+// shared-memory traffic, bounds every shape here); ties go to the earlier,
+// larger tile.  32 x 8 serves block widths just above a multiple of 16
+// (b = 101 pads to 104 instead of 112).
 template <typename CT, bool TA, bool TB>
 blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
                    int lda, const double* B, int ldb, double beta, double* C, int ldc) {
-  static constexpr int kShapes[4][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}};
+  static constexpr int kShapes[5][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}, {32, 8}};
   int best = 0;
   long long best_work = -1;
-  for (int t = 0; t < 4; ++t) {
+  for (int t = 0; t < 5; ++t) {
     const long long work = (long long)ceil_div(M, kShapes[t][0]) * kShapes[t][0] *
                            ((long long)ceil_div(N, kShapes[t][1]) * kShapes[t][1]);
     if (best_work < 0 || work < best_work) {
@@ -189,7 +195,8 @@ blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, 
     case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
     case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    default: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 3: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    default: return launch_tiles<CT, TA, TB, 32, 8>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   }
 }
 
