@@ -37,13 +37,14 @@ __device__ __forceinline__ double rsqrt_newton(double p) {
 
 constexpr double kPivMin = 1e-10;
 constexpr double kPivMinF32 = 1e-6;
-constexpr double kNearIdErr = 2e-16;  // error allowed in L, elementwise
+constexpr double kNearIdErr = 2e-16;     // error allowed in L, elementwise (FP64 Gram matrices)
+constexpr double kNearIdErrF32 = 1e-10;  // the same with FP32 Gram matrices (resolved to ~1e-7)
 
 // Near-identity shortcut.  When the equilibrated Gram matrix is I + E with
-// every off-diagonal |E_ij| <= e_b = sqrt(kNearIdErr / b) (about 1.4e-9 at
-// b = 101: the columns are already orthonormal to that level, as after a
-// first CholeskyQR pass), its Cholesky factor is L = I + tril(E) and
-// L^-1 = I - tril(E), each to within b e_b^2 = kNearIdErr elementwise
+// every off-diagonal |E_ij| <= e_b = sqrt(err / b) (err = kNearIdErr: about
+// 1.4e-9 at b = 101, the columns already orthonormal to that level, as after
+// a first CholeskyQR pass), its Cholesky factor is L = I + tril(E) and
+// L^-1 = I - tril(E), each to within b e_b^2 = err elementwise
 // (L L^T = I + E + tril(E) tril(E)^T), so S and B follow without a
 // factorisation.  The pivots are then 1 to that accuracy;
 // a live column whose scale is within a factor 1 + 1e-6 of the deflation
@@ -52,8 +53,8 @@ constexpr double kNearIdErr = 2e-16;  // error allowed in L, elementwise
 // non-finite entry sends the matrix to the full path.  Every thread of the
 // block calls it (it ends in a block-wide vote).
 __device__ bool near_identity(int b, const double* __restrict__ G, const double* d,
-                              const double* dinv, const int* dead, double thr) {
-  const double eb = sqrt(kNearIdErr / b);
+                              const double* dinv, const int* dead, double thr, double err) {
+  const double eb = sqrt(err / b);
   int slow = 0;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e % b, j = e / b;
@@ -95,8 +96,8 @@ __device__ void near_identity_write(int b, const double* __restrict__ G, const d
 // work: 2 b^2 doubles (shared or global).
 __global__ void __launch_bounds__(1024)
 chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict__ scale_ptr,
-                  double tol, double pivmin, double* __restrict__ S, double* __restrict__ Bout,
-                  double* gwork, int use_smem) {
+                  double tol, double pivmin, double near_err, double* __restrict__ S,
+                  double* __restrict__ Bout, double* gwork, int use_smem) {
   extern __shared__ double smem[];
   double* L = use_smem ? smem : gwork;          // b x b, ld b (lower used)
   double* Li = L + (size_t)b * b;               // inverse of L
@@ -117,7 +118,7 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
     dinv[j] = dz ? 1.0 : 1.0 / dj;
   }
   __syncthreads();
-  if (near_identity(b, G, d, dinv, dead, thr)) {
+  if (near_identity(b, G, d, dinv, dead, thr, near_err)) {
     near_identity_write(b, G, d, dinv, dead, S, Bout, tid, nt);
     return;
   }
@@ -255,7 +256,8 @@ __device__ inline void tile_of_lin(int lin, int& it, int& jt) {
 
 __global__ void __cluster_dims__(kCC, 1, 1) __launch_bounds__(kCThreads)
 chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restrict__ scale_ptr,
-                    double tol, double pivmin, double* __restrict__ S, double* __restrict__ Bout) {
+                    double tol, double pivmin, double near_err, double* __restrict__ S,
+                    double* __restrict__ Bout) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ double smem[];
   const CholLayout lay(b);
@@ -291,7 +293,7 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
   __syncthreads();
   // every CTA takes the same decision from the same data; none has touched
   // another's shared memory yet, so all may leave here
-  if (near_identity(b, G, d, dinv, dead, thr)) {
+  if (near_identity(b, G, d, dinv, dead, thr, near_err)) {
     near_identity_write(b, G, d, dinv, dead, S, Bout, rank * kCThreads + tid, kCC * kCThreads);
     return;
   }
@@ -437,12 +439,12 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
 }
 
 blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const double* scale,
-                       double tol, double pivmin, double* S, double* B, double* gwork) {
+                       double tol, double pivmin, double near_err, double* S, double* B, double* gwork) {
   if (b > 1024) return ctx->fail(BLWS_EINVAL, "block width %d exceeds 1024", b);
   if (b <= kCMaxB) {
     const size_t bytes = CholLayout(b).total * sizeof(double);
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL_CLUSTER, (const void*)chol_cluster_kernel, (int)bytes));
-    chol_cluster_kernel<<<kCC, kCThreads, bytes, s>>>(b, G, scale, tol, pivmin, S, B);
+    chol_cluster_kernel<<<kCC, kCThreads, bytes, s>>>(b, G, scale, tol, pivmin, near_err, S, B);
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
   }
@@ -451,8 +453,8 @@ blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const d
   if (use_smem) {
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_CHOL, (const void*)chol_equil_kernel, (int)need));
   }
-  chol_equil_kernel<<<1, 1024, use_smem ? need : 0, s>>>(b, G, scale, tol, pivmin, S, B, gwork,
-                                                          use_smem);
+  chol_equil_kernel<<<1, 1024, use_smem ? need : 0, s>>>(b, G, scale, tol, pivmin, near_err, S, B,
+                                                          gwork, use_smem);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
@@ -473,13 +475,14 @@ blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld, 
   BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, R, ld, R, ld, 0.0, G, b, fp32));
   // with FP32 Gram matrices a pivot is only resolved down to ~1e-6
   const double pivmin = fp32 ? kPivMinF32 : kPivMin;
-  BLWS_TRY(chol_equil(ctx, s, b, G, scale, tol, pivmin, S, B1, work));
+  const double near_err = fp32 ? kNearIdErrF32 : kNearIdErr;
+  BLWS_TRY(chol_equil(ctx, s, b, G, scale, tol, pivmin, near_err, S, B1, work));
   BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, R, ld, S, b, 0.0, tmp, ld, fp32));
   // pass 2 (columns are now unit or zero: same deflation rule against 1)
   BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, tmp, ld, tmp, ld, 0.0, G, b, fp32));
   double* one = nullptr;
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &one));
-  BLWS_TRY(chol_equil(ctx, s, b, G, one + SLOT_ONE, 0.5, pivmin, S, B2, work));
+  BLWS_TRY(chol_equil(ctx, s, b, G, one + SLOT_ONE, 0.5, pivmin, near_err, S, B2, work));
   BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, tmp, ld, S, b, 0.0, X, ld, fp32));
   // B = B2 B1
   BLWS_TRY(gemm(ctx, s, false, false, b, b, b, 1.0, B2, b, B1, b, 0.0, B, b));
