@@ -42,6 +42,7 @@ def test_defaults(lib):
     cfg = blws.BlwsConfig()
     assert lib.blws_config_default(ctypes.byref(cfg)) == 0
     assert (cfg.k, cfg.k_cold, cfg.precision) == (3, 4, 0)
+    assert (cfg.start, cfg.warm) == (0, 1)   # mixed start, warm restarts (Section 4.1)
     p = blws.RpcaParams()
     assert lib.rpca_params_default(ctypes.byref(p)) == 0
     assert p.tol == 1e-7 and p.rho == 1.5 and p.sv0 == 10 and p.mu_bar_ratio == 1e7
@@ -69,6 +70,19 @@ def test_null_arguments_are_rejected_without_a_gpu(lib):
     assert cfg.workers == 8 and cfg.hbm_budget == 0 and cfg.cfg.k == 3
 
 
+def test_invalid_configurations_are_rejected_before_any_device_call(lib):
+    # checked before the library touches a device, so this runs without a GPU
+    for field, bad in (("k", 0), ("k_cold", 0), ("precision", 3), ("start", 2), ("start", -1),
+                       ("warm", 2)):
+        cfg = blws.BlwsConfig()
+        lib.blws_config_default(ctypes.byref(cfg))
+        setattr(cfg, field, bad)
+        h = ctypes.c_void_p()
+        assert lib.blws_create(ctypes.byref(h), ctypes.byref(cfg)) == blws.EINVAL, field
+        assert not h.value
+    assert lib.blws_evd(None, None, 1, 1, 0.0, 1, None, 0, None, 0, None, None, None, None) == blws.EINVAL
+
+
 def test_request_bytes_grow_with_the_problem(lib):
     # the admission weight: RPCA holds Y, W and a second E (3 m n doubles) plus
     # the Lanczos blocks; mixed precision adds the TF32 planes (16 m n bytes)
@@ -78,6 +92,9 @@ def test_request_bytes_grow_with_the_problem(lib):
     b64 = lib.blws_request_bytes(ctypes.byref(req), 0)
     bmx = lib.blws_request_bytes(ctypes.byref(req), 1)
     assert b64 >= 3 * 1000 * 800 * 8 and bmx - b64 >= 16 * 1000 * 800
+    # the FP64-equivalent mode: 7 BF16 digit planes in each orientation and A as a product
+    btc = lib.blws_request_bytes(ctypes.byref(req), 2)
+    assert btc - b64 >= 28 * 1000 * 800 + 8 * 1000 * 800
     req.m, req.ld = 2000, 2000
     assert lib.blws_request_bytes(ctypes.byref(req), 0) > b64
     mc = blws.Request()
