@@ -60,7 +60,7 @@ CASES = [
     # m, n, rank of W, w (warm), r (out), k
     (40, 30, 4, 4, 5, 2),
     (67, 41, 6, 5, 7, 3),
-    (200, 200, 10, 11, 11, 3),   # config-1 shape, block 11, k = 3
+    (200, 200, 10, 11, 11, 3),   # the 200 x 200 rank-10 shape, block 11, k = 3
     (300, 17, 3, 3, 4, 2),       # tall, ragged
     (17, 300, 3, 4, 4, 3),       # wide
     (129, 130, 20, 18, 24, 3),   # width not a multiple of any tile, padding columns

@@ -94,7 +94,7 @@ def test_rpca_matches_oracle(ctxs, torch_mod, m, n, rank, frac, seed):
     assert abs(info["iters"] - i64["iters"]) <= 1
 
 
-def test_full_size_config2(ctxs, torch_mod):
+def test_full_size_rpca_2000x2000(ctxs, torch_mod):
     from paper_1012_0365_gb300 import blws
     _, coz = ctxs
     D, L0, S0 = syn.rpca_problem(2000, 2000, 100, 0.10, amp=50.0, seed=0)

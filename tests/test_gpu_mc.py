@@ -1,6 +1,6 @@
 """GPU parity of mc_solve (SVT of [Cai08] and the proximal / FPC form, each
 SVT by BLWS over the CSR operator, through the C ABI) against the FP64
-oracle's full-SVD hosts, and the full-size config-3 workload by properties.
+oracle's full-SVD hosts, and the full-size 5000 x 5000 rank-50 workload (10% observed) by properties.
 
 Both hosts stop on the observed residual, and two runs stopped at tol 1e-4
 can sit ~1e-5 apart on slightly different trajectories; so parity is taken
@@ -109,7 +109,7 @@ def test_empty_pattern(ctx, torch_mod):
     assert info["rank"] == 0 and U.shape == (20, 0)
 
 
-def test_full_size_config3(ctx, torch_mod):
+def test_full_size_mc_5000x5000(ctx, torch_mod):
     # m = n = 5000, rank 50, 10% observed: Table 2 pattern (relerr ~1.6e-4)
     P = syn.mc_problem(5000, 5000, 50, 0.10, seed=0)
     U, th, V, info = run(ctx, torch_mod, P, max_rank=200)

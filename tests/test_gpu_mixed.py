@@ -118,7 +118,7 @@ def test_mixed_svt_matches_fp64_svt(ctxs, torch_mod):
     assert rel(Am, A64) < 1e-5
 
 
-def test_mixed_full_size_config2(ctxs, torch_mod):
+def test_mixed_full_size_rpca_2000x2000(ctxs, torch_mod):
     from paper_1012_0365_gb300 import blws
     _, cmx = ctxs
     D, L0, S0 = syn.rpca_problem(2000, 2000, 100, 0.10, amp=50.0, seed=0)

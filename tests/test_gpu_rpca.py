@@ -45,7 +45,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("m,n,rank,frac,seed", [
-    (200, 200, 10, 0.05, 0),    # config 1
+    (200, 200, 10, 0.05, 0),    # 200 x 200, rank 10, 5% corrupted
     (61, 47, 3, 0.05, 1),       # ragged, not a tile multiple
     (47, 61, 3, 0.05, 2),
     (400, 40, 2, 0.10, 3),      # tall
@@ -63,7 +63,7 @@ def test_rpca_matches_oracle(ctx, torch_mod, m, n, rank, frac, seed):
     assert abs(info["iters"] - ref["iters"]) <= max(6, ref["iters"] // 5)
 
 
-def test_config1_default_tol_pattern(ctx, torch_mod):
+def test_200x200_default_tol_pattern(ctx, torch_mod):
     # at the host's default tol 1e-7: rank 10, ~2000 corrupted entries found
     D, L0, S0 = syn.rpca_problem(200, 200, 10, 0.05, amp=50.0, seed=0)
     A, E, info = solve(ctx, torch_mod, D)
@@ -98,8 +98,8 @@ def test_max_iter_reports_noconv(ctx, torch_mod):
 
 
 @pytest.mark.parametrize("m,n,rank", [(2000, 2000, 100), (20000, 200, 5)])
-def test_full_size_config2_properties(ctx, torch_mod, m, n, rank):
-    # the bench workload (config 2, square and video-like tall cases)
+def test_full_size_bench_workloads_properties(ctx, torch_mod, m, n, rank):
+    # the bench workload (2000 x 2000 rank 100, and the tall 20000 x 200 rank-5 case)
     D, L0, S0 = syn.rpca_problem(m, n, rank, 0.10, amp=50.0, seed=0)
     A, E, info = solve(ctx, torch_mod, D, tol=1e-9)
     assert info["status"] == 0

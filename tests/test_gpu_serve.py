@@ -4,7 +4,7 @@
   one-worker server with nothing else queued, and the same request solved
   while seven other workers run other solves, give bit-identical outputs
   (every reduction has a fixed order; no floating-point atomics).
-* Results in the mix still match the FP64 oracle (config 1 and a ragged
+* Results in the mix still match the FP64 oracle (200 x 200 rank 10 and a ragged
   case) within the parity bar of the direct solver.
 * Admission keeps the admitted requests' estimated bytes within the budget
   (a request larger than the whole budget runs alone).
