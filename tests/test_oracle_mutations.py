@@ -54,3 +54,41 @@ def test_pins_catch_wrong_shrink_sign(monkeypatch):
     D, L0, S0 = syn.rpca_problem(60, 60, 3, 0.05, seed=1)
     out = orp.rpca_ialm_full(D, tol=1e-8, max_iter=200)
     assert np.linalg.norm(out["A"] - L0) / np.linalg.norm(L0) > 1e-3
+
+
+def _evd_whole_space_error():
+    lam = [9.0, 7.0, 4.0, 1.0, -0.5, -3.0, -12.0, 0.25]
+    Q = syn.orthonormal(8, 8, seed=33)
+    W = (Q * np.asarray(lam)) @ Q.T
+    out = oracle.blws_evd_ref(W, 2.0, None, 2, 3, syn.gaussian_block(8, 4, seed=34))
+    return np.abs(out["lam"] - np.array([9.0, 7.0, 4.0])).max()
+
+
+def test_pins_catch_magnitude_ordering_in_bl_evd(monkeypatch):
+    # Algorithm 3 orders the eigenvalues of T_k algebraically; ordering by
+    # magnitude would put -12 first on an indefinite W
+    def bad_bl_evd(apply, X1, k, r, full_reorth=False):
+        Xs, Ms, Bs, _ = ob.block_lanczos(apply, X1, k, full_reorth)
+        lam, Z = np.linalg.eigh(ob.assemble_T(Ms, Bs))
+        order = np.argsort(-np.abs(lam), kind="stable")
+        return np.hstack(Xs) @ Z[:, order][:, :r], lam[order][:r]
+    assert _evd_whole_space_error() < 1e-12
+    monkeypatch.setattr(ob, "bl_evd", bad_bl_evd)
+    assert _evd_whole_space_error() > 1e-6
+
+
+def test_pins_catch_a_start_block_without_the_warm_columns(monkeypatch):
+    # BLWS's start block is the previous subspace: dropping it (random start
+    # only) loses the exactness of an invariant warm start at k = 1
+    lam = np.array([10.0, 6.0, 3.0, -1.0, -2.0, 0.5, 1.5, -8.0, 2.0, 0.0])
+    Q = syn.orthonormal(10, 10, seed=35)
+    W = (Q * lam) @ Q.T
+    ok = oracle.blws_evd_ref(W, 0.0, Q[:, :3], 1, 3)
+    assert np.abs(ok["lam"] - lam[:3]).max() < 1e-12
+    orig = ob.blws_evd_ref
+
+    def no_warm(W, eps, U0, k, r, G=None):
+        return orig(W, eps, None, k, r, syn.gaussian_block(W.shape[0], r, seed=36))
+    monkeypatch.setattr(oracle, "blws_evd_ref", no_warm)
+    bad = oracle.blws_evd_ref(W, 0.0, Q[:, :3], 1, 3)
+    assert np.abs(bad["lam"] - lam[:3]).max() > 1e-3
