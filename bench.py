@@ -280,11 +280,12 @@ def run_ablation(args):
            "config": {"workload": "rpca_2000x2000_r100 variants; size sweeps", "tol_rpca": 1e-7}}
     base = {"precision": 0}
     res["k_sweep"] = {str(k): rpca_case(2000, 100, dict(base, k=k), 2)[0] for k in (2, 3, 4)}
-    res["start"] = {"mixed [U;V]/sqrt2": rpca_case(2000, 100, dict(base, start=0), 2)[0],
+    default = res["k_sweep"]["3"]  # k = 3, mixed start, warm restarts
+    res["start"] = {"mixed [U;V]/sqrt2": default,
                     "standard [U;0]": rpca_case(2000, 100, dict(base, start=1), 2)[0]}
     # a cold (seeded Gaussian) block Lanczos of k_cold blocks in every outer iteration,
     # capped at 100 iterations: status -4 with the residual reached when it stalls
-    res["warm"] = {"warm (BLWS), k=3": rpca_case(2000, 100, dict(base, warm=1), 2)[0],
+    res["warm"] = {"warm (BLWS), k=3": default,
                    "cold every iteration, k_cold=4": rpca_case(2000, 100, dict(base, warm=0), 1, max_iter=100)[0],
                    "cold every iteration, k_cold=8": rpca_case(2000, 100, dict(base, warm=0, k_cold=8), 1,
                                                                max_iter=100)[0]}
