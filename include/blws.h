@@ -78,7 +78,7 @@ typedef struct {
                      draws extra start columns.  Default 0x5eed. */
   int device;     /* CUDA device ordinal the context binds to.  Default 0. */
   int start;      /* warm-start block of blws_svt, rpca_solve and mc_solve
-                     (Section 4.1):
+                     (Section 4.1; blws_evd has a single subspace and ignores it):
                      0 (default) the mixed start [U; V]/sqrt(2), 1 the
                      standard start [U; 0] the paper compares it with. */
   int warm;       /* 1 (default): every outer iteration of rpca_solve /
