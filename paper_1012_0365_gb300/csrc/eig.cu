@@ -607,7 +607,7 @@ blws_status sym_eig_level(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
     identity_minus<<<eb, 256, 0, s>>>(n, R);
     BLWS_CHECK_LAUNCH(ctx);
     BLWS_TRY(gemm(ctx, s, false, false, n, n, n, 1.0, T, n, X, n, 0.0, TX, n));
-    BLWS_TRY(gemm(ctx, s, true, false, n, n, n, 1.0, X, n, TX, n, 0.0, S, n));
+    BLWS_TRY(gemm_sym(ctx, s, true, false, n, n, 1.0, X, n, TX, n, S, n));  // X^T T X: one triangle
     oa_norms_partial<<<nparts, 256, 0, s>>>(n, S, R, T, tri ? grp : nullptr, part);
     BLWS_CHECK_LAUNCH(ctx);
     oa_lambda<<<1, 256, 0, s>>>(n, nparts, S, R, part, lam_u, delta);
@@ -755,7 +755,7 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(binv, hinv.data(), sizeof(double) * n2, cudaMemcpyHostToDevice, s));
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(bid, hid.data(), sizeof(int) * n2, cudaMemcpyHostToDevice, s));
   BLWS_TRY(gemm(ctx, s, false, false, n, n2, n, 1.0, T, n, Xu, n, 0.0, TX, n));
-  BLWS_TRY(gemm(ctx, s, true, false, n2, n2, n, 1.0, Xu, n, TX, n, 0.0, S, n2));
+  BLWS_TRY(gemm_sym(ctx, s, true, false, n2, n, 1.0, Xu, n, TX, n, S, n2));
   cluster_blocks<<<std::min(ceil_div((long long)n2 * n2, 256), ctx->sms * 4), 256, 0, s>>>(
       n2, S, bid, bmu, binv, K);
   BLWS_CHECK_LAUNCH(ctx);

@@ -25,7 +25,7 @@ template <typename CT, bool TA, bool TB, int BM, int BN>
 __global__ void __launch_bounds__(kThreads)
 gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __restrict__ A,
                 int lda, const double* __restrict__ B, int ldb, double beta, double* C, int ldc,
-                double* __restrict__ part) {
+                double* __restrict__ part, int sym) {
   // TX x TY threads over the tile, TM x TN outputs each: 16 x 16 threads, or
   // for tiles narrower than 16 columns 256 / BN threads down the rows
   constexpr int TX = BN >= 16 ? 16 : kThreads / BN, TY = kThreads / TX;
@@ -35,6 +35,9 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
   __shared__ CT Bs[kBK][BN + 1];
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // sym: the result is symmetric (M = N); a tile wholly below the diagonal is
+  // left to its mirror image
+  if (sym && m0 > n0 + BN - 1) return;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   CT acc[TM][TN];
@@ -88,9 +91,12 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
       const double av = (double)acc[i][j];
       if (part) {
         part[(size_t)blockIdx.z * M * N + gi + (size_t)gj * M] = av;
-      } else {
+      } else if (!sym) {
         double* c = C + gi + (size_t)gj * ldc;
         *c = beta == 0.0 ? alpha * av : fma(alpha, av, beta * *c);
+      } else if (gi <= gj) {  // (beta = 0) the upper triangle and its mirror, each written once
+        C[gi + (size_t)gj * ldc] = alpha * av;
+        C[gj + (size_t)gi * ldc] = alpha * av;
       }
     }
   }
@@ -102,7 +108,7 @@ gemm_f64_kernel(int M, int N, int K, int kchunk, double alpha, const double* __r
 // q + G, ... in order (loads issued 8 at a time), then the group adds its lanes
 // with a fixed shuffle tree -- a fixed order for given M, N, splits.
 __global__ void splitk_reduce(int M, int N, int splits, int G, double alpha, const double* __restrict__ part,
-                              double beta, double* C, int ldc) {
+                              double beta, double* C, int ldc, int sym) {
   const size_t total = (size_t)M * N;
   const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   const size_t nth = (size_t)gridDim.x * blockDim.x;
@@ -113,15 +119,21 @@ __global__ void splitk_reduce(int M, int N, int splits, int G, double alpha, con
     const size_t e = t / G;
     double acc = 0.0;
     if (e < total) {
+      // sym (M = N): an element below the diagonal sums its mirror's partials
+      size_t src = e;
+      if (sym) {
+        const size_t i = e % M, j = e / M;
+        if (i > j) src = j + i * (size_t)M;
+      }
       int z = q;
       for (; z + 7 * G < splits; z += 8 * G) {
         double v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(z + u * G) * total + e];
+        for (int u = 0; u < 8; ++u) v[u] = part[(size_t)(z + u * G) * total + src];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc += v[u];
       }
-      for (; z < splits; z += G) acc += part[(size_t)z * total + e];
+      for (; z < splits; z += G) acc += part[(size_t)z * total + src];
     }
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (q == 0 && e < total) {
@@ -139,7 +151,7 @@ constexpr int kF32MaxChunk = 256;
 template <typename CT, bool TA, bool TB, int BM, int BN>
 blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha,
                          const double* A, int lda, const double* B, int ldb, double beta,
-                         double* C, int ldc) {
+                         double* C, int ldc, bool sym) {
   const int tm = ceil_div(M, BM), tn = ceil_div(N, BN);
   const int tiles = tm * tn;
   // DFMA-bound: balance the SMs.  About 8 CTAs per SM (of which ~4 are
@@ -159,7 +171,7 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
   if (splits > 1) BLWS_TRY(ctx->get(BUF_SPLITK, (size_t)splits * M * N, &part));
   dim3 grid(tm, tn, splits);
   gemm_f64_kernel<CT, TA, TB, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, alpha, A, lda, B,
-                                                                ldb, beta, C, ldc, part);
+                                                                ldb, beta, C, ldc, part, sym ? 1 : 0);
   BLWS_CHECK_LAUNCH(ctx);
   if (splits > 1) {
     const size_t total = (size_t)M * N;
@@ -167,7 +179,7 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
     int G = 1;
     while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)ctx->sms * 8 * 256) G *= 2;
     const int blocks = (int)std::min<size_t>((total * G + 255) / 256, (size_t)ctx->sms * 8);
-    splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, alpha, part, beta, C, ldc);
+    splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, alpha, part, beta, C, ldc, sym ? 1 : 0);
     BLWS_CHECK_LAUNCH(ctx);
   }
   return BLWS_OK;
@@ -179,7 +191,7 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
 // (b = 101 pads to 104 instead of 112).
 template <typename CT, bool TA, bool TB>
 blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
-                   int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+                   int lda, const double* B, int ldb, double beta, double* C, int ldc, bool sym) {
   static constexpr int kShapes[5][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}, {32, 8}};
   int best = 0;
   long long best_work = -1;
@@ -192,11 +204,11 @@ blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, 
     }
   }
   switch (best) {
-    case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    case 3: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    default: return launch_tiles<CT, TA, TB, 32, 8>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    case 3: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    default: return launch_tiles<CT, TA, TB, 32, 8>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
   }
 }
 
@@ -268,6 +280,25 @@ __global__ void scale_kernel(int M, int N, double beta, double* C, int ldc) {
 
 }  // namespace
 
+namespace {
+
+blws_status gemm_any(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                     const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                     int ldc, bool fp32, bool sym) {
+  if (fp32) {
+    if (!ta && !tb) return gemm_t<float, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    if (ta && !tb) return gemm_t<float, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    if (!ta && tb) return gemm_t<float, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+    return gemm_t<float, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  }
+  if (!ta && !tb) return gemm_t<double, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  if (ta && !tb) return gemm_t<double, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  if (!ta && tb) return gemm_t<double, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  return gemm_t<double, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+}
+
+}  // namespace
+
 blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
                  const double* A, int lda, const double* B, int ldb, double beta, double* C,
                  int ldc, bool fp32) {
@@ -282,16 +313,18 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
   if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)M * N * K >= kOzGemmMin &&
       std::min(M, N) >= 16 && K >= 64)
     return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (fp32) {
-    if (!ta && !tb) return gemm_t<float, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    if (ta && !tb) return gemm_t<float, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    if (!ta && tb) return gemm_t<float, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    return gemm_t<float, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  }
-  if (!ta && !tb) return gemm_t<double, false, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (ta && !tb) return gemm_t<double, true, false>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  if (!ta && tb) return gemm_t<double, false, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  return gemm_t<double, true, true>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  // A^T A (the Gram matrices): symmetric, so one triangle of tiles is computed
+  const bool sym = ta && !tb && A == B && lda == ldb && M == N && beta == 0.0;
+  return gemm_any(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, fp32, sym);
+}
+
+blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, double alpha,
+                     const double* A, int lda, const double* B, int ldb, double* C, int ldc, bool fp32) {
+  if (n <= 0) return BLWS_OK;
+  if (K <= 0 || (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)n * n * K >= kOzGemmMin &&
+                 n >= 16 && K >= 64))
+    return gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32);
+  return gemm_any(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32, true);
 }
 
 blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld, double* out) {
@@ -388,14 +421,14 @@ cudaError_t noalloc_gemm(cudaStream_t s, int sms, double* scratch, int M, int N,
   double* part = splits > 1 ? scratch : nullptr;
   dim3 grid(ceil_div(M, BM), ceil_div(N, BN), splits);
   gemm_f64_kernel<double, TA, false, BM, BN><<<grid, kThreads, 0, s>>>(M, N, K, kchunk, 1.0, A, lda, B, ldb,
-                                                               0.0, C, ldc, part);
+                                                               0.0, C, ldc, part, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   const size_t total = (size_t)M * N;
   int G = 1;  // the same lane-group rule as the context path
   while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)sms * 8 * 256) G *= 2;
   const int blocks = (int)std::min<size_t>((total * G + 255) / 256, (size_t)sms * 8);
-  splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, 1.0, part, 0.0, C, ldc);
+  splitk_reduce<<<blocks, 256, 0, s>>>(M, N, splits, G, 1.0, part, 0.0, C, ldc, 0);
   return cudaGetLastError();
 }
 

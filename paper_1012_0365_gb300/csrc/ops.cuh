@@ -17,6 +17,13 @@ namespace blws {
 blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K,
                  double alpha, const double* A, int lda, const double* B, int ldb,
                  double beta, double* C, int ldc, bool fp32 = false);
+// C = alpha op(A) op(B) (n x n) for a product known to be symmetric, such as
+// X^T (T X) with T symmetric: the tiles of one triangle are computed and
+// mirrored, so C is exactly symmetric.  (gemm does the same by itself for
+// A^T A.)
+blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, double alpha,
+                     const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                     bool fp32 = false);
 blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
                     const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
 constexpr double kOzGemmMin = 8.0e6;
