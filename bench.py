@@ -41,7 +41,7 @@ MC_WORKLOADS = {
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9  # SMs x DFMA/clk x flops x max clock
 # DRAM bytes of one product with the augmented matrix (both gemm_f64 launches), from the
 # ncu capture in profiles/gemm_f64_dual_apply_2000x2000_b101.md (b = 101)
-APPLY_TRAFFIC = {"rpca_2000x2000_r100": 33622272 + 33621504 + 256}
+APPLY_TRAFFIC = {"rpca_2000x2000_r100": 33622016 + 33624320}
 
 
 def dist_env():
