@@ -62,6 +62,7 @@ def symmetric_problem(m, rank, noise=0.05, seed=0):
     d = np.where(np.arange(rank) % 3 == 2, -1.0, 1.0) * rng.uniform(1.0, 2.0, rank) * m
     E = rng.standard_normal((m, m))
     W = (X * d) @ X.T / m + noise * math.sqrt(m) * (E + E.T) / 2
+    W = (W + W.T) / 2  # exactly symmetric (the product above is only to rounding)
     return W, int(np.count_nonzero(d > 0))
 
 

@@ -32,7 +32,7 @@ def test_mc_problem_is_a_sorted_csr_of_the_planted_matrix():
 
 def test_symmetric_problem():
     W, npos = syn.symmetric_problem(50, 6, seed=2)
-    np.testing.assert_allclose(W, W.T, rtol=0, atol=1e-12 * np.abs(W).max())
+    np.testing.assert_array_equal(W, W.T)
     assert npos == 4                                  # every third of 6 is negative
     lam = np.sort(np.linalg.eigvalsh(W))[::-1]
     assert lam[npos - 1] > 5 * abs(lam[npos])         # the positive signal stands above the rest
