@@ -250,3 +250,20 @@ def test_evd_of_augmented_matrix_gives_singular_values():
     X0 = np.vstack([U[:, :3], Vt[:3].T]) / np.sqrt(2.0)
     out = oracle.blws_evd_ref(augmented(W), 0.5, X0, 2, 3)
     np.testing.assert_allclose(out["lam"], s[:3], atol=1e-12)
+
+
+def test_warm_start_block_is_the_mixed_start_orthonormalised():
+    # Section 4.1: X~_1 = [U; V] / sqrt(2); with orthonormal U, V its columns are
+    # already orthonormal, so the QR keeps them (up to sign) and appends the
+    # extra columns' orthogonal complement
+    U = syn.orthonormal(20, 3, seed=50)
+    V = syn.orthonormal(15, 3, seed=51)
+    G = syn.gaussian_block(35, 2, seed=52)
+    X = oracle.warm_start_block(U, V, G)
+    np.testing.assert_allclose(X.T @ X, np.eye(5), atol=1e-13)
+    mixed = np.vstack([U, V]) / np.sqrt(2.0)
+    np.testing.assert_allclose(np.abs(np.sum(X[:, :3] * mixed, axis=0)), 1.0, atol=1e-13)
+    # the extra columns lie in span(mixed, G)
+    B = np.hstack([mixed, G])
+    P = B @ np.linalg.lstsq(B, X[:, 3:], rcond=None)[0]
+    np.testing.assert_allclose(P, X[:, 3:], atol=1e-12)
