@@ -38,10 +38,21 @@ MC_WORKLOADS = {
     # name: (m, n, rank, observed fraction)
     "mc_5000x5000_r50": (5000, 5000, 50, 0.10),
 }
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07e9 / 1e9  # SMs x DFMA/clk x flops x max clock
-# DRAM bytes of one product with the augmented matrix (both gemm_f64 launches), from the
-# ncu capture in profiles/gemm_f64_dual_apply_2000x2000_b101.md (b = 101)
+# DRAM bytes (read + write) of one product with the augmented matrix, both
+# gemm_f64_kernel<double, ., 0, 32, 8> launches, from one ncu capture of the
+# 2000 x 2000 workload at b = 101 with the current FP64 GEMM kernel
 APPLY_TRAFFIC = {"rpca_2000x2000_r100": 33622016 + 33624320}
+APPLY_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the two gemm_f64_kernel "
+                        "<double,{0,1},0,32,8> launches of blws_apply (b=101), bench.py --profile-apply")
+
+
+def fp64_peak_gflops(torch, sm_max_mhz):
+    """FP64 peak derived from unit counts: SMs (read from the device) x 2 DFMA
+    per clock per SM x 2 flops x the maximum SM clock (sampled by nvidia-smi,
+    else the GB300's 2070 MHz)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    return sms * 2 * 2 * mhz * 1e6 / 1e9, sms, mhz
 
 
 def dist_env():
@@ -118,30 +129,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_sample(D, iters_full, budget_s=20.0):
-    """Time the FP64 oracle (full-SVD inexact ALM) for a bounded number of
-    iterations and scale to one full solve (same iteration count)."""
+def blas_threads():
+    """Host threads the oracle's LAPACK/BLAS calls use (OpenBLAS: every core
+    unless an environment variable caps it)."""
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        v = os.environ.get(var)
+        if v and v.isdigit():
+            return int(v)
+    return os.cpu_count()
+
+
+def cpu_oracle_solve(D, tol):
+    """One complete solve of the FP64 oracle (inexact ALM with a full LAPACK SVD
+    in every iteration) on the host cores, timed; its A and E are the reference
+    every GPU leg's relerr_vs_oracle is taken against."""
     import oracle
-    # ||D||_2 set-up plus as many iterations as fit the budget (at least 2)
     t0 = time.perf_counter()
-    n_it = 0
-    setup = None
-    while True:
-        n_it += 1
-        t1 = time.perf_counter()
-        out = oracle.rpca_ialm_full(D, tol=0.0, max_iter=n_it)
-        dt = time.perf_counter() - t1
-        if setup is None:
-            setup = dt  # one iteration + set-up
-        if dt > budget_s / 3 or n_it >= 3:
-            break
-    per_iter = max((dt - setup) / max(n_it - 1, 1), 1e-9) if n_it > 1 else dt
-    est = setup + per_iter * (iters_full - 1)
-    return {"value": 1.0 / est, "unit": "solves/s", "cores": os.cpu_count(),
-            "kind": "oracle",
-            "sample": "%d of %d inexact-ALM iterations (full LAPACK SVD each) on the same "
-                      "workload, scaled to the full iteration count; %.1f s of CPU work"
-                      % (n_it, iters_full, time.perf_counter() - t0)}
+    out = oracle.rpca_ialm_full(D, tol=tol)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "solves/s", "cores": blas_threads(), "kind": "oracle",
+            "ms_per_solve": dt * 1e3, "iters": out["iters"], "rank": out["rank"],
+            "sample": "one complete solve of the same workload to tol %g (%d inexact-ALM iterations, "
+                      "full LAPACK SVD each, %.1f s)" % (tol, out["iters"], dt)}, out
+
+
+def relerr(torch, X, ref):
+    """||X - ref||_F / ||ref||_F, X a CUDA tensor and ref a host array."""
+    R = torch.from_numpy(np.ascontiguousarray(ref)).to(X.device)
+    return float(torch.linalg.norm(X - R) / torch.linalg.norm(R))
 
 
 def fullsvd_gpu_sample(torch, Dg, lam, iters_full, sample_iters=2):
@@ -239,6 +254,7 @@ def run_mc(args):
     nnz = int(vals.numel())
     flops = 4.0 * nnz * b
     achieved = flops / (spmm_ms / 1e3) / 1e9
+    peak = fp64_peak_gflops(torch, None)[0]
     lat = np.array(ms)
     return {"metric": "mc_solves_per_s", "value": args.steps / (float(np.sum(ms)) / 1e3), "unit": "solves/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)),
@@ -249,11 +265,31 @@ def run_mc(args):
             "solve": {"iters": info["iters"], "rank": info["rank"], "residual": info["residual"],
                       "relerr_vs_planted": rel},
             "roofline": {"kernel": "spmm_rows (S X_v and S^T X_u, b=%d)" % b, "bound": "alu",
-                         "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                         "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
                          "ms_per_product": spmm_ms,
                          "note": "blws_apply on the sparse operator with a prebuilt CSC mirror (includes "
                                  "the row-major copy of X)"}}
+
+
+def mc_oracle_parity(torch):
+    """Matrix completion against the FP64 oracle on a small case (200 x 200,
+    rank 5, 6 samples per degree of freedom): SVT of [Cai08] run to tol 1e-8
+    on both sides approaches the unique minimiser, where the iterates can be
+    compared (the oracle takes a full LAPACK SVD per iteration)."""
+    import oracle
+    from paper_1012_0365_gb300 import blws, synthetic as syn
+    m = n = 200
+    r = 5
+    P = syn.mc_problem(m, n, r, 6 * r * (m + n - r) / (m * n), seed=0)
+    ctx = blws.Context(k=3)
+    U, th, V, info = ctx.mc_solve(m, n, torch.from_numpy(P["rowptr"]).cuda(), torch.from_numpy(P["cols"]).cuda(),
+                                  torch.from_numpy(P["vals"]).cuda(), max_rank=60, tol=1e-8, max_iter=3000)
+    ref = oracle.mc_svt_full(m, n, P["rows"], P["cols"], P["vals"], tol=1e-8, max_iter=3000)
+    X = ((U * th) @ V.t()).cpu().numpy()
+    Xr = (ref["U"] * ref["th"]) @ ref["V"].T
+    return {"workload": "mc_200x200_r5_6dof", "tol": 1e-8, "iters": info["iters"], "oracle_iters": ref["iters"],
+            "relerr_vs_oracle": float(np.linalg.norm(X - Xr) / np.linalg.norm(Xr))}
 
 
 def run_ablation(args):
@@ -532,7 +568,13 @@ def run_serve(args):
 
 
 def run_reference(args, ws, rank):
-    """--impl reference: the FP64 CPU oracle on the host cores."""
+    """--impl reference: the FP64 CPU oracle (full-SVD inexact ALM) on the host
+    cores, on the same workload.  One step is one outer iteration of the oracle
+    (its full SVD dominates and costs the same in every iteration); the
+    set-up (||D||_2 by a full SVD, Y_0, mu_0) is timed once, apart.  W warm-up
+    iterations run untimed, then K timed ones; the solves/s figure is
+    1 / (set-up + iterations-per-solve x mean iteration time), with the
+    oracle's own iteration count on this workload (--ref-iters)."""
     from paper_1012_0365_gb300 import synthetic as syn
     import oracle
     if rank != 0:
@@ -541,29 +583,28 @@ def run_reference(args, ws, rank):
         return {"impl": "reference", "unavailable": "the CPU reference arm is defined on the RPCA workloads"}
     m, n, r, f = WORKLOADS[args.workload]
     D, L0, _ = syn.rpca_problem(m, n, r, f, seed=0)
-    # one full solve's iteration count is fixed by the workload (the GPU path
-    # needs the same count within one): measure it on a short oracle run is too
-    # slow at full size, so take it from the planted problem's known behaviour
-    iters_full = args.ref_iters
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        oracle.rpca_ialm_full(D, tol=0.0, max_iter=args.ref_sample_iters)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt / args.ref_sample_iters * iters_full)
-    value = 1.0 / float(np.mean(times))
+    stamps = []
+    t0 = time.perf_counter()
+    oracle.rpca_ialm_full(D, tol=0.0, max_iter=args.warmup + args.steps,
+                          progress=lambda: stamps.append(time.perf_counter()))
+    setup = stamps[0] - t0
+    iters = np.diff(np.array(stamps))           # one entry per outer iteration
+    timed = iters[args.warmup:args.warmup + args.steps]
+    per_iter = float(np.mean(timed))
+    solve_s = setup + args.ref_iters * per_iter
+    value = 1.0 / solve_s
     return {"metric": "rpca_solves_per_s", "value": value, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_iter,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "corrupt": f,
-                       "tol": args.tol},
-            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                       "tol": args.tol, "step": "one outer inexact-ALM iteration of the oracle"},
+            "ms_per_solve": 1e3 * solve_s, "setup_ms": 1e3 * setup,
+            "cpu_baseline": {"kind": "oracle", "cores": blas_threads(), "value": value,
                              "unit": "solves/s",
-                             "sample": "each step: %d inexact-ALM iterations with full LAPACK "
-                                       "SVD, scaled to %d iterations per solve"
-                                       % (args.ref_sample_iters, iters_full)},
+                             "sample": "%d timed inexact-ALM iterations (full LAPACK SVD each) after %d "
+                                       "untimed, plus the set-up timed once; a solve = set-up + %d "
+                                       "iterations" % (args.steps, args.warmup, args.ref_iters)},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -580,8 +621,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fullsvd", action="store_true", help="skip the full-SVD GPU comparison leg")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision measurement")
+    ap.add_argument("--no-extra-legs", action="store_true",
+                    help="skip the matrix-completion, batch and serving sub-objects of the default line")
     ap.add_argument("--ref-iters", type=int, default=25)
-    ap.add_argument("--ref-sample-iters", type=int, default=2)
     ap.add_argument("--profile-solve", action="store_true",
                     help="run one untimed solve only (for ncu launch lists)")
     ap.add_argument("--profile-apply", action="store_true",
@@ -690,6 +732,7 @@ def main():
     total_ms = max_over_ranks(dist, float(np.sum(step_ms)), "cuda")
     value = job_rate(ws, args.steps, total_ms)
     relerr = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
+    kept = {"fp64": (A.clone(), E.clone())}  # for the relerr against the oracle, below
 
     # ---- end to end through the public API with host buffers ----
     e2e_ms = []
@@ -743,6 +786,7 @@ def main():
             ev1.synchronize()
             mixed_ms.append(ev0.elapsed_time(ev1))
         mrel = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
+        kept["mixed"] = (A.clone(), E.clone())
         mixed = {"value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(mixed_ms)), "cuda")),
                  "unit": "solves/s",
                  "ms_per_step": float(np.mean(mixed_ms)),
@@ -770,6 +814,7 @@ def main():
             ev1.synchronize()
             tc_ms.append(ev0.elapsed_time(ev1))
         trel = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
+        kept["fp64tc"] = (A.clone(), E.clone())
         fp64tc = {"value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(tc_ms)), "cuda")),
                   "unit": "solves/s",
                   "ms_per_step": float(np.mean(tc_ms)),
@@ -787,9 +832,36 @@ def main():
     if not args.no_fullsvd and ws == 1:
         lam = 1.0 / math.sqrt(max(m, n))
         fullsvd = fullsvd_gpu_sample(torch, Dg, lam, info["iters"])
+    # the other workloads of the metric, each as a compact sub-object: matrix
+    # completion (5000^2, rank 50, 10% observed), the uneven batch (256
+    # instances through the server) and one rate of the serving loop
+    extra = {}
+    if not args.no_extra_legs and ws == 1:
+        sub = argparse.Namespace(**vars(args))
+        sub.workload, sub.precision, sub.steps, sub.warmup, sub.profile_solve = (
+            "mc_5000x5000_r50", "fp64", 3, 1, False)
+        mcl = run_mc(sub)
+        extra["mc"] = {k: mcl[k] for k in ("value", "unit", "ms_per_step", "latency_ms", "solve",
+                                             "roofline", "config")}
+        extra["mc"]["steps"], extra["mc"]["warmup"] = sub.steps, sub.warmup
+        extra["mc"]["oracle_parity"] = mc_oracle_parity(torch)
+        sub = argparse.Namespace(**vars(args))
+        sub.precision, sub.batch_count, sub.workers = "fp64", 256, 16
+        bl = run_batch(sub)
+        extra["batch"] = {k: bl[k] for k in ("value", "unit", "config", "solved_ok", "relerr_vs_planted",
+                                             "latency_ms", "sequential", "speedup_vs_sequential")}
+        sub = argparse.Namespace(**vars(args))
+        sub.precision, sub.serve_rates, sub.serve_requests, sub.workers = "fp64", [0.5], 24, 16
+        sv = run_serve(sub)
+        extra["serve"] = {"capacity_solves_per_s": sv["value"], "config": sv["config"],
+                          "rate": sv["sweep"][0]}
     cpu = None
+    rel_oracle = {}
     if not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_oracle_sample(D, info["iters"])
+        cpu, ref = cpu_oracle_solve(D, args.tol)
+        for mode, (Am, Em) in kept.items():
+            rel_oracle[mode] = {"A": relerr(torch, Am, ref["A"]), "E": relerr(torch, Em, ref["E"])}
+    peak, sms, mhz = fp64_peak_gflops(torch, clocks.get("sm_max_mhz"))
     lat = np.array(step_ms)
     out = {
         "metric": "rpca_solves_per_s",
@@ -810,29 +882,35 @@ def main():
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "solve": {"iters": info["iters"], "rank": info["rank"], "nnzE": info["nnzE"],
-                  "residual": info["residual"], "relerr_vs_planted": relerr},
+                  "residual": info["residual"], "relerr_vs_planted": relerr,
+                  "relerr_vs_oracle": rel_oracle.get("fp64")},
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * n * 8,
                 "d2h_bytes_per_step": 2 * m * n * 8},
         "gpu_launches": int(launches),
         "roofline": {"kernel": "gemm_f64 (block product with the augmented matrix, b=%d)" % b,
-                     "bound": "alu", "achieved": achieved * 1e3, "peak": FP64_PEAK_GFLOPS,
-                     "unit": "GFLOP/s", "frac": achieved * 1e3 / FP64_PEAK_GFLOPS,
+                     "bound": "alu", "achieved": achieved * 1e3, "peak": peak,
+                     "unit": "GFLOP/s", "frac": achieved * 1e3 / peak,
                      "traffic": APPLY_TRAFFIC.get(args.workload) if b == 101 else None,
+                     "traffic_source": APPLY_TRAFFIC_SOURCE if b == 101 else None,
                      "algorithmic_bytes": 2.0 * m * n * 8,
-                     "peak_source": "FP64 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts "
-                                    "and the maximum SM clock; MEASURED_PEAKS.json has no FP64 figure)"},
+                     "algorithmic_flops": flops,
+                     "peak_source": "FP64 derived from unit counts: %d SMs x 2 DFMA/clk x 2 x %.0f MHz "
+                                    "(MEASURED_PEAKS.json has no FP64 figure)" % (sms, mhz)},
         "clocks": clocks,
         "wall_s": t_wall,
     }
     if cpu:
         out["cpu_baseline"] = cpu
     if mixed:
+        mixed["relerr_vs_oracle"] = rel_oracle.get("mixed")
         out["mixed_precision"] = mixed
     if fp64tc:
+        fp64tc["relerr_vs_oracle"] = rel_oracle.get("fp64tc")
         out["fp64_tensor_core"] = fp64tc
     if fullsvd:
         out["fullsvd_same_gpu"] = fullsvd
         out["fullsvd_same_gpu"]["blws_speedup"] = value / fullsvd["value"]
+    out.update(extra)
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()

@@ -194,7 +194,9 @@ blws_status blws_evd(blws_ctx* ctx, const double* W, int m, int ldw, double eps,
  *   X   (m+n) x b, leading dimension ldx >= m+n (device, FP64)
  *   P   (m+n) x b, leading dimension ldp >= m+n (device, FP64, output)
  * The building block every BLWS step repeats k times; exported so callers
- * (and benchmarks) can run and time it on its own.  Does not synchronise. */
+ * (and benchmarks) can run and time it on its own.  Does not synchronise, so
+ * a bounded tensor-core wait that gives up inside it (BLWS_ETIMEOUT from the
+ * calls that synchronise) is not reported by this call. */
 blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx, int b,
                        double* P, int ldp, void* stream);
 
@@ -222,17 +224,53 @@ blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx
  * Every element the call reads from the array was written by the same call,
  * so nothing needs clearing between calls.
  *
- * The first call on a device (that device current) looks up the array's
- * device address and the SM count; make that first call before any stream
- * capture.  All calls share the one array: calls that can overlap on the
- * GPU (different streams, or different host threads) race on it and must
- * be serialised by the caller.
+ * Every call looks up the array's device address in the calling thread's
+ * current context (a lookup, no allocation or synchronisation), so the
+ * address is never stale after cudaDeviceReset and is right for a caller
+ * that runs in its own driver-API context.  The first call on a device also
+ * loads the library's device code and reads the SM count; make that first
+ * call before any stream capture.  All calls share the one array: calls that
+ * can overlap on the GPU (different streams, or different host threads) race
+ * on it and must be serialised by the caller.
  *
  * Returns BLWS_OK, BLWS_EINVAL (bad pointer or size, or scratch need above
  * the maximum), BLWS_ECUDA (a launch or the set-up failed) or BLWS_ENOTSUP
  * (device ordinal >= 64).  Does not synchronise. */
 blws_status blws_apply_noalloc(const double* W, int m, int n, int ldw, const double* X, int ldx,
                                int b, double* P, int ldp, void* stream);
+
+/* The dense block product every step of Algorithms 2 and 3 is built from
+ * (P = W~ X, M_l = X_l^T P_l, R_l = P_l - X_l M_l - X_{l-1} B_{l-1}^T, the
+ * CholeskyQR2 Gram matrices, the Ritz lift Q_k Z of Algorithm 3, and the
+ * refinement products of the T_k eigen-solver), exported with the
+ * arithmetic the context's precision gives it inside the procedure:
+ *   C = alpha op(A) op(B) + beta C,  op(X) = X^T when ta / tb is nonzero;
+ *   C is M x N, the inner size is K; A, B, C device FP64 column-major with
+ *   lda >= (ta ? K : M), ldb >= (tb ? N : K), ldc >= M.  beta == 0 never
+ *   reads C.
+ *   sym != 0: the product is known to be symmetric (A^T A, or X^T (T X) with
+ *   T symmetric); one triangle of tiles is computed and mirrored, so C is
+ *   exactly symmetric.  Needs M == N and beta == 0.
+ * In a BLWS_PREC_FP64_TC context products of at least 8e6 multiply-adds run
+ * as BF16 digit-plane products on the tensor cores (FP64-equivalent), the
+ * rest on the FP64 pipe; BLWS_PREC_MIXED uses FP32 arithmetic with FP64
+ * sums; BLWS_PREC_FP64 is FP64 throughout.  Synchronises `stream`.  Returns
+ * BLWS_EINVAL for bad sizes (nothing launched), BLWS_ETIMEOUT if a bounded
+ * tensor-core wait gave up, BLWS_ECUDA for a failed launch. */
+blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double alpha,
+                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                      int ldc, int sym, void* stream);
+
+/* Self-test of the bounded waits (no counterpart in the paper).  Every wait
+ * of the tensor-core kernels (a TMA copy or an MMA that should complete) is
+ * capped; when a cap is reached the kernel raises an error word and returns,
+ * and the calls that synchronise report BLWS_ETIMEOUT.  This call launches
+ * one small kernel that waits, through the same bounded wait, on a barrier
+ * nothing arrives at, with a cap of `polls` polls (1 .. 65536, well under a
+ * millisecond); it returns BLWS_ETIMEOUT, which shows the path from a wait
+ * that gives up to the status a caller sees.  No copy, MMA or tensor memory
+ * is involved.  Synchronises `stream`. */
+blws_status blws_wait_probe(blws_ctx* ctx, unsigned polls, void* stream);
 
 /* Robust PCA (Section 5, Table 1): min ||A||_* + lambda ||E||_1 s.t. D = A+E
  * by inexact ALM with every SVT evaluated by BLWS. */

@@ -34,8 +34,12 @@ def rank_predict(sv, svp, n):
 
 
 def rpca_ialm_full(D, lam=None, tol=1e-7, max_iter=1000, rho=1.5, sv0=10,
-                   mu0_factor=1.25, mu_bar_ratio=1e7):
-    """Inexact-ALM RPCA with full-SVD SVT.  Returns a dict of results."""
+                   mu0_factor=1.25, mu_bar_ratio=1e7, progress=None):
+    """Inexact-ALM RPCA with full-SVD SVT.  Returns a dict of results.
+
+    ``progress`` (optional, for timing only) is called with no arguments once
+    the set-up (||D||_2, Y_0, mu_0) is done and again at the end of every
+    iteration; it sees none of the arithmetic."""
     D = np.asarray(D, dtype=np.float64)
     m, n = D.shape
     if lam is None:
@@ -53,6 +57,8 @@ def rpca_ialm_full(D, lam=None, tol=1e-7, max_iter=1000, rho=1.5, sv0=10,
     hist = []
     svp = 0
     it = 0
+    if progress:
+        progress()
     for it in range(1, max_iter + 1):
         E = theta(D - A + Y / mu, lam / mu)
         U, th, V, svp = svt_factored(D - E + Y / mu, 1.0 / mu)
@@ -63,6 +69,8 @@ def rpca_ialm_full(D, lam=None, tol=1e-7, max_iter=1000, rho=1.5, sv0=10,
         mu = min(mu * rho, mu_bar)
         res = float(np.linalg.norm(Z, "fro")) / d_norm
         hist.append((res, svp, sv))
+        if progress:
+            progress()
         if res < tol:
             break
     return {"A": A, "E": E, "Y": Y, "iters": it, "rank": svp,

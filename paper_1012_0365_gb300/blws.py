@@ -21,7 +21,7 @@ EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_st
            "blws_svt", "blws_evd", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
            "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
-           "blws_csc_mirror")
+           "blws_csc_mirror", "blws_gemm", "blws_wait_probe")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -127,6 +127,8 @@ def load():
     lib.blws_server_stats_get.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.blws_server_destroy.argtypes = [vp]
     lib.blws_csc_mirror.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, vp, vp]
+    lib.blws_gemm.argtypes = [vp, ci, ci, ci, ci, ci, cd, vp, ci, vp, ci, cd, vp, ci, ci, vp]
+    lib.blws_wait_probe.argtypes = [vp, ctypes.c_uint, vp]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
@@ -298,6 +300,28 @@ class Context:
         if st != OK:
             self._raise(st, "blws_apply")
         return P
+
+    def gemm(self, A, B, C, alpha=1.0, beta=0.0, ta=False, tb=False, sym=False, stream=None):
+        """C = alpha op(A) op(B) + beta C with the context's block-product
+        arithmetic (blws_gemm).  A, B, C column-major FP64 CUDA tensors; op(X)
+        is X^T when ta / tb.  Synchronises.  Returns C."""
+        M, N = C.shape
+        K = A.shape[0] if ta else A.shape[1]
+        _check_colmajor(A, A.shape[0], A.shape[1], "A")
+        _check_colmajor(B, B.shape[0], B.shape[1], "B")
+        _check_colmajor(C, M, N, "C")
+        if (A.shape[1] if ta else A.shape[0]) != M or (B.shape[1] if tb else B.shape[0]) != K or \
+                (B.shape[0] if tb else B.shape[1]) != N:
+            raise ValueError("gemm: shapes do not match")
+        st = load().blws_gemm(self._h, int(ta), int(tb), M, N, K, float(alpha), _ptr(A), A.shape[0],
+                              _ptr(B), B.shape[0], float(beta), _ptr(C), M, int(sym), _stream(stream))
+        if st != OK:
+            self._raise(st, "blws_gemm")
+        return C
+
+    def wait_probe(self, polls=256, stream=None):
+        """Run the bounded-wait self-test; returns its status (ETIMEOUT expected)."""
+        return load().blws_wait_probe(self._h, int(polls), _stream(stream))
 
     def csc_mirror(self, m, n, rowptr, colidx, stream=None):
         """(colptr, rowidx, perm): the column-major mirror of a CSR pattern (int32 tensors)."""

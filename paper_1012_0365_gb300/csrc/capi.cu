@@ -43,7 +43,10 @@ blws_status Ctx::get(Buf b, size_t bytes, void** out) {
   if (bytes > cap[b]) {
     if (buf[b]) {
       // growth happens between solver phases; make sure nothing still uses it
-      BLWS_TRY_CUDA(this, cudaDeviceSynchronize());
+      if (sole_stream)
+        BLWS_TRY_CUDA(this, cudaStreamSynchronize(sole_stream));
+      else
+        BLWS_TRY_CUDA(this, cudaDeviceSynchronize());
       BLWS_TRY_CUDA(this, cudaFree(buf[b]));
       buf[b] = nullptr;
       cap[b] = 0;
@@ -63,6 +66,20 @@ blws_status Ctx::get(Buf b, size_t bytes, void** out) {
   return BLWS_OK;
 }
 
+blws_status Ctx::trim() {
+  if (sole_stream)
+    BLWS_TRY_CUDA(this, cudaStreamSynchronize(sole_stream));
+  else
+    BLWS_TRY_CUDA(this, cudaDeviceSynchronize());
+  for (int b = 0; b < BUF_COUNT_; ++b) {
+    if (b == BUF_SCAL || !buf[b]) continue;
+    BLWS_TRY_CUDA(this, cudaFree(buf[b]));
+    buf[b] = nullptr;
+    cap[b] = 0;
+  }
+  return BLWS_OK;
+}
+
 }  // namespace blws
 
 using blws::Ctx;
@@ -75,6 +92,20 @@ blws_status bind_device(blws_ctx* ctx) {
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return ctx->fail(BLWS_ECUDA, "cudaSetDevice(%d): %s", ctx->device, cudaGetErrorString(e));
   return BLWS_OK;
+}
+
+// The tensor-core kernels raise SLOT_TCERR when a bounded wait gives up.  Every
+// entry point that can launch one clears it first, and the ones that
+// synchronise report it (BLWS_ETIMEOUT) from the slots they copy back.
+blws_status clear_tc_error(blws_ctx* ctx, cudaStream_t s) {
+  double* scal = nullptr;
+  BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(scal + blws::SLOT_TCERR, 0, sizeof(double), s));
+  return BLWS_OK;
+}
+
+bool tc_error_seen(const blws_ctx* ctx) {
+  return *reinterpret_cast<const int*>(ctx->host_pinned + blws::SLOT_TCERR) != 0;
 }
 
 }  // namespace
@@ -251,6 +282,7 @@ blws_status blws_apply(blws_ctx* ctx, const blws_op* W, const double* X, int ldx
     return ctx->fail(BLWS_EINVAL, "blws_apply: bad sizes");
   BLWS_TRY(bind_device(ctx));
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BLWS_TRY(clear_tc_error(ctx, s));
   blws::Operator op;
   BLWS_TRY(make_operator(ctx, W, s, &op));
   BLWS_TRY(blws::blws_reserve(ctx, W->m, W->n, b, 1));
@@ -290,6 +322,7 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
   a.cold = (w == 0);
   a.standard = ctx->cfg.start == 1;
   a.k = a.cold ? ctx->cfg.k_cold : ctx->cfg.k;
+  BLWS_TRY(clear_tc_error(ctx, s));
   blws::TcPlanes Wr, Wc;
   blws::OzPlanes Or, Oc;
   BLWS_TRY(attach_planes(ctx, s, &op, &Wr, &Wc, &Or, &Oc));
@@ -302,6 +335,7 @@ blws_status blws_svt(blws_ctx* ctx, const blws_op* W, double eps, int r, const d
                                      cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   *count = *reinterpret_cast<int*>(ctx->host_pinned + blws::SLOT_COUNT);
+  if (tc_error_seen(ctx)) return ctx->fail(BLWS_ETIMEOUT, "blws_svt: a tensor-core wait ran out");
   return BLWS_OK;
 }
 
@@ -337,11 +371,13 @@ blws_status blws_evd(blws_ctx* ctx, const double* W, int m, int ldw, double eps,
   double* scal;
   BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
   int* cdev = reinterpret_cast<int*>(scal + blws::SLOT_COUNT);
+  BLWS_TRY(clear_tc_error(ctx, s));
   BLWS_TRY(blws::blws_run(ctx, s, op, a, U, m, nullptr, 0, lam, cdev));
   BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
                                      cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   *count = *reinterpret_cast<int*>(ctx->host_pinned + blws::SLOT_COUNT);
+  if (tc_error_seen(ctx)) return ctx->fail(BLWS_ETIMEOUT, "blws_evd: a tensor-core wait ran out");
   return BLWS_OK;
 }
 
@@ -406,6 +442,49 @@ blws_status mc_solve(blws_ctx* ctx, int m, int n, int nnz, const int* rowptr, co
   BLWS_TRY(bind_device(ctx));
   return blws::mc_run(ctx, reinterpret_cast<cudaStream_t>(stream), m, n, nnz, rowptr, colidx, vals,
                       q, max_rank, U, theta, V, info);
+}
+
+blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double alpha,
+                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
+                      int ldc, int sym, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (!A || !B || !C) return ctx->fail(BLWS_EINVAL, "blws_gemm: null argument");
+  if (M < 1 || N < 1 || K < 1 || lda < (ta ? K : M) || ldb < (tb ? N : K) || ldc < M ||
+      !std::isfinite(alpha) || !std::isfinite(beta))
+    return ctx->fail(BLWS_EINVAL, "blws_gemm: bad sizes or scalars");
+  if (sym && (M != N || beta != 0.0))
+    return ctx->fail(BLWS_EINVAL, "blws_gemm: a symmetric result needs M == N and beta == 0");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BLWS_TRY(clear_tc_error(ctx, s));
+  const bool f32 = ctx->cfg.precision == BLWS_PREC_MIXED;
+  if (sym)
+    BLWS_TRY(blws::gemm_sym(ctx, s, ta != 0, tb != 0, N, K, alpha, A, lda, B, ldb, C, ldc, f32));
+  else
+    BLWS_TRY(blws::gemm(ctx, s, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, f32));
+  double* scal;
+  BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  if (tc_error_seen(ctx)) return ctx->fail(BLWS_ETIMEOUT, "blws_gemm: a tensor-core wait ran out");
+  return BLWS_OK;
+}
+
+blws_status blws_wait_probe(blws_ctx* ctx, unsigned polls, void* stream) {
+  if (!ctx) return BLWS_EINVAL;
+  if (polls < 1 || polls > (1u << 16)) return ctx->fail(BLWS_EINVAL, "blws_wait_probe: polls in [1, 65536]");
+  BLWS_TRY(bind_device(ctx));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  BLWS_TRY(clear_tc_error(ctx, s));
+  BLWS_TRY(blws::wait_probe(ctx, s, polls));
+  double* scal;
+  BLWS_TRY(ctx->get(blws::BUF_SCAL, blws::SLOT_MAX, &scal));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * blws::SLOT_MAX,
+                                     cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  if (tc_error_seen(ctx)) return ctx->fail(BLWS_ETIMEOUT, "blws_wait_probe: the wait gave up after %u polls", polls);
+  return BLWS_OK;
 }
 
 }  // extern "C"

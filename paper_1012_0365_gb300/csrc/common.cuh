@@ -37,8 +37,10 @@ namespace blws {
 
 // ------------------------------------------------------------- workspace --
 // Named device buffers owned by the context, each grown on demand.  Growth
-// synchronises the device (cudaFree), so it happens outside steady state:
-// a solver sizes its buffers once before its first iteration.
+// frees the old buffer after the work that may still use it has finished (the
+// whole device, or only the context's own stream when it has one), so it
+// happens outside steady state: a solver sizes its buffers once before its
+// first iteration.
 enum Buf {
   BUF_Q = 0,     // Lanczos basis Q_k, (m+n) x (k b)
   BUF_P,         // W~ X_l / residual R_l, (m+n) x b
@@ -80,12 +82,18 @@ struct Ctx {
   void* buf[BUF_COUNT_] = {nullptr};
   size_t cap[BUF_COUNT_] = {0};
   double* host_pinned = nullptr;  // small pinned staging area for scalars
+  // set when every call on this context uses this one stream (a server
+  // worker): buffer growth then waits for that stream instead of the device
+  cudaStream_t sole_stream = nullptr;
   unsigned long long launches = 0; // kernels launched through this context
   char last_error[512] = {0};
 
   blws_status fail(blws_status code, const char* fmt, ...);
   // device buffer `b` with at least `bytes` bytes (grown on demand)
   blws_status get(Buf b, size_t bytes, void** out);
+  // free every workspace buffer but the scalar slots (the next call
+  // allocates again what it needs)
+  blws_status trim();
   // dynamic shared memory limit of a kernel.  The attribute belongs to the
   // kernel (process-wide, per device), not to a context: it only ever grows,
   // under a lock, so that contexts on other threads never lower it under a
@@ -97,6 +105,12 @@ struct Ctx {
   // (environment BLWS_EIG=jacobi at context creation)
   int eig_route = 0;
   unsigned long long tri_fallbacks = 0;  // tridiagonal stage results replaced by Jacobi
+  // device bytes the workspace holds now
+  size_t held_bytes() const {
+    size_t t = 0;
+    for (int b = 0; b < BUF_COUNT_; ++b) t += cap[b];
+    return t;
+  }
   template <typename T>
   blws_status get(Buf b, size_t count, T** out) {
     void* p = nullptr;

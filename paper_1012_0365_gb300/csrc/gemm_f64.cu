@@ -310,20 +310,21 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
   }
-  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)M * N * K >= kOzGemmMin &&
-      std::min(M, N) >= 16 && K >= 64)
-    return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
   // A^T A (the Gram matrices): symmetric, so one triangle of tiles is computed
   const bool sym = ta && !tb && A == B && lda == ldb && M == N && beta == 0.0;
+  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)M * N * K >= kOzGemmMin &&
+      std::min(M, N) >= 16 && K >= 64)
+    return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
   return gemm_any(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, fp32, sym);
 }
 
 blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, double alpha,
                      const double* A, int lda, const double* B, int ldb, double* C, int ldc, bool fp32) {
   if (n <= 0) return BLWS_OK;
-  if (K <= 0 || (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)n * n * K >= kOzGemmMin &&
-                 n >= 16 && K >= 64))
-    return gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32);
+  if (K <= 0) return gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32);
+  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)n * n * K >= kOzGemmMin && n >= 16 &&
+      K >= 64)
+    return oz_gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, true);
   return gemm_any(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32, true);
 }
 
@@ -364,34 +365,39 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-double* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
 int g_noalloc_sms[kNoAllocMaxDevices] = {0};
 
-// device address of the scratch array and the SM count, looked up once per
-// device with that device current
+// Device address of the scratch array in the current context, and the SM
+// count (looked up once per device).  The address is looked up on every call
+// (no allocation, no synchronisation): it belongs to a context, and a cached
+// copy would go stale after cudaDeviceReset or point into another context
+// when the caller runs in a driver-API context of its own.
 blws_status noalloc_setup(int dev, double** addr, int* sms) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return BLWS_ENOTSUP;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return BLWS_ECUDA;
+  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
-      cudaGetLastError();
-      return BLWS_ECUDA;
-    }
+  if (!g_noalloc_sms[dev]) {
     int count = 0;
     if (cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
       cudaGetLastError();
       return BLWS_ECUDA;
     }
     g_noalloc_sms[dev] = count;
-    g_noalloc_addr[dev] = static_cast<double*>(p);
   }
-  *addr = g_noalloc_addr[dev];
+  *addr = static_cast<double*>(p);
   *sms = g_noalloc_sms[dev];
   return BLWS_OK;
 }
 
-// the split-K factor the allocating path picks for this GEMM (same rule)
+// The split-K factor of this path.  It is deliberately coarser than the
+// allocating path's (about two CTAs per SM instead of eight, and only for an
+// inner dimension above 4 k-blocks), to bound the static scratch; the tile
+// shape follows N alone instead of the padding-minimising search.  So the
+// results agree with blws_apply to rounding, not bit for bit.
 template <int BM, int BN>
 int noalloc_splits(int sms, int M, int N, int K, int* kchunk) {
   const int tiles = ceil_div(M, BM) * ceil_div(N, BN);

@@ -69,6 +69,7 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
   }
   int* flag = reinterpret_cast<int*>(scal + SLOT_FLAG);
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), s));
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(scal + SLOT_TCERR, 0, sizeof(double), s));
   check_finite<<<std::min(ceil_div(nnz, 256), ctx->sms * 8), 256, 0, s>>>(nnz, vals, flag);
   BLWS_CHECK_LAUNCH(ctx);
   BLWS_TRY(sumsq(ctx, s, nnz, 1, vals, nnz, scal + SLOT_NORM));
@@ -171,6 +172,8 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
                                          cudaMemcpyDeviceToHost, s));
       BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
       c = *reinterpret_cast<int*>(ctx->host_pinned + SLOT_COUNT);
+      if (*reinterpret_cast<int*>(ctx->host_pinned + SLOT_TCERR))
+        return ctx->fail(BLWS_ETIMEOUT, "mc_solve: a tensor-core wait ran out");
       w = sk;
       // [Cai08]: if the last computed value is still above tau, widen by l
       if (c < sk || sk >= bcap) break;
@@ -211,6 +214,8 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
     BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     const double r2 = ctx->host_pinned[SLOT_NORM];
     if (!isfinite(r2)) return ctx->fail(BLWS_ENONFINITE, "mc_solve: iterate became non-finite");
+    if (*reinterpret_cast<int*>(ctx->host_pinned + SLOT_TCERR))
+      return ctx->fail(BLWS_ETIMEOUT, "mc_solve: a tensor-core wait ran out");
     res = sqrt(r2) / norm_pm;
     r_prev = c;
     if (res <= p.tol) {

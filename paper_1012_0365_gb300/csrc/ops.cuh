@@ -24,8 +24,11 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
 blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, double alpha,
                      const double* A, int lda, const double* B, int ldb, double* C, int ldc,
                      bool fp32 = false);
+// sym: the product is known to be symmetric (M = N, beta = 0): the result is
+// made exactly symmetric (each element below the diagonal from its mirror)
 blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
-                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc);
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                    bool sym = false);
 constexpr double kOzGemmMin = 8.0e6;
 
 // sum of squares of an M x N matrix (ld) into *out (device), deterministic
@@ -119,5 +122,10 @@ blws_status oz_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int l
 // planes in both orientations (Wr: m rows, Wc: n rows).
 blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const OzPlanes& Wc, int m, int n,
                           const double* X, int ldx, int b, double* P, int ldp);
+
+// Bounded-wait self-test: one CTA waits on an mbarrier nothing arrives at,
+// through the tensor-core kernels' bounded wait with `polls` polls, and sets
+// SLOT_TCERR when the wait gives up (the path a stalled copy or MMA takes).
+blws_status wait_probe(Ctx* ctx, cudaStream_t s, unsigned polls);
 
 }  // namespace blws

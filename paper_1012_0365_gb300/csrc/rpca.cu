@@ -273,6 +273,8 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   // norms of D: Frobenius, max-abs (and finiteness)
   int* nonfinite = reinterpret_cast<int*>(scal + SLOT_FLAG);
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(nonfinite, 0, sizeof(int), s));
+  // a bounded tensor-core wait that gave up in an earlier call is not this solve's
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(scal + SLOT_TCERR, 0, sizeof(double), s));
   BLWS_TRY(sumsq(ctx, s, m, n, D, ld, scal + SLOT_NORM));
   maxabs_partial<<<gb, 256, 0, s>>>(m, n, ld, D, red, nonfinite);
   BLWS_CHECK_LAUNCH(ctx);

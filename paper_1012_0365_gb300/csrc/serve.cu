@@ -3,11 +3,17 @@
 // non-blocking CUDA stream, fed from one FIFO queue with admission by device
 // memory.  Solves admitted together run concurrently on their streams.
 //
-// Admission: the head of the queue starts when a worker is idle and its
-// estimated device bytes fit into the budget minus what the running solves
-// hold (a request larger than the whole budget starts only when nothing else
-// runs).  Requests keep arrival order: a large head is not overtaken by
-// smaller ones behind it.
+// Admission: the head of the queue starts when a worker is idle and the device
+// bytes every worker would then hold fit the budget.  A worker holds the
+// larger of its running request's estimate and what its context's workspace
+// retains from earlier requests (workspace buffers only grow), so memory kept
+// by idle workers counts too.  When nothing runs, the head starts anyway (a
+// request larger than the whole budget runs alone), taken by the idle worker
+// that retains the most workspace, so that it reuses that memory instead of
+// adding to it.  A worker that finishes while the workers together hold more
+// than the budget frees its workspace.  Requests keep arrival order: a large
+// head is not overtaken by smaller ones behind it.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -49,6 +55,8 @@ struct blws_server {
   bool stopping = false;
   size_t in_use = 0;
   int running = 0;
+  std::vector<size_t> held;  // per worker: bytes its context's workspace retains
+  std::vector<size_t> est;   // per worker: estimate of its running request (0: idle)
   blws_server_stats stats{};
   blws_status start_status = BLWS_OK;
   int started = 0;
@@ -56,7 +64,11 @@ struct blws_server {
 
 namespace {
 
-size_t rpca_bytes(int m, int n, int ld, int k, int k_cold, int sv0, int precision) {
+// workspace every solve reserves whatever its size: the split-K partial sums
+// of the FP64 GEMMs (16 x SMs x 64 x 64 doubles) and the reduction partials
+size_t fixed_bytes(int sms) { return (size_t)16 * sms * 64 * 64 * 8 + (size_t)sms * 8 * 8 + 4096 * 8; }
+
+size_t rpca_bytes(int m, int n, int ld, int k, int k_cold, int sv0, int precision, int sms) {
   const size_t N = (size_t)m + n;
   const int pmin = std::min(m, n);
   // widest Lanczos block the solve is expected to reach: the rank prediction
@@ -71,17 +83,33 @@ size_t rpca_bytes(int m, int n, int ld, int k, int k_cold, int sv0, int precisio
   if (precision == BLWS_PREC_MIXED) b += (size_t)16 * m * n + 4 * N * best * 4;  // TF32 planes
   if (precision == BLWS_PREC_FP64_TC)  // BF16 digit planes; A as a product
     b += (size_t)28 * m * n + 28 * N * 128 + (size_t)ld * n * 8;
-  return b;
+  return b + fixed_bytes(sms);
 }
 
-size_t mc_bytes(int m, int n, int nnz, int max_rank, int k, int k_cold) {
+size_t mc_bytes(int m, int n, int nnz, int max_rank, int k, int k_cold, int sms) {
   const size_t N = (size_t)m + n;
   const size_t b = (size_t)std::max(1, max_rank);
   const size_t kb = (size_t)std::max(k, k_cold) * b;
   size_t s = (size_t)nnz * (4 + 4 + 8 + 8) + ((size_t)n + 1) * 4;  // CSC mirror, iterate values
   s += N * kb * 8 + 2 * N * b * 8 + 3 * kb * kb * 8 + 9 * kb * kb * 4;
   s += 2 * N * b * 8;  // factors of the iterate
-  return s;
+  return s + fixed_bytes(sms);
+}
+
+// the idle worker that retains the most workspace (lowest index on ties)
+int largest_idle(const blws_server* srv) {
+  int best = -1;
+  for (size_t v = 0; v < srv->held.size(); ++v)
+    if (srv->est[v] == 0 && (best < 0 || srv->held[v] > srv->held[best])) best = (int)v;
+  return best;
+}
+
+// device bytes all workers hold if `worker` takes a request of `need` bytes
+size_t held_with(const blws_server* srv, int worker, size_t need) {
+  size_t t = 0;
+  for (size_t v = 0; v < srv->held.size(); ++v)
+    t += std::max(srv->held[v], (int)v == worker ? need : srv->est[v]);
+  return t;
 }
 
 void worker_main(blws_server* srv, int index) {
@@ -90,13 +118,13 @@ void worker_main(blws_server* srv, int index) {
   blws_status st = blws_create(&ctx, &srv->cfg.cfg);
   if (st == BLWS_OK && cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess)
     st = BLWS_ECUDA;
+  if (st == BLWS_OK) ctx->sole_stream = stream;  // growth waits for this worker's stream only
   {
     std::lock_guard<std::mutex> lock(srv->mu);
     if (st != BLWS_OK && srv->start_status == BLWS_OK) srv->start_status = st;
     ++srv->started;
   }
   srv->cv_done.notify_all();
-  (void)index;
   for (;;) {
     Job job;
     {
@@ -104,12 +132,14 @@ void worker_main(blws_server* srv, int index) {
       srv->cv_work.wait(lock, [&] {
         if (srv->queue.empty()) return srv->stopping;
         const size_t need = srv->queue.front().bytes;
-        return srv->running == 0 || srv->in_use + need <= srv->cfg.hbm_budget;
+        if (held_with(srv, index, need) <= srv->cfg.hbm_budget) return true;
+        return srv->running == 0 && largest_idle(srv) == index;
       });
       if (srv->queue.empty()) break;  // stopping and drained
       job = srv->queue.front();
       srv->queue.pop_front();
-      srv->in_use += job.bytes;
+      srv->est[index] = job.bytes;
+      srv->in_use = held_with(srv, -1, 0);
       ++srv->running;
       srv->stats.in_use = srv->in_use;
       srv->stats.peak_in_use = std::max(srv->stats.peak_in_use, srv->in_use);
@@ -132,9 +162,22 @@ void worker_main(blws_server* srv, int index) {
     const Clock::time_point t1 = Clock::now();
     d.res.queue_ms = std::chrono::duration<double, std::milli>(t0 - job.submitted).count();
     d.res.run_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    bool over = false;
     {
       std::lock_guard<std::mutex> lock(srv->mu);
-      srv->in_use -= job.bytes;
+      if (ctx) srv->held[index] = ctx->held_bytes();
+      srv->stats.peak_in_use = std::max(srv->stats.peak_in_use, held_with(srv, -1, 0));
+      srv->est[index] = 0;
+      over = held_with(srv, -1, 0) > srv->cfg.hbm_budget;
+    }
+    // over the budget (other workers' retained workspace included): give this
+    // worker's workspace back before taking more work
+    if (over && ctx && ctx->trim() != BLWS_OK && d.res.status == BLWS_OK) d.res.status = BLWS_ECUDA;
+    {
+      std::lock_guard<std::mutex> lock(srv->mu);
+      if (ctx) srv->held[index] = ctx->held_bytes();
+      srv->in_use = held_with(srv, -1, 0);
+      srv->stats.peak_in_use = std::max(srv->stats.peak_in_use, srv->in_use);
       --srv->running;
       srv->stats.in_use = srv->in_use;
       ++srv->stats.completed;
@@ -162,9 +205,15 @@ size_t blws_request_bytes(const blws_request* req, int precision) {
   if (!req) return 0;
   blws_config c;
   blws_config_default(&c);
+  // SM count of the current device (the split-K reservation scales with it)
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 152;
+  }
   if (req->kind == BLWS_REQ_RPCA)
-    return rpca_bytes(req->m, req->n, req->ld, c.k, c.k_cold, std::max(req->rpca.sv0, 1), precision);
-  return mc_bytes(req->m, req->n, req->nnz, req->max_rank, c.k, c.k_cold);
+    return rpca_bytes(req->m, req->n, req->ld, c.k, c.k_cold, std::max(req->rpca.sv0, 1), precision, sms);
+  return mc_bytes(req->m, req->n, req->nnz, req->max_rank, c.k, c.k_cold, sms);
 }
 
 blws_status blws_server_create(blws_server** out, const blws_server_config* cfg) {
@@ -184,6 +233,8 @@ blws_status blws_server_create(blws_server** out, const blws_server_config* cfg)
   if (!srv) return BLWS_ENOMEM;
   srv->cfg = c;
   srv->stats.budget = c.hbm_budget;
+  srv->held.assign(c.workers, 0);
+  srv->est.assign(c.workers, 0);
   for (int i = 0; i < c.workers; ++i) srv->threads.emplace_back(worker_main, srv, i);
   blws_status st;
   {

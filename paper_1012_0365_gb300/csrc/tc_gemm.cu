@@ -404,3 +404,35 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
 }
 
 }  // namespace blws
+
+// ------------------------------------------------ bounded-wait self-test --
+// One CTA initialises an mbarrier that expects one arrival and waits for its
+// first phase through the same bounded wait the tensor-core kernels use;
+// nothing arrives, so after `polls` polls the wait gives up and the kernel
+// raises the context's tensor-core error word, as a producer/consumer kernel
+// does when a copy or an MMA never completes.  No copy, MMA or tensor memory
+// is involved, so giving up leaves nothing in flight.
+namespace blws {
+namespace {
+
+__global__ void wait_probe_kernel(uint32_t polls, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, polls)) atomicExch(err, 1);
+}
+
+}  // namespace
+
+blws_status wait_probe(Ctx* ctx, cudaStream_t s, unsigned polls) {
+  double* scal = nullptr;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  wait_probe_kernel<<<1, 32, 0, s>>>(polls, reinterpret_cast<int*>(scal + SLOT_TCERR));
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+}  // namespace blws

@@ -370,20 +370,24 @@ __global__ void oz_planes_rows(int m, int n, int ld, int plane_rows, const doubl
   }
 }
 
-// P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64, split order
+// P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64, split order.
+// sym (a product known to be symmetric, M = N, beta = 0): an element below the
+// diagonal is formed from its mirror's partials, so P is exactly symmetric.
 __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const float2* __restrict__ part,
                           const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ P,
-                          int ldp, double alpha = 1.0, double beta = 0.0) {
+                          int ldp, double alpha = 1.0, double beta = 0.0, int sym = 0) {
   const size_t total = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
        e += (size_t)gridDim.x * blockDim.x) {
     const int r = (int)(e % M), j = (int)(e / M);
+    const bool mirror = sym && r > j;
+    const int rr = mirror ? j : r, jj = mirror ? r : j;
     double acc = 0.0;
     for (int z = 0; z < splits; ++z) {
-      const float2 v = part[((size_t)z * npad + j) * Mpad + r];
+      const float2 v = part[((size_t)z * npad + jj) * Mpad + rr];
       acc += (double)v.x + (double)v.y;
     }
-    const double v = ldexp(acc, ea[r] + eb[j]);
+    const double v = ldexp(acc, ea[rr] + eb[jj]);
     double* c = P + r + (size_t)j * ldp;
     *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
   }
@@ -546,7 +550,8 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
 // product, split along K to fill the GPU, and the FP64 reduction applies the
 // scales, alpha and beta.
 blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
-                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc) {
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                    bool sym) {
   BLWS_TRY(oz_encoder(ctx));
   const int ngroups = ceil_div(N, kOzBN), npad = ngroups * kOzBN, ldk = oz_ld(K);
   const size_t pa = (size_t)kOzS * M * ldk, pb = (size_t)kOzS * npad * ldk;
@@ -604,7 +609,7 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
   BLWS_CHECK_LAUNCH(ctx);
   const size_t tot = (size_t)M * N;
   oz_reduce<<<std::min(ceil_div((long long)tot, 256), ctx->sms * 8), 256, 0, s>>>(
-      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta);
+      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta, sym && M == N && beta == 0.0 ? 1 : 0);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }

@@ -67,11 +67,25 @@ CASES = [
     (513, 257, 30, 33, 33, 2),   # T_k of 66
     (600, 400, 40, 60, 60, 3),   # T_k of 180: the block-pair Jacobi path
     (1, 9, 1, 1, 1, 2),          # a single row
+    (700, 700, 60, 150, 150, 3),  # T_k of 450: tridiagonal reduction on a 4-CTA cluster
+    (700, 700, 60, 230, 230, 3),  # T_k of 690: tridiagonal reduction on an 8-CTA cluster
 ]
 
 
 @pytest.mark.parametrize("m,n,rank,w,r,k", CASES)
 def test_blws_svt_matches_oracle(blws, torch_mod, m, n, rank, w, r, k):
+    check_blws_svt(blws, torch_mod, m, n, rank, w, r, k, blws.PREC_FP64)
+
+
+@pytest.mark.parametrize("m,n,rank,w,r,k", [c for c in CASES if c[0] >= 200])
+def test_blws_svt_fp64_tensor_core_matches_oracle(blws, torch_mod, m, n, rank, w, r, k):
+    # the FP64-equivalent mode: digit-plane products for W~ X and for every
+    # product of at least 8e6 multiply-adds (Gram matrices, projections, Ritz
+    # lift, eigen refinement), at the same bars
+    check_blws_svt(blws, torch_mod, m, n, rank, w, r, k, blws.PREC_FP64_TC)
+
+
+def check_blws_svt(blws, torch_mod, m, n, rank, w, r, k, precision):
     torch = torch_mod
     W = structured(m, n, rank, seed=m * 7 + n)
     s = np.linalg.svd(W, compute_uv=False)
@@ -83,7 +97,7 @@ def test_blws_svt_matches_oracle(blws, torch_mod, m, n, rank, w, r, k):
     b = max(r, w)
     G = syn.gaussian_block(m + n, b - w, seed=5) if b > w else None
     ref = oracle.blws_svt_ref(W, eps, U0, V0, k, r, G)
-    ctx = blws.Context(k=k)
+    ctx = blws.Context(k=k, precision=precision)
     U, V, sig, c = ctx.blws_svt(gpu(blws, torch, W), eps, r, gpu(blws, torch, U0),
                                 gpu(blws, torch, V0), None if G is None else gpu(blws, torch, G))
     U, V, sig = U.cpu().numpy(), V.cpu().numpy(), sig.cpu().numpy()

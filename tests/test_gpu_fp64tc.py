@@ -102,3 +102,63 @@ def test_full_size_rpca_2000x2000(ctxs, torch_mod):
     assert info["status"] == 0 and info["rank"] == 100
     assert rel(A.cpu().numpy(), L0) < 1e-6
     assert rel(E.cpu().numpy(), S0) < 1e-6
+
+
+def _colmajor_np(torch, x):
+    from paper_1012_0365_gb300 import blws
+    return blws.colmajor(torch.from_numpy(np.ascontiguousarray(x)))
+
+
+# shapes of the solver's large products: the Ritz lift Q_k Z (4000 x 101, inner
+# 303), a Gram matrix / block coefficient (101 x 101, inner 4000), a refinement
+# product of the T_k eigen-solver (303^3), and a ragged case; each has at least
+# 8e6 multiply-adds, so it takes the digit-plane route; one small case below
+# that threshold stays on the FP64 pipe of the same context
+@pytest.mark.parametrize("M,N,K", [(4000, 101, 303), (101, 101, 4000), (303, 303, 303), (517, 230, 1290),
+                                   (50, 40, 30)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+def test_general_digit_products_match_numpy(ctxs, torch_mod, M, N, K, ta, tb):
+    # C = alpha op(A) op(B) + beta C through blws_gemm against an FP64 NumPy product
+    torch = torch_mod
+    _, coz = ctxs
+    rng = np.random.default_rng(M * 7 + N * 3 + K + 2 * ta + tb)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    C0 = rng.standard_normal((M, N))
+    alpha, beta = -1.37, 0.61
+    C = _colmajor_np(torch, C0)
+    coz.gemm(_colmajor_np(torch, A), _colmajor_np(torch, B), C, alpha=alpha, beta=beta, ta=ta, tb=tb)
+    opA = A.T if ta else A
+    opB = B.T if tb else B
+    prod = opA @ opB
+    ref = alpha * prod + beta * C0
+    # digit truncation: ~2^-49 of each row's / column's largest entry per term,
+    # summed over K with random signs: ~1e-14 of the product for Gaussian data
+    err = np.linalg.norm(C.cpu().numpy() - ref) / np.linalg.norm(prod)
+    assert err < 1e-13, err
+
+
+@pytest.mark.parametrize("n,K", [(303, 303), (101, 4000)])
+def test_symmetric_digit_products_are_exactly_symmetric(ctxs, torch_mod, n, K):
+    # X^T (T X) with T symmetric (the eigen-solver's projected matrix) and
+    # X^T X (a CholeskyQR Gram matrix): the digit-plane route mirrors one
+    # triangle, so the result is symmetric bit for bit, and matches NumPy
+    torch = torch_mod
+    _, coz = ctxs
+    rng = np.random.default_rng(n + K)
+    X = rng.standard_normal((K, n))
+    G = rng.standard_normal((K, K))
+    T = (G + G.T) / 2
+    TX = T @ X
+    C = _colmajor_np(torch, np.zeros((n, n)))
+    coz.gemm(_colmajor_np(torch, X), _colmajor_np(torch, TX), C, ta=True, sym=True)
+    Ch = C.cpu().numpy()
+    assert np.array_equal(Ch, Ch.T)
+    ref = X.T @ TX
+    assert np.linalg.norm(Ch - ref) / np.linalg.norm(ref) < 1e-13
+    Xg = _colmajor_np(torch, X)
+    Gm = _colmajor_np(torch, np.zeros((n, n)))
+    coz.gemm(Xg, Xg, Gm, ta=True)  # A^T A is detected and made symmetric by itself
+    Gh = Gm.cpu().numpy()
+    assert np.array_equal(Gh, Gh.T)
+    assert np.linalg.norm(Gh - X.T @ X) / np.linalg.norm(X.T @ X) < 1e-13

@@ -147,3 +147,50 @@ def test_wait_twice_is_rejected(torch_mod):
     with pytest.raises(blws.BlwsError):
         srv.wait(t)
     srv.close()
+
+
+def test_device_memory_stays_within_the_budget(torch_mod):
+    # a mix of small and large requests: the device memory the server's
+    # workers hold (read from cudaMemGetInfo while they run, minus what torch
+    # itself allocates for the outputs) stays within the admission budget,
+    # because retained worker workspace counts against it and is given back
+    # under pressure
+    import threading
+    import time
+    torch = torch_mod
+    from paper_1012_0365_gb300 import blws
+    small = syn.rpca_problem(300, 300, 5, 0.05, seed=8)[0]
+    large = syn.rpca_problem(1500, 1200, 30, 0.05, seed=9)[0]
+    Ds, Dl = blws.colmajor(torch.from_numpy(small)), blws.colmajor(torch.from_numpy(large))
+    req = blws.Request()
+    req.kind, req.m, req.n, req.ld = blws.REQ_RPCA, 1500, 1200, 1500
+    blws.load().rpca_params_default(__import__("ctypes").byref(req.rpca))
+    big = blws.load().blws_request_bytes(__import__("ctypes").byref(req), 0)
+    budget = int(big * 2.5)
+    # load every kernel module once (lazy loading takes device memory of its own)
+    blws.Context().rpca_solve(Ds)
+    torch.cuda.synchronize()
+    srv = blws.Server(workers=6, hbm_budget=budget)
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    peak = [0]
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            used = free0 - torch.cuda.mem_get_info()[0] - (torch.cuda.memory_reserved() - reserved0)
+            peak[0] = max(peak[0], used)
+            time.sleep(0.002)
+
+    th = threading.Thread(target=sample)
+    th.start()
+    order = [Dl, Ds, Ds, Dl, Ds, Dl, Dl, Ds, Ds, Ds, Dl, Ds]
+    tickets = [srv.submit_rpca(D) for D in order]
+    infos = [srv.wait(t)[2] for t in tickets]
+    stop.set()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    assert all(i["status"] == 0 for i in infos)
+    assert st["peak_in_use"] <= budget
+    assert peak[0] <= budget + (32 << 20), (peak[0], budget)

@@ -64,12 +64,36 @@ def test_noalloc_matches_allocating_apply_two_calls(env):
         assert err < TOL, (call, err)
 
 
+SCRATCH_DOUBLES = 2 << 20  # the header's stated maximum (16 MiB)
+KBK = 16                   # k-block of the FP64 GEMM tiles
+
+
+def noalloc_need(sms, M, N, K):
+    """Scratch doubles of one product by the header's rule: the inner
+    dimension is split (s > 1) only while the product has fewer than two tiles
+    per SM, and then needs s * M * N doubles."""
+    bm, bn = (128, 16) if N <= 16 else (64, 32) if N <= 32 else (64, 64)
+    tiles = -(-M // bm) * -(-N // bn)
+    splits = 1
+    if tiles < 2 * sms and K > 4 * KBK:
+        splits = min(-(-2 * sms // tiles), -(-K // (4 * KBK)))
+    kchunk = -(-(-(-K // splits)) // KBK) * KBK
+    splits = -(-K // kchunk)
+    return splits * M * N if splits > 1 else 0
+
+
 def test_noalloc_rejects_scratch_beyond_the_maximum(env):
     torch, blws = env
     lib = blws.load()
-    # m x b = 19000 x 64 fills 297 tiles (< 2 per SM), so the product splits
-    # its inner dimension in two: 2 * 19000 * 64 doubles > 2^21
-    m, n, b = 19000, 100, 64
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # W X_v with m rows and b = 64: 64 x 64 tiles; with one tile short of two
+    # per SM the inner dimension splits in two and needs 2 m b doubles, more
+    # than the array holds once the GPU has more than 128 SMs
+    b = 64
+    m = (2 * sms - 1) * 64
+    n = 100
+    if noalloc_need(sms, m, b, n) <= SCRATCH_DOUBLES:
+        pytest.skip("no product of this shape exceeds the scratch on %d SMs" % sms)
     W = blws.empty_colmajor(m, n).zero_()
     X = blws.empty_colmajor(m + n, b).zero_()
     P = blws.empty_colmajor(m + n, b).fill_(3.0)
