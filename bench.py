@@ -153,7 +153,7 @@ def cpu_oracle_solve(D, tol):
                       "full LAPACK SVD each, %.1f s)" % (tol, out["iters"], dt)}, out
 
 
-def relerr(torch, X, ref):
+def relerr_to(torch, X, ref):
     """||X - ref||_F / ||ref||_F, X a CUDA tensor and ref a host array."""
     R = torch.from_numpy(np.ascontiguousarray(ref)).to(X.device)
     return float(torch.linalg.norm(X - R) / torch.linalg.norm(R))
@@ -860,7 +860,7 @@ def main():
     if not args.no_cpu_baseline and ws == 1:
         cpu, ref = cpu_oracle_solve(D, args.tol)
         for mode, (Am, Em) in kept.items():
-            rel_oracle[mode] = {"A": relerr(torch, Am, ref["A"]), "E": relerr(torch, Em, ref["E"])}
+            rel_oracle[mode] = {"A": relerr_to(torch, Am, ref["A"]), "E": relerr_to(torch, Em, ref["E"])}
     peak, sms, mhz = fp64_peak_gflops(torch, clocks.get("sm_max_mhz"))
     lat = np.array(step_ms)
     out = {

@@ -139,6 +139,7 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   ctx->cfg = c;
   ctx->device = c.device;
   if (const char* ev = std::getenv("BLWS_EIG")) ctx->eig_route = std::strcmp(ev, "jacobi") == 0 ? 1 : 0;
+  if (const char* ev = std::getenv("BLWS_TRI")) ctx->tri_route = std::strcmp(ev, "packed") == 0 ? 1 : 0;
   blws_status st = bind_device(ctx);
   cudaDeviceProp prop;
   if (st == BLWS_OK && cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) st = BLWS_ECUDA;

@@ -98,12 +98,16 @@ struct Ctx {
   // kernel (process-wide, per device), not to a context: it only ever grows,
   // under a lock, so that contexts on other threads never lower it under a
   // launch that needs more (defined in capi.cu).
-  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_TRI, ATTR_TRI_INV, ATTR_TRI_CL, ATTR_TRI_CL8, ATTR_OZ, ATTR_COUNT_ };
+  enum SmemAttr { ATTR_CHOL, ATTR_CHOL_CLUSTER, ATTR_JACOBI_CTA, ATTR_JACOBI_BLOCK, ATTR_TRI, ATTR_TRI_INV, ATTR_TRI_CL, ATTR_TRI_CL8, ATTR_OZ,
+                  ATTR_TRI_ROWS1, ATTR_TRI_ROWS2, ATTR_TRI_ROWS4, ATTR_TRI_ROWS8, ATTR_COUNT_ };
   blws_status smem_limit(SmemAttr which, const void* func, int bytes);
   int jacobi_block_per_sm = 0;  // occupancy of the block Jacobi kernel (queried once)
   // FP32 eigen stage: 0 the tridiagonal route where it applies, 1 Jacobi only
   // (environment BLWS_EIG=jacobi at context creation)
   int eig_route = 0;
+  // tridiagonal reduction: 0 by rows on a cluster where it fits, 1 the packed
+  // kernels (environment BLWS_TRI=packed at context creation)
+  int tri_route = 0;
   unsigned long long tri_fallbacks = 0;  // tridiagonal stage results replaced by Jacobi
   // device bytes the workspace holds now
   size_t held_bytes() const {

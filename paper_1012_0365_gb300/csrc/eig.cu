@@ -458,29 +458,35 @@ __global__ void oa_norms_partial(int n, const double* __restrict__ S, const doub
 // off-diagonal partials; writes lam[n] and delta (scal[0]).
 __global__ void oa_lambda(int n, int nparts, const double* __restrict__ S, const double* __restrict__ R,
                           const double* __restrict__ part, double* lam, double* delta) {
-  __shared__ double red[256];
-  double dsum = 0.0;
+  __shared__ double red[3][256];
+  double dsum = 0.0, r2 = 0.0, t2 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double l = S[i + (size_t)i * n] / (1.0 - R[i + (size_t)i * n]);
     lam[i] = l;
     const double dv = S[i + (size_t)i * n] - l;
     dsum = fma(dv, dv, dsum);
   }
-  red[threadIdx.x] = dsum;
+  // the CTA partials of oa_norms_partial: thread t adds parts t, t + 256, ...
+  // (fixed assignment and tree: deterministic)
+  for (int c = threadIdx.x; c < nparts; c += blockDim.x) {
+    dsum += part[3 * c + 0];
+    r2 += part[3 * c + 1];
+    t2 += part[3 * c + 2];
+  }
+  red[0][threadIdx.x] = dsum;
+  red[1][threadIdx.x] = r2;
+  red[2][threadIdx.x] = t2;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+      red[2][threadIdx.x] += red[2][threadIdx.x + w];
+    }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    double s_off = red[0], r2 = 0.0, t2 = 0.0;
-    for (int c = 0; c < nparts; ++c) {
-      s_off += part[3 * c + 0];
-      r2 += part[3 * c + 1];
-      t2 += part[3 * c + 2];
-    }
-    *delta = kClusterGamma * 2.0 * (sqrt(s_off) + sqrt(t2) * sqrt(r2));
-  }
+  if (threadIdx.x == 0)
+    *delta = kClusterGamma * 2.0 * (sqrt(red[0][0]) + sqrt(red[2][0]) * sqrt(red[1][0]));
 }
 
 __global__ void oa_correction(int n, const double* __restrict__ S, const double* __restrict__ R,

@@ -541,6 +541,240 @@ int cl_smem_bytes(int n) {
          w * (int)sizeof(float);
 }
 
+
+// ----------------------------- 1c. tridiagonalisation by rows on a cluster --
+// The same Householder reduction with the whole symmetric matrix stored (both
+// triangles) and its rows dealt out round-robin: row i lives in CTA i mod kCl
+// (kCl = 1, 2, 4 or 8 CTAs of one thread-block cluster) as local row
+// i / kCl, and local row l belongs to warp l mod 32.  A warp then owns whole
+// rows: the trailing update and the product p = A22 v of a row are one pass
+// over it with a warp-level sum, and no column sums have to be gathered
+// across warps.  Every CTA keeps the per-index vectors (pending update
+// pv, pw and the current reflector v) in full.  Step k:
+//   (1) the warp owning row k applies the pending update to it, forms the
+//       reflector and writes v (and tau) into every CTA; cluster barrier;
+//   (2) every warp updates its trailing rows and forms p_i = tau a_i . v;
+//       each CTA's sum of p_i v_i goes to every CTA; cluster barrier;
+//   (3) K = tau / 2 sum p_i v_i (the CTA sums in rank order), and the owner
+//       of row i writes the next pending pair (v_i, w_i = p_i - K v_i) into
+//       every CTA; cluster barrier.
+// Every sum has a fixed order, so the result is deterministic.
+constexpr int kRowsMaxN1 = 236, kRowsMaxN2 = 330, kRowsMaxN4 = 468, kRowsMaxN8 = 656;
+
+template <int kCl>
+__host__ __device__ constexpr int rows_per_cta(int n) { return (n + kCl - 1) / kCl; }
+
+template <int kCl>
+int rows_smem_bytes(int n) {
+  return n * (int)sizeof(float4) + rows_per_cta<kCl>(n) * (n + 1) * (int)sizeof(float);
+}
+
+// smallest cluster whose share of the full matrix fits one CTA (0: none)
+inline int rows_cluster(int n) {
+  if (n <= kRowsMaxN1) return 1;
+  if (n <= kRowsMaxN2) return 2;
+  if (n <= kRowsMaxN4) return 4;
+  if (n <= kRowsMaxN8) return 8;
+  return 0;
+}
+
+// the pending rank-2 term pv_i pw_j + pw_i pv_j of element (i, j), rounded the
+// same way for (j, i): both products, then their sum (each operation is
+// commutative), so the stored matrix stays exactly symmetric
+__device__ __forceinline__ float sym_upd(const float4& qi, const float4& qj) {
+  return __fadd_rn(__fmul_rn(qi.x, qj.y), __fmul_rn(qi.y, qj.x));
+}
+
+template <int kCl>
+__device__ __forceinline__ void rows_sync() {
+  if constexpr (kCl > 1) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+// the same shared-memory object in CTA r of the cluster
+template <int kCl, typename P>
+__device__ __forceinline__ P* rows_remote(P* p, int r) {
+  if constexpr (kCl > 1) {
+    return cg::this_cluster().map_shared_rank(p, r);
+  } else {
+    return p;
+  }
+}
+
+template <int kCl>
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTriThreads)
+tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
+                float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ tscale) {
+  extern __shared__ float4 smr[];
+  __shared__ float red[32];
+  __shared__ double redd[32];
+  __shared__ float sh_part[kCl];  // every CTA's sum of p_i v_i (written by that CTA)
+  __shared__ float sh_tau;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  int rank = 0;
+  if constexpr (kCl > 1) rank = (int)cg::this_cluster().block_rank();
+  const int R = rows_per_cta<kCl>(n);
+  float4* cv = smr;                                   // x, y: pending update; z: reflector
+  float* pb = reinterpret_cast<float*>(cv + n);       // p_i of the local rows
+  float* A = pb + R;                                  // local row l at A + l n
+  // scale: largest |T_ij| over the lower triangle (every CTA finds the same)
+  double mx = 0.0;
+  for (int j = wid; j < n; j += nw) {
+#pragma unroll 4
+    for (int i = j + lane; i < n; i += 32) mx = fmax(mx, fabs(T[i + (size_t)j * n]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) redd[wid] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < nw; ++w) mx = fmax(mx, redd[w]);
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);
+  const double scale = ldexp(1.0, -ex);
+  if (tid == 0 && rank == 0) *tscale = (float)ldexp(1.0, ex);  // T = 2^ex x the scaled matrix
+  // own rows, both triangles from the lower one: (i, j) = T[max + min n]
+  for (int l = wid; l < R; l += nw) {
+    const int i = l * kCl + rank;
+    if (i >= n) break;
+    float* row = A + (size_t)l * n;
+    for (int j = lane; j < n; j += 32)
+      row[j] = (float)((j >= i ? T[j + (size_t)i * n] : T[i + (size_t)j * n]) * scale);
+  }
+  for (int t = tid; t < n; t += blockDim.x) cv[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  rows_sync<kCl>();  // every CTA running and initialised before any remote write
+  for (int k = 0; k + 2 < n; ++k) {
+    // (1) row k: pending update, reflector into every CTA
+    const int lk = k / kCl;
+    if (rank == k % kCl && wid == (lk & 31)) {
+      float* row = A + (size_t)lk * n;
+      const float4 qk = cv[k];
+      float ssq = 0.0f;
+      for (int j = k + lane; j < n; j += 32) {
+        const float4 q = cv[j];
+        const float a = row[j] - sym_upd(qk, q);
+        row[j] = a;
+        if (j >= k + 2) ssq = fmaf(a, a, ssq);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+      __syncwarp();
+      const float alpha = row[k + 1];
+      float tau = 0.0f, beta = alpha, vscale = 0.0f;
+      if (ssq > 0.0f) {
+        const float nrm = sqrtf(fmaf(alpha, alpha, ssq));
+        beta = alpha >= 0.0f ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        vscale = 1.0f / (alpha - beta);
+      }
+      if (lane == 0) {
+        dv[k] = row[k];
+        ev[k] = beta;
+        tauv[k] = tau;
+#pragma unroll
+        for (int r = 0; r < kCl; ++r) *rows_remote<kCl>(&sh_tau, r) = tau;
+      }
+      for (int j = lane; j < n; j += 32) {
+        float v = 0.0f;
+        if (j == k + 1) v = 1.0f;
+        else if (j > k + 1 && tau != 0.0f) v = row[j] * vscale;
+        V[j + (size_t)k * n] = v;
+        if (j > k) {
+#pragma unroll
+          for (int r = 0; r < kCl; ++r) rows_remote<kCl>(cv, r)[j].z = v;
+        }
+      }
+    }
+    rows_sync<kCl>();
+    // (2) trailing rows: pending update and p_i = tau a_i . v, two rows per pass
+    const float tau = sh_tau;
+    const int l0 = (k + kCl - rank) / kCl;  // first local row with a global index > k
+    float pvw = 0.0f;                       // this warp's sum of p_i v_i
+    for (int l = l0 + ((wid - l0) & 31); l < R; l += 64) {
+      const int i0 = l * kCl + rank, i1 = (l + 32) * kCl + rank;
+      if (i0 >= n) break;
+      const bool two = l + 32 < R && i1 < n;
+      float* r0 = A + (size_t)l * n;
+      float* r1 = A + (size_t)(l + 32) * n;
+      const float4 q0 = cv[i0];
+      const float4 q1 = two ? cv[i1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float s0 = 0.0f, s1 = 0.0f;
+      if (two) {
+        for (int j = k + 1 + lane; j < n; j += 32) {
+          const float4 q = cv[j];
+          const float a0 = r0[j] - sym_upd(q0, q);
+          const float a1 = r1[j] - sym_upd(q1, q);
+          r0[j] = a0;
+          r1[j] = a1;
+          s0 = fmaf(a0, q.z, s0);
+          s1 = fmaf(a1, q.z, s1);
+        }
+      } else {
+        for (int j = k + 1 + lane; j < n; j += 32) {
+          const float4 q = cv[j];
+          const float a0 = r0[j] - sym_upd(q0, q);
+          r0[j] = a0;
+          s0 = fmaf(a0, q.z, s0);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      const float p0 = tau * s0, p1 = tau * s1;
+      if (lane == 0) {
+        pb[l] = p0;
+        if (two) pb[l + 32] = p1;
+      }
+      pvw = fmaf(p0, q0.z, pvw);
+      if (two) pvw = fmaf(p1, q1.z, pvw);
+    }
+    if (lane == 0) red[wid] = pvw;
+    __syncthreads();
+    if (wid == 0) {
+      float t = lane < nw ? red[lane] : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane < kCl) rows_remote<kCl>(sh_part, lane)[rank] = t;
+    }
+    rows_sync<kCl>();
+    // (3) K and the next pending pair (v_i, w_i) of the local rows, into every CTA
+    float K = 0.0f;
+#pragma unroll
+    for (int r = 0; r < kCl; ++r) K += sh_part[r];
+    K *= 0.5f * tau;
+    for (int l = l0 + tid; l < R; l += blockDim.x) {
+      const int i = l * kCl + rank;
+      if (i >= n) break;
+      const float v = cv[i].z;
+      const float2 vw = make_float2(v, pb[l] - K * v);
+#pragma unroll
+      for (int r = 0; r < kCl; ++r) *reinterpret_cast<float2*>(&rows_remote<kCl>(cv, r)[i]) = vw;
+    }
+    rows_sync<kCl>();
+  }
+  // the last 2 x 2 block receives the last pending update
+  if (tid == 0) {
+    if (n >= 2) {
+      const int a = n - 2, b = n - 1;
+      const float4 qa = cv[a], qb = cv[b];
+      if (rank == a % kCl) {
+        const float* ra = A + (size_t)(a / kCl) * n;
+        dv[a] = ra[a] - sym_upd(qa, qa);
+        ev[a] = ra[b] - sym_upd(qa, qb);
+        tauv[a] = 0.0f;
+      }
+      if (rank == b % kCl) dv[b] = A[(size_t)(b / kCl) * n + b] - sym_upd(qb, qb);
+    } else if (rank == 0) {
+      dv[0] = A[0];
+    }
+  }
+}
+
 // ------------------------------------------------------ 2. eigenvalues --
 // lam[j] = the (j+1)-th smallest eigenvalue of tridiag(d, e), one warp each.
 __device__ __forceinline__ int sturm_count(int n, const float* sd, const float* se2, float x) {
@@ -988,6 +1222,8 @@ tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw
 bool tri_fits(Ctx* ctx, int n) {
   if (n <= kTriOneCtaMaxN) return true;
   if (n > kTriMaxN) return false;
+  if (ctx->tri_route == 0 && rows_cluster(n) > 0)
+    return (size_t)rows_smem_bytes<8>(n) + 1024 <= ctx->smem_optin;
   const int bytes = n <= kTriCl4MaxN ? cl_smem_bytes<4>(n) : cl_smem_bytes<8>(n);
   return (size_t)bytes + 1024 <= ctx->smem_optin;
 }
@@ -1015,7 +1251,18 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   float* tauv = ev + n;
   float* lam = tauv + n;
   float* tscale = lam + n;
-  if (on_cluster && cl8) {
+  // the reduction by rows (section 1c) wherever a cluster's share fits, else
+  // the packed kernels (also selectable with BLWS_TRI=packed at context creation)
+  const int kc = ctx->tri_route == 0 ? rows_cluster(n) : 0;
+  if (kc == 1) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_ROWS1, (const void*)tri_rows_kernel<1>, rows_smem_bytes<1>(n)));
+  } else if (kc == 2) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_ROWS2, (const void*)tri_rows_kernel<2>, rows_smem_bytes<2>(n)));
+  } else if (kc == 4) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_ROWS4, (const void*)tri_rows_kernel<4>, rows_smem_bytes<4>(n)));
+  } else if (kc == 8) {
+    BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_ROWS8, (const void*)tri_rows_kernel<8>, rows_smem_bytes<8>(n)));
+  } else if (on_cluster && cl8) {
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL8, (const void*)tri_reduce_cluster_kernel<8>, cl_smem_bytes<8>(n)));
   } else if (on_cluster) {
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_CL, (const void*)tri_reduce_cluster_kernel<4>, cl_smem_bytes<4>(n)));
@@ -1029,7 +1276,15 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_INV, (const void*)tri_group_qr_kernel, gsmem));
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
-  if (on_cluster && cl8)
+  if (kc == 1)
+    tri_rows_kernel<1><<<1, kTriThreads, rows_smem_bytes<1>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+  else if (kc == 2)
+    tri_rows_kernel<2><<<2, kTriThreads, rows_smem_bytes<2>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+  else if (kc == 4)
+    tri_rows_kernel<4><<<4, kTriThreads, rows_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+  else if (kc == 8)
+    tri_rows_kernel<8><<<8, kTriThreads, rows_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+  else if (on_cluster && cl8)
     tri_reduce_cluster_kernel<8><<<8, kTriThreads, cl_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
   else if (on_cluster)
     tri_reduce_cluster_kernel<4><<<4, kTriThreads, cl_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);

