@@ -46,6 +46,72 @@ APPLY_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the
                         "<double,{0,1},0,32,8> launches of blws_apply (b=101), bench.py --profile-apply")
 
 
+MODE_DTYPE = {
+    "fp64": "f64 throughout (DFMA products)",
+    "mixed": "tf32x3 tensor-core products (hi+lo split, f32 sums of <= 256 terms, f64 beyond), f64 "
+             "Cholesky/eigen/count; fp64-equivalent digit-plane products once the residual < 1e-5",
+    "fp64tc": "fp64-equivalent products: 7 bf16 digit planes per operand on tcgen05 (exact f32 sums of "
+              "256 terms, ~1e-14 relative); Cholesky, eigen stage and count f64",
+}
+LEG_KEY = {"fp64": "fp64_dfma", "mixed": "mixed_precision", "fp64tc": "fp64_tensor_core"}
+# tensor-core work per multiply-add of the product with W~: 28 BF16 digit-pair
+# MMAs (FP64-equivalent mode), 3 TF32 MMAs (mixed mode); 2 flops each
+TENSOR_MMAS = {"fp64tc": 28, "mixed": 3}
+# DRAM bytes (read + write) of one launch of the digit-plane kernel for the
+# 2000 x 2000 product at b = 101, from one ncu capture (filled in below when
+# a capture of the current kernel exists; None otherwise)
+OZ_TRAFFIC = {}
+
+
+def measured_peaks():
+    """The measured peaks of this machine (HBM copy GB/s, bf16 TFLOP/s
+    burst and sustained), else the recipe's fallback figures."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
+                "source": "of measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
+
+
+def roofline(torch, mode, ms, launches, work, clocks, workload, b):
+    """Roofline object of the dominant kernel, the product with W~ (step a2),
+    from the device time the library's event timing measured over the timed
+    solves (ms over `launches` products doing `work` multiply-adds)."""
+    if not launches or ms <= 0:
+        return None
+    per = ms / launches / 1e3  # seconds per product
+    if mode == "fp64":
+        peak, sms, mhz = fp64_peak_gflops(torch, clocks.get("sm_max_mhz"))
+        achieved = 2.0 * work / launches / per / 1e9
+        return {"kernel": "gemm_f64 x 2 (P = [W X_v; W^T X_u], b=%d at the end)" % b, "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
+                "traffic": APPLY_TRAFFIC.get(workload) if b == 101 else None,
+                "traffic_source": APPLY_TRAFFIC_SOURCE if b == 101 else None,
+                "launches": launches, "us_per_launch": per * 1e6,
+                "algorithmic": "2 x (2 m n b) FP64 flops per product",
+                "peak_source": "FP64 derived from unit counts: %d SMs x 2 DFMA/clk x 2 x %.0f MHz "
+                               "(MEASURED_PEAKS.json has no FP64 figure)" % (sms, mhz)}
+    pk = measured_peaks()
+    mmas = TENSOR_MMAS[mode]
+    achieved = 2.0 * mmas * work / launches / per / 1e12
+    # timed inside long solves: the sustained bf16 figure; TF32 at half the bf16 rate
+    peak = pk["bf16_sustained"] * (0.5 if mode == "mixed" else 1.0)
+    kern = "oz_kernel (digit-plane products, both halves of P in one launch)" if mode == "fp64tc" else \
+        "tc_tf32x3_kernel (split-TF32 products, both halves of P in one launch)"
+    tr = OZ_TRAFFIC.get(workload) if mode == "fp64tc" and b == 101 else None
+    return {"kernel": kern + ", b=%d at the end" % b, "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr,
+            "launches": launches, "us_per_launch": per * 1e6,
+            "algorithmic": "%d x 2 x (2 m n b) %s tensor flops per product (b unpadded)"
+                           % (mmas, "bf16" if mode == "fp64tc" else "tf32"),
+            "fp64_equivalent_tflops": 2.0 * work / launches / per / 1e12,
+            "peak_source": "bf16 sustained %s%s" % (pk["source"], ", x 0.5 for tf32 (nominal ratio)"
+                                                     if mode == "mixed" else "")}
+
+
 def fp64_peak_gflops(torch, sm_max_mhz):
     """FP64 peak derived from unit counts: SMs (read from the device) x 2 DFMA
     per clock per SM x 2 flops x the maximum SM clock (sampled by nvidia-smi,
@@ -628,6 +694,8 @@ def main():
                     help="run one untimed solve only (for ncu launch lists)")
     ap.add_argument("--profile-apply", action="store_true",
                     help="run the block product with W~ a few times only (for ncu captures)")
+    ap.add_argument("--headline", default="fp64tc", choices=["fp64", "mixed", "fp64tc"],
+                    help="precision mode of the headline value (the others become sub-objects)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "fp64tc"],
                     help="context precision of --profile-solve / --profile-apply / --batch / --serve")
     ap.add_argument("--batch", action="store_true", help="uneven batch through the server (own JSON line)")
@@ -677,16 +745,16 @@ def main():
     E = blws.empty_colmajor(m, n)
     Ah = torch.empty((n, m), dtype=torch.float64).pin_memory()
     Eh = torch.empty((n, m), dtype=torch.float64).pin_memory()
-    ctx = blws.Context(k=args.k, device=local_rank)
+    head = PRECISIONS[args.headline]
+    ctx = blws.Context(k=args.k, device=local_rank, precision=head)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def solve():
-        return ctx.rpca_solve(Dg, tol=args.tol, A=A, E=E)
+    def solve(c=None):
+        return (c or ctx).rpca_solve(Dg, tol=args.tol, A=A, E=E)
 
     if args.profile_solve or args.profile_apply:
-        if args.precision != "fp64":
-            ctx = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[args.precision])
+        ctx = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[args.precision])
         if args.profile_solve:
             l0 = ctx.launches
             _, _, info = solve()
@@ -714,6 +782,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
+    ctx.timing_start()  # events around every product with W~ (step a2) in the timed steps
     for _ in range(args.steps):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True)
@@ -727,12 +796,13 @@ def main():
     if dist:
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
+    apply_ms, apply_n, apply_work = ctx.timing_stop()
     launches = ctx.launches - launches0
     clocks = sampler.stop()
     total_ms = max_over_ranks(dist, float(np.sum(step_ms)), "cuda")
     value = job_rate(ws, args.steps, total_ms)
     relerr = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
-    kept = {"fp64": (A.clone(), E.clone())}  # for the relerr against the oracle, below
+    kept = {args.headline: (A.clone(), E.clone())}  # for the relerr against the oracle, below
 
     # ---- end to end through the public API with host buffers ----
     e2e_ms = []
@@ -746,83 +816,37 @@ def main():
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = job_rate(ws, 1, max_over_ranks(dist, float(np.mean(e2e_ms)), "cuda"))
+    roof = roofline(torch, args.headline, apply_ms, apply_n, apply_work, clocks, args.workload,
+                    info["rank"] + 1)
 
-    # ---- roofline of the dominant kernel: the block product with W~ ----
-    b = max(info["rank"] + 1, 1)
-    X = blws.colmajor(torch.randn(m + n, b, dtype=torch.float64, device="cuda"))
-    P = blws.empty_colmajor(m + n, b)
-    for _ in range(3):
-        ctx.apply(Dg, X, P)
-    reps = 10
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(reps):
-        ctx.apply(Dg, X, P)
-    ev1.record(stream)
-    ev1.synchronize()
-    apply_ms = ev0.elapsed_time(ev1) / reps
-    flops = 4.0 * m * n * b
-    achieved = flops / (apply_ms / 1e3) / 1e12
-
-    # ---- the mixed-precision mode (TF32x3 tensor-core products, FP64 tail) ----
-    mixed = None
+    # ---- the other precision modes, each as a sub-object ----
+    legs = {}
     if not args.no_mixed:
-        ctxm = blws.Context(k=args.k, device=local_rank, precision=blws.PREC_MIXED)
-
-        def solve_mixed():
-            return ctxm.rpca_solve(Dg, tol=args.tol, A=A, E=E)
-
-        for _ in range(args.warmup):
-            solve_mixed()
-        mixed_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            _, _, minfo = solve_mixed()
-            ev1.record(stream)
-            ev1.synchronize()
-            mixed_ms.append(ev0.elapsed_time(ev1))
-        mrel = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
-        kept["mixed"] = (A.clone(), E.clone())
-        mixed = {"value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(mixed_ms)), "cuda")),
-                 "unit": "solves/s",
-                 "ms_per_step": float(np.mean(mixed_ms)),
-                 "latency_ms": {"p50": float(np.percentile(mixed_ms, 50)),
-                                "p99": float(np.percentile(mixed_ms, 99))},
-                 "dtype": "tf32x3 tensor-core products, f32 tall products, f64 Cholesky/eigen/count; "
-                          "f64 products once the residual < 1e-5",
-                 "iters": minfo["iters"], "mixed_iters": minfo["mixed_iters"],
-                 "residual": minfo["residual"], "relerr_vs_planted": mrel}
-
-    # ---- FP64-equivalent products on the tensor cores (BF16 digit planes) ----
-    fp64tc = None
-    if not args.no_mixed:
-        ctxt = blws.Context(k=args.k, device=local_rank, precision=blws.PREC_FP64_TC)
-        for _ in range(args.warmup):
-            ctxt.rpca_solve(Dg, tol=args.tol, A=A, E=E)
-        tc_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            _, _, tinfo = ctxt.rpca_solve(Dg, tol=args.tol, A=A, E=E)
-            ev1.record(stream)
-            ev1.synchronize()
-            tc_ms.append(ev0.elapsed_time(ev1))
-        trel = float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0))
-        kept["fp64tc"] = (A.clone(), E.clone())
-        fp64tc = {"value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(tc_ms)), "cuda")),
-                  "unit": "solves/s",
-                  "ms_per_step": float(np.mean(tc_ms)),
-                  "latency_ms": {"p50": float(np.percentile(tc_ms, 50)),
-                                 "p99": float(np.percentile(tc_ms, 99))},
-                  "dtype": "products with W from 7 BF16 digit planes per operand on tcgen05 (exact "
-                           "FP32 sums, ~1e-14 relative); everything else f64",
-                  "iters": tinfo["iters"], "residual": tinfo["residual"], "relerr_vs_planted": trel}
+        for mode in [x for x in ("fp64", "mixed", "fp64tc") if x != args.headline]:
+            c2 = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[mode])
+            for _ in range(args.warmup):
+                solve(c2)
+            ms2 = []
+            c2.timing_start()
+            for _ in range(args.steps):
+                flush.zero_()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                _, _, i2 = solve(c2)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms2.append(ev0.elapsed_time(ev1))
+            a_ms, a_n, a_work = c2.timing_stop()
+            kept[mode] = (A.clone(), E.clone())
+            legs[mode] = {
+                "value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(ms2)), "cuda")),
+                "unit": "solves/s", "ms_per_step": float(np.mean(ms2)),
+                "latency_ms": {"p50": float(np.percentile(ms2, 50)), "p99": float(np.percentile(ms2, 99))},
+                "dtype": MODE_DTYPE[mode], "iters": i2["iters"], "mixed_iters": i2["mixed_iters"],
+                "residual": i2["residual"],
+                "relerr_vs_planted": float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0)),
+                "roofline": roofline(torch, mode, a_ms, a_n, a_work, clocks, args.workload, i2["rank"] + 1)}
 
     if rank != 0:
         if dist:
@@ -861,7 +885,6 @@ def main():
         cpu, ref = cpu_oracle_solve(D, args.tol)
         for mode, (Am, Em) in kept.items():
             rel_oracle[mode] = {"A": relerr_to(torch, Am, ref["A"]), "E": relerr_to(torch, Em, ref["E"])}
-    peak, sms, mhz = fp64_peak_gflops(torch, clocks.get("sm_max_mhz"))
     lat = np.array(step_ms)
     out = {
         "metric": "rpca_solves_per_s",
@@ -877,36 +900,27 @@ def main():
         "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "rank": r, "corrupt": f,
-                   "tol": args.tol, "k": args.k, "l2": "flushed between steps (512 MB write)",
+                   "tol": args.tol, "k": args.k, "precision": args.headline,
+                   "arithmetic": MODE_DTYPE[args.headline],
+                   "l2": "flushed between steps (512 MB write)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},
         "solve": {"iters": info["iters"], "rank": info["rank"], "nnzE": info["nnzE"],
                   "residual": info["residual"], "relerr_vs_planted": relerr,
-                  "relerr_vs_oracle": rel_oracle.get("fp64")},
+                  "relerr_vs_oracle": rel_oracle.get(args.headline)},
         "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": m * n * 8,
                 "d2h_bytes_per_step": 2 * m * n * 8},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "gemm_f64 (block product with the augmented matrix, b=%d)" % b,
-                     "bound": "alu", "achieved": achieved * 1e3, "peak": peak,
-                     "unit": "GFLOP/s", "frac": achieved * 1e3 / peak,
-                     "traffic": APPLY_TRAFFIC.get(args.workload) if b == 101 else None,
-                     "traffic_source": APPLY_TRAFFIC_SOURCE if b == 101 else None,
-                     "algorithmic_bytes": 2.0 * m * n * 8,
-                     "algorithmic_flops": flops,
-                     "peak_source": "FP64 derived from unit counts: %d SMs x 2 DFMA/clk x 2 x %.0f MHz "
-                                    "(MEASURED_PEAKS.json has no FP64 figure)" % (sms, mhz)},
+        "roofline": roof,
         "clocks": clocks,
         "wall_s": t_wall,
     }
     if cpu:
         out["cpu_baseline"] = cpu
-    if mixed:
-        mixed["relerr_vs_oracle"] = rel_oracle.get("mixed")
-        out["mixed_precision"] = mixed
-    if fp64tc:
-        fp64tc["relerr_vs_oracle"] = rel_oracle.get("fp64tc")
-        out["fp64_tensor_core"] = fp64tc
+    for mode, leg in legs.items():
+        leg["relerr_vs_oracle"] = rel_oracle.get(mode)
+        out[LEG_KEY[mode]] = leg
     if fullsvd:
         out["fullsvd_same_gpu"] = fullsvd
         out["fullsvd_same_gpu"]["blws_speedup"] = value / fullsvd["value"]

@@ -261,6 +261,20 @@ blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double
                       const double* A, int lda, const double* B, int ldb, double beta, double* C,
                       int ldc, int sym, void* stream);
 
+/* Device timing of step a2 (Section 4, end: the product P = W~ X with the
+ * zero blocks skipped), the dominant step of the procedure.  After
+ * blws_timing_start, every product with a dense W that this context runs
+ * (inside blws_svt, blws_evd, blws_apply, rpca_solve) is bracketed by a pair
+ * of CUDA events on its stream, around the product's kernel (the digit-plane
+ * kernel in BLWS_PREC_FP64_TC, the TF32x3 kernel in BLWS_PREC_MIXED, both FP64
+ * GEMMs and their split-K reduction in BLWS_PREC_FP64).  blws_timing_stop
+ * waits for the last event and returns the summed device time (*ms), the
+ * number of products (*launches) and their multiply-adds (*work = sum of
+ * 2 m n b: both halves of each product).  Recording costs two event records
+ * per product; timing is off by default. */
+blws_status blws_timing_start(blws_ctx* ctx);
+blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, double* work);
+
 /* Self-test of the bounded waits (no counterpart in the paper).  Every wait
  * of the tensor-core kernels (a TMA copy or an MMA that should complete) is
  * capped; when a cap is reached the kernel raises an error word and returns,

@@ -21,7 +21,7 @@ EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_st
            "blws_svt", "blws_evd", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
            "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
-           "blws_csc_mirror", "blws_gemm", "blws_wait_probe")
+           "blws_csc_mirror", "blws_gemm", "blws_wait_probe", "blws_timing_start", "blws_timing_stop")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -129,6 +129,8 @@ def load():
     lib.blws_csc_mirror.argtypes = [vp, ci, ci, ci, vp, vp, vp, vp, vp, vp]
     lib.blws_gemm.argtypes = [vp, ci, ci, ci, ci, ci, cd, vp, ci, vp, ci, cd, vp, ci, ci, vp]
     lib.blws_wait_probe.argtypes = [vp, ctypes.c_uint, vp]
+    lib.blws_timing_start.argtypes = [vp]
+    lib.blws_timing_stop.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(cd)]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
@@ -318,6 +320,20 @@ class Context:
         if st != OK:
             self._raise(st, "blws_gemm")
         return C
+
+    def timing_start(self):
+        """Start timing the products with the augmented matrix (step a2)."""
+        st = load().blws_timing_start(self._h)
+        if st != OK:
+            self._raise(st, "blws_timing_start")
+
+    def timing_stop(self):
+        """Stop timing; returns (device ms, products, multiply-adds)."""
+        ms, n, work = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double()
+        st = load().blws_timing_stop(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(work))
+        if st != OK:
+            self._raise(st, "blws_timing_stop")
+        return ms.value, int(n.value), work.value
 
     def wait_probe(self, polls=256, stream=None):
         """Run the bounded-wait self-test; returns its status (ETIMEOUT expected)."""

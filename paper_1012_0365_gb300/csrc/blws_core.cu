@@ -96,9 +96,10 @@ blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double*
   if (op.W && op.Wr && op.Wc && tc_npad(b) > 0)
     return tc_dual_apply(ctx, s, *op.Wr, *op.Wc, m, n, X, ldx, b, P, ldp);
   if (op.W) {
+    BLWS_TRY(ctx->time_begin(s));
     BLWS_TRY(gemm(ctx, s, false, false, m, b, n, 1.0, op.W, op.ldw, X + m, ldx, 0.0, P, ldp));
     BLWS_TRY(gemm(ctx, s, true, false, n, b, m, 1.0, op.W, op.ldw, X, ldx, 0.0, P + m, ldp));
-    return BLWS_OK;
+    return ctx->time_end(s, 2.0 * m * n * b);
   }
   return apply_sparse(ctx, s, op, X, ldx, b, P, ldp);
 }

@@ -66,6 +66,30 @@ blws_status Ctx::get(Buf b, size_t bytes, void** out) {
   return BLWS_OK;
 }
 
+blws_status Ctx::time_begin(cudaStream_t s) {
+  if (!timing) return BLWS_OK;
+  if (tused == tcap) {  // grow the event pool (between products, not in a kernel's way)
+    const size_t ncap = tcap ? 2 * tcap : 256;
+    cudaEvent_t* n = new (std::nothrow) cudaEvent_t[2 * ncap];
+    if (!n) return fail(BLWS_ENOMEM, "timing events");
+    for (size_t i = 0; i < 2 * tcap; ++i) n[i] = tev[i];
+    for (size_t i = 2 * tcap; i < 2 * ncap; ++i) BLWS_TRY_CUDA(this, cudaEventCreate(&n[i]));
+    delete[] tev;
+    tev = n;
+    tcap = ncap;
+  }
+  BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused], s));
+  return BLWS_OK;
+}
+
+blws_status Ctx::time_end(cudaStream_t s, double work) {
+  if (!timing) return BLWS_OK;
+  BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused + 1], s));
+  ++tused;
+  twork += work;
+  return BLWS_OK;
+}
+
 blws_status Ctx::trim() {
   if (sole_stream)
     BLWS_TRY_CUDA(this, cudaStreamSynchronize(sole_stream));
@@ -171,6 +195,8 @@ blws_status blws_destroy(blws_ctx* ctx) {
   for (int b = 0; b < blws::BUF_COUNT_; ++b)
     if (ctx->buf[b]) cudaFree(ctx->buf[b]);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  for (size_t i = 0; i < 2 * ctx->tcap; ++i) cudaEventDestroy(ctx->tev[i]);
+  delete[] ctx->tev;
   delete ctx;
   return BLWS_OK;
 }
@@ -469,6 +495,33 @@ blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double
                                      cudaMemcpyDeviceToHost, s));
   BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   if (tc_error_seen(ctx)) return ctx->fail(BLWS_ETIMEOUT, "blws_gemm: a tensor-core wait ran out");
+  return BLWS_OK;
+}
+
+blws_status blws_timing_start(blws_ctx* ctx) {
+  if (!ctx) return BLWS_EINVAL;
+  ctx->timing = true;
+  ctx->tused = 0;
+  ctx->twork = 0.0;
+  return BLWS_OK;
+}
+
+blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, double* work) {
+  if (!ctx || !ms || !launches || !work) return BLWS_EINVAL;
+  ctx->timing = false;
+  BLWS_TRY(bind_device(ctx));
+  double total = 0.0;
+  for (size_t i = 0; i < ctx->tused; ++i) {
+    BLWS_TRY_CUDA(ctx, cudaEventSynchronize(ctx->tev[2 * i + 1]));
+    float t = 0.0f;
+    BLWS_TRY_CUDA(ctx, cudaEventElapsedTime(&t, ctx->tev[2 * i], ctx->tev[2 * i + 1]));
+    total += t;
+  }
+  *ms = total;
+  *launches = ctx->tused;
+  *work = ctx->twork;
+  ctx->tused = 0;
+  ctx->twork = 0.0;
   return BLWS_OK;
 }
 

@@ -70,7 +70,8 @@ enum Buf {
   BUF_TRI,       // eigen-solver: tridiagonal-route scratch (FP32)
   BUF_EIG_GRP,   // eigen-solver: sorted group ids of the tridiagonal route
   BUF_OZ_G,      // FP64-equivalent general products: digit planes of both operands
-  BUF_RPCA_A,    // RPCA, FP64-equivalent mode: A = U diag(theta) V^T as a product (m x n)
+  BUF_RPCA_A,    // RPCA, FP64-equivalent and mixed modes: A = U diag(theta) V^T as a product (m x n)
+  BUF_TC_G,      // mixed precision: TF32 planes of both operands of a general product
   BUF_COUNT_
 };
 
@@ -105,6 +106,19 @@ struct Ctx {
   // FP32 eigen stage: 0 the tridiagonal route where it applies, 1 Jacobi only
   // (environment BLWS_EIG=jacobi at context creation)
   int eig_route = 0;
+  // timing of the product with the augmented matrix (step a2), on request
+  // (blws_timing_start / blws_timing_stop): a pair of events around the
+  // kernel(s) of each product, and the work m n b it did
+  bool timing = false;
+  cudaEvent_t* tev = nullptr;   // 2 * tcap events
+  size_t tcap = 0, tused = 0;
+  double twork = 0.0;
+  // events around one product's kernels (no-ops unless timing is on)
+  blws_status time_begin(cudaStream_t s);
+  blws_status time_end(cudaStream_t s, double work);
+  // a mixed-precision solve in its refinement tail: FP64 products go to the
+  // FP64-equivalent digit-plane kernels as in a BLWS_PREC_FP64_TC context
+  bool oz_tail = false;
   // tridiagonal reduction: 0 by rows on a cluster where it fits, 1 the packed
   // kernels (environment BLWS_TRI=packed at context creation)
   int tri_route = 0;

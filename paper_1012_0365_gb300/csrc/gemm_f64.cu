@@ -312,9 +312,13 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
   }
   // A^T A (the Gram matrices): symmetric, so one triangle of tiles is computed
   const bool sym = ta && !tb && A == B && lda == ldb && M == N && beta == 0.0;
-  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)M * N * K >= kOzGemmMin &&
+  if (!fp32 && (ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->oz_tail) && (double)M * N * K >= kOzGemmMin &&
       std::min(M, N) >= 16 && K >= 64)
     return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  // mixed precision: the FP32-level block products on the tensor cores (TF32 hi + lo)
+  if (fp32 && ctx->cfg.precision == BLWS_PREC_MIXED && (double)M * N * K >= kTcGemmMin &&
+      std::min(M, N) >= 16 && K >= 32)
+    return tc_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
   return gemm_any(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, fp32, sym);
 }
 
@@ -322,9 +326,12 @@ blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, d
                      const double* A, int lda, const double* B, int ldb, double* C, int ldc, bool fp32) {
   if (n <= 0) return BLWS_OK;
   if (K <= 0) return gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32);
-  if (!fp32 && ctx->cfg.precision == BLWS_PREC_FP64_TC && (double)n * n * K >= kOzGemmMin && n >= 16 &&
+  if (!fp32 && (ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->oz_tail) && (double)n * n * K >= kOzGemmMin && n >= 16 &&
       K >= 64)
     return oz_gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, true);
+  if (fp32 && ctx->cfg.precision == BLWS_PREC_MIXED && (double)n * n * K >= kTcGemmMin && n >= 16 &&
+      K >= 32 && n <= 256)
+    return tc_gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, true);
   return gemm_any(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32, true);
 }
 

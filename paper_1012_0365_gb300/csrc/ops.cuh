@@ -93,6 +93,13 @@ blws_status tc_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int l
 // transposed planes of the m x n column-major A: plane(i, j) = A[i + j lda]
 blws_status tc_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int lda, int m, int n,
                                 const TcPlanes& out);
+// C = alpha op(A) op(B) + beta C from split TF32 operands on the tensor cores
+// (mixed-precision block products; any N, 256 columns per launch); sym: the
+// product is known to be symmetric and C is made exactly so (N <= 256)
+blws_status tc_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                    bool sym = false);
+constexpr double kTcGemmMin = 4.0e6;
 // P = [W X_v; W^T X_u] (FP64 out) from W's row-major planes Wr (m rows) and
 // column-major planes Wc (n rows); X is (m+n) x b FP64, b <= 256.
 blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const TcPlanes& Wc, int m,

@@ -12,7 +12,8 @@
 // SVT input W.  Reads D, E, Y; writes E', Y, W.  In the FP64-equivalent mode
 // the rank-c product is an FP64 ALU bound of its own (2c flops per element),
 // so there A = (U diag(theta)) V^T is formed first as a digit-plane
-// tensor-core product and the pass reads it (EP_PRE).
+// tensor-core product and the pass reads it (EP_PRE); the mixed mode forms it
+// the same way from split TF32 operands on the tensor cores.
 #include <math.h>
 
 #include <algorithm>
@@ -336,15 +337,22 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   // mixed precision: TF32 planes of W in both orientations, rebuilt from W
   // each iteration until the residual reaches p.mixed_tol
   bool mixed = ctx->cfg.precision == BLWS_PREC_MIXED;
-  const bool fp64tc = ctx->cfg.precision == BLWS_PREC_FP64_TC;
+  // FP64-equivalent digit-plane products: the whole solve in a FP64_TC
+  // context, and the refinement tail of a mixed one (switched on below)
+  bool fp64tc = ctx->cfg.precision == BLWS_PREC_FP64_TC;
+  struct TailReset {  // the context's tail switch never outlives this solve
+    Ctx* c;
+    ~TailReset() { c->oz_tail = false; }
+  } tail_reset{ctx};
   int mixed_iters = 0;
   TcPlanes Wr{}, Wc{};
   OzPlanes Or{}, Oc{};
   double* Apre = nullptr;
-  if (fp64tc) {
-    BLWS_TRY(oz_alloc(ctx, m, n, &Or, &Oc));
-    BLWS_TRY(ctx->get(BUF_RPCA_A, (size_t)ld * n, &Apre));
-  }
+  // (a mixed solve takes both plane sets from one workspace buffer, the digit
+  // planes first, at their larger size: the TF32 planes of the mixed phase
+  // and the digit planes of its tail are never in use at the same time)
+  if (fp64tc || mixed) BLWS_TRY(oz_alloc(ctx, m, n, &Or, &Oc));
+  if (fp64tc || mixed) BLWS_TRY(ctx->get(BUF_RPCA_A, (size_t)ld * n, &Apre));
   if (mixed) {
     const int ldr = tc_ld(n), ldc = tc_ld(m);
     float* wp = nullptr;
@@ -400,13 +408,15 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     // FP64-equivalent mode: A = (U diag(theta)) V^T over the sv computed pairs
     // (theta is zero past the count) as a digit-plane product, when it is
     // large enough for gemm to route it there
-    if (fp64tc && sv >= 64) {
+    // mixed mode: the same product from split TF32 operands on the tensor cores
+    const bool pre = (fp64tc && sv >= 64) || (mixed && sv >= 16 && std::min(m, n) >= 16);
+    if (pre) {
       double* Us = nullptr;
       BLWS_TRY(ctx->get(BUF_P2, (size_t)m * sv, &Us));  // CholeskyQR scratch, free here
       scale_columns<<<std::min(ceil_div((long long)m * sv, 256), ctx->sms * 8), 256, 0, s>>>(
           m, sv, Uw, th, Us);
       BLWS_CHECK_LAUNCH(ctx);
-      BLWS_TRY(gemm(ctx, s, false, true, m, n, sv, 1.0, Us, m, Vw, n, 0.0, Apre, ld));
+      BLWS_TRY(gemm(ctx, s, false, true, m, n, sv, 1.0, Us, m, Vw, n, 0.0, Apre, ld, mixed));
       rpca_epilogue<EP_PRE, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
                                                           Ecur, Enext, Y, W, Apre, mu, mu_next,
                                                           lam, zpart);
@@ -444,7 +454,13 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       converged = true;
       break;
     }
-    if (mixed && res < p.mixed_tol) mixed = false;  // FP64 products from here on
+    if (mixed && res < p.mixed_tol) {
+      // the refinement tail: FP64-equivalent products (BF16 digit planes on the
+      // tensor cores, errors at the FP64 level) from here on
+      mixed = false;
+      fp64tc = true;
+      ctx->oz_tail = true;
+    }
   }
   if (!converged) it = p.max_iter;
   // outputs: A = U diag(th) V^T of the last SVT; E = the E of that iteration

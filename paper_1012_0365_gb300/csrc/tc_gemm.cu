@@ -200,6 +200,35 @@ __global__ void tc_reduce(int M, int N, int npad, int splits, int Mpad, const fl
   }
 }
 
+// C = alpha (sum over splits) + beta C for a general product, each output
+// summed by a group of G lanes (lane q adds splits q, q + G, ... in order, then
+// a fixed shuffle tree); sym (M = N, beta = 0): an element below the diagonal
+// is formed from its mirror's partials, so C is exactly symmetric
+__global__ void tc_reduce_ab(int M, int N, int npad, int splits, int Mpad, const float* __restrict__ part,
+                             double alpha, double beta, double* C, int ldc, int sym, int G) {
+  const size_t total = (size_t)M * N;
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  const int q = (int)(tid % G);
+  const size_t span = (total * G + nth - 1) / nth * nth;  // the same trip count in every lane
+  for (size_t t = tid; t < span; t += nth) {
+    const size_t e = t / G;
+    double acc = 0.0;
+    if (e < total) {
+      const int r = (int)(e % M), j = (int)(e / M);
+      const bool mirror = sym && r > j;
+      const int rr = mirror ? j : r, jj = mirror ? r : j;
+      for (int z = q; z < splits; z += G) acc += (double)part[((size_t)z * npad + jj) * Mpad + rr];
+    }
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (q == 0 && e < total) {
+      const int r = (int)(e % M), j = (int)(e / M);
+      double* c = C + r + (size_t)j * ldc;
+      *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+    }
+  }
+}
+
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -384,6 +413,7 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
   jobs.N = b;
   jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
   const int blocks = jobs.blocks0 + tiles1 * splits[1];
+  BLWS_TRY(ctx->time_begin(s));
   switch (npad) {
     case 16: BLWS_TRY((launch_tc<16, 5>(ctx, s, jobs, blocks))); break;
     case 32: BLWS_TRY((launch_tc<32, 5>(ctx, s, jobs, blocks))); break;
@@ -393,6 +423,7 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
     case 192: BLWS_TRY((launch_tc<192, 2>(ctx, s, jobs, blocks))); break;
     default: BLWS_TRY((launch_tc<256, 2>(ctx, s, jobs, blocks))); break;
   }
+  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b));
   for (int t = 0; t < 2; ++t) {
     const size_t total = (size_t)Ms[t] * b;
     if (total == 0) continue;
@@ -432,6 +463,88 @@ blws_status wait_probe(Ctx* ctx, cudaStream_t s, unsigned polls) {
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
   wait_probe_kernel<<<1, 32, 0, s>>>(polls, reinterpret_cast<int*>(scal + SLOT_TCERR));
   BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+
+}  // namespace blws
+
+// ------------------------------------------------------- general products --
+namespace blws {
+
+// C = alpha op(A) op(B) + beta C from split TF32 operands (three tcgen05
+// products per K step, FP32 sums of at most 256 terms, FP64 beyond), for the
+// mixed-precision mode's block products.  The columns of op(B) go through the
+// accumulator 256 at a time.
+blws_status tc_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
+                    const double* A, int lda, const double* B, int ldb, double beta, double* C, int ldc,
+                    bool sym) {
+  if (M <= 0 || N <= 0 || K <= 0) return ctx->fail(BLWS_EINVAL, "tc_gemm: empty product");
+  BLWS_TRY(get_encoder(ctx));
+  constexpr int kCols = 256;
+  const int ldk = tc_ld(K);
+  const int nmax = std::min(N, kCols);
+  float* base = nullptr;
+  BLWS_TRY(ctx->get(BUF_TC_G, (size_t)2 * ((size_t)M + nmax) * ldk, &base));
+  const TcPlanes Ap{base, base + (size_t)M * ldk, M, K, ldk};
+  float* bbase = base + (size_t)2 * M * ldk;
+  // rows of op(A), K-major
+  if (ta) BLWS_TRY(tc_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
+  else BLWS_TRY(tc_planes_from_rows(ctx, s, A, lda, M, K, Ap));
+  const int tiles = ceil_div(M, kTcBM);
+  const int kblocks = ceil_div(K, kTcBK);
+  // about one wave of CTAs, at least two K blocks each
+  const int per = ceil_div(ctx->sms, std::max(1, tiles));
+  int sp = std::max(1, std::min(per, ceil_div(kblocks, 2)));
+  sp = std::max(sp, ceil_div(K, kTcMaxChunk));
+  const int kchunk = ceil_div(kblocks, sp) * kTcBK;
+  const int splits = ceil_div(K, kchunk);
+  double* scal = nullptr;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  for (int j0 = 0; j0 < N; j0 += kCols) {
+    const int nc = std::min(kCols, N - j0);
+    const int npad = tc_npad(nc);
+    const TcPlanes Bp{bbase, bbase + (size_t)nc * ldk, nc, K, ldk};
+    // columns j0 .. j0 + nc of op(B) as rows, K-major
+    if (tb) BLWS_TRY(tc_planes_from_rows(ctx, s, B + j0, ldb, nc, K, Bp));
+    else BLWS_TRY(tc_planes_from_cols(ctx, s, B + (size_t)j0 * ldb, ldb, 0, K, nc, Bp));
+    float* part = nullptr;
+    BLWS_TRY(ctx->get(BUF_TC_PART, (size_t)splits * npad * tiles * kTcBM, &part));
+    TcJobs jobs;
+    memset(&jobs, 0, sizeof(jobs));
+    TcJob& J = jobs.job[0];
+    BLWS_TRY(encode_plane(ctx, &J.a_hi, Ap.hi, M, K, ldk, kTcBM));
+    BLWS_TRY(encode_plane(ctx, &J.a_lo, Ap.lo, M, K, ldk, kTcBM));
+    BLWS_TRY(encode_plane(ctx, &J.b_hi, Bp.hi, nc, K, ldk, npad));
+    BLWS_TRY(encode_plane(ctx, &J.b_lo, Bp.lo, nc, K, ldk, npad));
+    J.part = part;
+    J.M = M;
+    J.K = K;
+    J.tiles = tiles;
+    J.splits = splits;
+    J.kchunk = kchunk;
+    J.Mpad = tiles * kTcBM;
+    jobs.job[1] = J;  // unused: every block belongs to job 0
+    jobs.blocks0 = tiles * splits;
+    jobs.N = nc;
+    jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
+    const int blocks = jobs.blocks0;
+    switch (npad) {
+      case 16: BLWS_TRY((launch_tc<16, 5>(ctx, s, jobs, blocks))); break;
+      case 32: BLWS_TRY((launch_tc<32, 5>(ctx, s, jobs, blocks))); break;
+      case 64: BLWS_TRY((launch_tc<64, 4>(ctx, s, jobs, blocks))); break;
+      case 96: BLWS_TRY((launch_tc<96, 3>(ctx, s, jobs, blocks))); break;
+      case 128: BLWS_TRY((launch_tc<128, 3>(ctx, s, jobs, blocks))); break;
+      case 192: BLWS_TRY((launch_tc<192, 2>(ctx, s, jobs, blocks))); break;
+      default: BLWS_TRY((launch_tc<256, 2>(ctx, s, jobs, blocks))); break;
+    }
+    const size_t total = (size_t)M * nc;
+    int G = 1;
+    while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)ctx->sms * 8 * 256) G *= 2;
+    const bool symc = sym && N <= kCols && M == N && beta == 0.0;
+    tc_reduce_ab<<<(int)std::min<size_t>((total * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
+        M, nc, npad, splits, J.Mpad, part, alpha, beta, C + (size_t)j0 * ldc, ldc, symc ? 1 : 0, G);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
   return BLWS_OK;
 }
 

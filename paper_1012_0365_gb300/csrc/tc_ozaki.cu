@@ -99,7 +99,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
   __shared__ __align__(8) uint64_t full_bar[kOzStages];
   __shared__ __align__(8) uint64_t empty_bar[kOzStages];
   __shared__ __align__(8) uint64_t chunk_bar;    // MMA -> drain: a chunk's levels are complete
-  __shared__ __align__(8) uint64_t drained_bar;  // drain -> MMA: the levels may be overwritten
+  // drain -> MMA, one per level: the level's accumulator of the previous chunk
+  // has been read and may be overwritten (the next chunk's MMAs start on the
+  // levels already drained while the drain works through the rest)
+  __shared__ __align__(8) uint64_t level_bar[kOzLevels];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail_sh;
 
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&chunk_bar, 1);
-    mbar_init(&drained_bar, 128);  // the four drain warps
+    for (int L = 0; L < kOzLevels; ++L) mbar_init(&level_bar[L], 128);  // the four drain warps
     fail_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -165,18 +168,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = bf16_idesc(kOzBM, kOzBN);
     int kb = 0;
-    for (int c = 0; c < nchunks && !fail_sh; ++c) {
-      if (c > 0 && !mbar_wait(&drained_bar, (uint32_t)((c - 1) & 1))) {
-        fail_sh = 1;
-        break;
-      }
-      tc_fence_after();
+    bool stop = false;
+    for (int c = 0; c < nchunks && !stop; ++c) {
       const int kb_end = min(nk, kb + kPerChunk);
       for (int kc = 0; kb < kb_end; ++kb, ++kc) {
         const int s = kb % kOzStages;
         const uint32_t round = (uint32_t)(kb / kOzStages);
         if (!mbar_wait(&full_bar[s], round & 1u)) {
-          fail_sh = 1;
+          stop = true;
           break;
         }
         tc_fence_after();
@@ -190,10 +189,19 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
             const uint64_t ad = sw64_desc(st + (uint32_t)(t - 1) * A_BYTES + kk * 32);
             const uint64_t bd = sw64_desc(st + kOzS * A_BYTES + (uint32_t)(u - 1) * B_BYTES + kk * 32);
             const uint32_t acc = (kc > 0 || kk > 0 || !first_of_level) ? 1u : 0u;
-            mma_bf16(tbase + (uint32_t)((L - 2) * kOzBN), ad, bd, idesc, acc);
+            if (c > 0 && !acc) {  // the level restarts: its previous chunk must be drained
+              if (!mbar_wait(&level_bar[L - 2], (uint32_t)((c - 1) & 1))) stop = true;
+              tc_fence_after();
+            }
+            if (!stop) mma_bf16(tbase + (uint32_t)((L - 2) * kOzBN), ad, bd, idesc, acc);
           }
         }
         mma_commit(&empty_bar[s]);
+        if (stop) break;
+      }
+      if (stop) {
+        fail_sh = 1;
+        break;
       }
       mma_commit(&chunk_bar);  // this chunk's levels complete once the MMAs above are done
     }
@@ -229,16 +237,20 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
 #pragma unroll 1
     for (int L = 2; L <= kOzS + 1; ++L) {
       const float scale = __uint_as_float((uint32_t)(127 - 7 * L) << 23);  // 2^(-7 L), exact
+      float v[kOzBN];
 #pragma unroll
       for (int c0 = 0; c0 < kOzBN; c0 += 16) {
-        float v[16];
-        tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * kOzBN + c0), v);
+        float w16[16];
+        tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * kOzBN + c0), w16);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) two_sum_acc(hi[c0 + j], lo[c0 + j], v[j] * scale);
+        for (int j = 0; j < 16; ++j) v[c0 + j] = w16[j];
       }
+      // the level is in registers: release it to the next chunk's MMAs
+      tc_fence_before();
+      mbar_arrive(&level_bar[L - 2]);
+#pragma unroll
+      for (int j = 0; j < kOzBN; ++j) two_sum_acc(hi[j], lo[j], v[j] * scale);
     }
-    tc_fence_before();
-    mbar_arrive(&drained_bar);
   }
   if (ok && !fail_sh) {
     // (hi, lo) pairs out; the FP64 combination and the power-of-two scales are
@@ -304,17 +316,21 @@ __global__ void oz_fill(int n, int v, int* E) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) E[i] = v;
 }
 
-// digit planes of the column-major slab, one CTA per plane row r (= column r
-// of A, K along A's rows row0 .. row0 + inner): the column's maximum, its
-// exponent E[r], then its digits (plane t, (r, k) at t plane_rows ld + r ld + k;
-// zero padding up to ld)
+// digit planes of the column-major slab: plane row r (= column r of A, K along
+// A's rows row0 .. row0 + inner) is split by `chunks` CTAs, each of which finds
+// the column's maximum (all of it: every CTA of the column gets the same
+// exponent without a second launch) and writes the digits of its share of
+// 0 .. ld (plane t, (r, k) at t plane_rows ld + r ld + k; zero padding past
+// inner); the first CTA of the column records the exponent E[r]
 __global__ void __launch_bounds__(256)
 oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __restrict__ A, int lda,
-               int row0, int* E, __nv_bfloat16* planes) {
+               int row0, int chunks, int* E, __nv_bfloat16* planes) {
   __shared__ double red[8];
   __shared__ int e_sh;
   const size_t plane = (size_t)plane_rows * ld;
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+  const int span = (ld + chunks - 1) / chunks;
+  for (int item = blockIdx.x; item < rows * chunks; item += gridDim.x) {
+    const int r = item / chunks, c = item % chunks;
     const double* col = A + row0 + (size_t)r * lda;
     double mx = 0.0;
     for (int k = threadIdx.x; k < inner; k += blockDim.x) mx = fmax(mx, fabs(col[k]));
@@ -326,11 +342,12 @@ oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __rest
       double m2 = 0.0;
       for (int w = 0; w < (int)blockDim.x / 32; ++w) m2 = fmax(m2, red[w]);
       e_sh = scale_exp(m2);
-      E[r] = e_sh;
+      if (c == 0) E[r] = e_sh;
     }
     __syncthreads();
     const int er = e_sh;
-    for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    const int kend = min(ld, (c + 1) * span);
+    for (int k = c * span + threadIdx.x; k < kend; k += blockDim.x) {
       int a[kOzS];
       if (k < inner) {
         digits(col[k], er, a);
@@ -370,27 +387,62 @@ __global__ void oz_planes_rows(int m, int n, int ld, int plane_rows, const doubl
   }
 }
 
-// P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64, split order.
-// sym (a product known to be symmetric, M = N, beta = 0): an element below the
-// diagonal is formed from its mirror's partials, so P is exactly symmetric.
+// P(r, j) = 2^(E_r + F_j) sum over splits of (hi + lo), in FP64.  Each output
+// is summed by a group of G lanes (G a power of two up to 32, so that small
+// outputs with many splits still fill the GPU): lane q adds splits q, q + G, ...
+// in order, then the group adds its lanes with a fixed shuffle tree -- a fixed
+// order for given sizes.  sym (a product known to be symmetric, M = N,
+// beta = 0): an element below the diagonal is formed from its mirror's
+// partials, so P is exactly symmetric.
 __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const float2* __restrict__ part,
                           const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ P,
-                          int ldp, double alpha = 1.0, double beta = 0.0, int sym = 0) {
+                          int ldp, double alpha, double beta, int sym, int G) {
   const size_t total = (size_t)M * N;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
-       e += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e % M), j = (int)(e / M);
-    const bool mirror = sym && r > j;
-    const int rr = mirror ? j : r, jj = mirror ? r : j;
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t nth = (size_t)gridDim.x * blockDim.x;
+  const int q = (int)(tid % G);
+  // every lane of a warp runs the same number of iterations (the shuffles need them all)
+  const size_t span = (total * G + nth - 1) / nth * nth;
+  for (size_t t = tid; t < span; t += nth) {
+    const size_t e = t / G;
     double acc = 0.0;
-    for (int z = 0; z < splits; ++z) {
-      const float2 v = part[((size_t)z * npad + jj) * Mpad + rr];
-      acc += (double)v.x + (double)v.y;
+    int rr = 0, jj = 0;
+    if (e < total) {
+      const int r = (int)(e % M), j = (int)(e / M);
+      const bool mirror = sym && r > j;
+      rr = mirror ? j : r;
+      jj = mirror ? r : j;
+      const size_t zs = (size_t)npad * Mpad;
+      const float2* src = part + (size_t)jj * Mpad + rr;
+      int z = q;
+      for (; z + 3 * G < splits; z += 4 * G) {  // four independent loads, then the sums in order
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = src[(size_t)(z + u * G) * zs];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc += (double)v[u].x + (double)v[u].y;
+      }
+      for (; z < splits; z += G) {
+        const float2 v = src[(size_t)z * zs];
+        acc += (double)v.x + (double)v.y;
+      }
     }
-    const double v = ldexp(acc, ea[rr] + eb[jj]);
-    double* c = P + r + (size_t)j * ldp;
-    *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (q == 0 && e < total) {
+      const int r = (int)(e % M), j = (int)(e / M);
+      const double v = ldexp(acc, ea[rr] + eb[jj]);
+      double* c = P + r + (size_t)j * ldp;
+      *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
+    }
   }
+}
+
+// lanes per output of oz_reduce: enough to fill ~8 x 256 threads per SM, at
+// most 32 and the split count
+int oz_lanes(int sms, size_t total, int splits) {
+  int G = 1;
+  while (G < 32 && 2 * G <= splits && total * (size_t)(2 * G) <= (size_t)sms * 8 * 256) G *= 2;
+  return G;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_oz_encode = nullptr;
@@ -409,13 +461,15 @@ blws_status oz_encoder(Ctx* ctx) {
   return BLWS_OK;
 }
 
-// 3-D map over S digit planes of rows x inner BF16 (ld elements per row)
-blws_status oz_encode(Ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int rows, int inner, int ld,
-                      int box_rows) {
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld % 8))
+// 3-D map over S digit planes of rows x inner BF16 (ld elements per row, planes
+// plane_rows rows apart); rows past `rows` read as zero digits (the copy's
+// out-of-bounds fill), so padding rows need not be written
+blws_status oz_encode(Ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int rows, int plane_rows, int inner,
+                      int ld, int box_rows) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld % 8) || rows > plane_rows)
     return ctx->fail(BLWS_EINVAL, "digit plane not 16-byte aligned");
   cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)kOzS};
-  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)rows * ld * 2};
+  cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)plane_rows * ld * 2};
   cuuint32_t box[3] = {(cuuint32_t)kOzBK, (cuuint32_t)box_rows, (cuuint32_t)kOzS};
   cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = g_oz_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base),
@@ -427,6 +481,26 @@ blws_status oz_encode(Ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int
 }
 
 size_t oz_smem_bytes() { return (size_t)kOzStages * kOzS * (kOzBM + kOzBN) * kOzBK * 2 + 1024; }
+
+// Split of K for a product of `units` (row tile, column group) CTAs over
+// `kblocks` K blocks with `share` SMs: the split count that minimises waves x
+// (K blocks per CTA + a fixed CTA overhead of about two K blocks), fewest
+// splits on ties.  Splits fall on K-block boundaries; each split still sums
+// its terms 256 at a time.
+int oz_pick_splits(int share, int units, int kblocks) {
+  share = std::max(share, 1);
+  int best = 1;
+  long long best_cost = -1;
+  for (int sp = 1; sp <= std::min(kblocks, 256); ++sp) {
+    const long long waves = ceil_div((long long)units * sp, share);
+    const long long cost = waves * (ceil_div(kblocks, sp) + 2);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = sp;
+    }
+  }
+  return best;
+}
 
 }  // namespace
 
@@ -462,8 +536,11 @@ blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int l
 blws_status oz_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int lda, int row0, int inner,
                                 int rows, const OzPlanes& out) {
   if (rows <= 0) return BLWS_OK;
-  oz_planes_cols<<<std::min(rows, ctx->sms * 16), 256, 0, s>>>(rows, out.rows, inner, out.ld, A, lda,
-                                                               row0, out.e, out.d);
+  // a few CTAs per column when there are too few columns to fill the GPU
+  // (each rereads its column for the maximum: cheap next to the digit writes)
+  const int chunks = std::max(1, std::min(8, ceil_div(2 * ctx->sms, rows)));
+  oz_planes_cols<<<std::min(rows * chunks, ctx->sms * 16), 256, 0, s>>>(rows, out.rows, inner, out.ld, A, lda,
+                                                                        row0, chunks, out.e, out.d);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
@@ -480,8 +557,6 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   BLWS_TRY(ctx->get(BUF_OZ_E, (size_t)2 * npad * sizeof(int), (void**)&xe));
   OzPlanes Xu{xp, xe, npad, m, ldu};
   OzPlanes Xv{xp + (size_t)kOzS * npad * ldu, xe + npad, npad, n, ldv};
-  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(xe, 0, sizeof(int) * 2 * npad, s));
-  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(xp, 0, (size_t)kOzS * npad * (ldu + ldv) * sizeof(__nv_bfloat16), s));
   BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, 0, m, b, Xu));
   BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, m, n, b, Xv));
 
@@ -491,13 +566,14 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   memset(&jobs, 0, sizeof(jobs));
   int splits[2], kchunk[2];
   size_t off[2], total = 0;
+  // the SMs are shared between the two products in proportion to their work
+  // (a tall W gives one product few row tiles and a long K: it needs the split)
+  const double work0 = (double)tiles[0] * ceil_div(Ks[0], kOzBK), work1 = (double)tiles[1] * ceil_div(Ks[1], kOzBK);
   for (int t = 0; t < 2; ++t) {
-    // each product alone fills about one wave (a tall W gives one product
-    // few row tiles and a long K: it needs the split)
-    const int kchunks = ceil_div(Ks[t], kOzChunk);
-    const int per = ceil_div(ctx->sms, std::max(1, tiles[t] * ngroups));
-    const int sp = std::max(1, std::min(per, kchunks));
-    kchunk[t] = ceil_div(kchunks, sp) * kOzChunk;
+    const int kblocks = ceil_div(Ks[t], kOzBK);
+    const int share = (int)std::lround(ctx->sms * (t ? work1 : work0) / (work0 + work1));
+    const int sp = oz_pick_splits(share, tiles[t] * ngroups, kblocks);
+    kchunk[t] = ceil_div(kblocks, sp) * kOzBK;
     splits[t] = ceil_div(Ks[t], kchunk[t]);
     off[t] = total;
     total += (size_t)splits[t] * npad * tiles[t] * kOzBM;
@@ -508,8 +584,8 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   const OzPlanes* B[2] = {&Xv, &Xu};
   for (int t = 0; t < 2; ++t) {
     OzJob& J = jobs.job[t];
-    BLWS_TRY(oz_encode(ctx, &J.a, A[t]->d, Ms[t], Ks[t], A[t]->ld, kOzBM));
-    BLWS_TRY(oz_encode(ctx, &J.b, B[t]->d, npad, Ks[t], B[t]->ld, kOzBN));
+    BLWS_TRY(oz_encode(ctx, &J.a, A[t]->d, Ms[t], Ms[t], Ks[t], A[t]->ld, kOzBM));
+    BLWS_TRY(oz_encode(ctx, &J.b, B[t]->d, b, npad, Ks[t], B[t]->ld, kOzBN));
     J.ea = A[t]->e;
     J.eb = B[t]->e;
     J.part = part + off[t];
@@ -530,13 +606,16 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   const int blocks = jobs.blocks0 + tiles[1] * ngroups * splits[1];
   const int bytes = (int)oz_smem_bytes();
   BLWS_TRY_CUDA(ctx, cudaFuncSetAttribute(oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  BLWS_TRY(ctx->time_begin(s));
   oz_kernel<<<blocks, kOzThreads, bytes, s>>>(jobs);
   BLWS_CHECK_LAUNCH(ctx);
+  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b));
   for (int t = 0; t < 2; ++t) {
     const size_t tot = (size_t)Ms[t] * b;
-    oz_reduce<<<std::min(ceil_div((long long)tot, 256), ctx->sms * 8), 256, 0, s>>>(
+    const int G = oz_lanes(ctx->sms, tot, splits[t]);
+    oz_reduce<<<(int)std::min<size_t>((tot * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
         Ms[t], b, npad, splits[t], jobs.job[t].Mpad, jobs.job[t].part, A[t]->e, B[t]->e,
-        P + (t ? m : 0), ldp);
+        P + (t ? m : 0), ldp, 1.0, 0.0, 0, G);
     BLWS_CHECK_LAUNCH(ctx);
   }
   return BLWS_OK;
@@ -564,28 +643,23 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
   int* eb = ea + M;
   const OzPlanes Ap{da, ea, M, K, ldk};
   const OzPlanes Bp{db, eb, npad, K, ldk};
-  // op(B) columns beyond N stay zero digits with exponent 0
-  if (npad > N) {
-    BLWS_TRY_CUDA(ctx, cudaMemsetAsync(db, 0, pb * sizeof(__nv_bfloat16), s));
-    BLWS_TRY_CUDA(ctx, cudaMemsetAsync(eb, 0, sizeof(int) * npad, s));
-  }
   if (ta) BLWS_TRY(oz_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
   else BLWS_TRY(oz_planes_from_rows(ctx, s, A, lda, M, K, Ap));
   if (!tb) BLWS_TRY(oz_planes_from_cols(ctx, s, B, ldb, 0, K, N, Bp));
   else BLWS_TRY(oz_planes_from_rows(ctx, s, B, ldb, N, K, OzPlanes{db, eb, npad, K, ldk}));
   const int tiles = ceil_div(M, kOzBM);
-  const int kchunks = ceil_div(K, kOzChunk);
-  const int per = ceil_div(ctx->sms, std::max(1, tiles * ngroups));
-  const int sp = std::max(1, std::min(per, kchunks));
-  const int kchunk = ceil_div(kchunks, sp) * kOzChunk;
+  const int kblocks = ceil_div(K, kOzBK);
+  const int sp = oz_pick_splits(ctx->sms, tiles * ngroups, kblocks);
+  const int kchunk = ceil_div(kblocks, sp) * kOzBK;
   const int splits = ceil_div(K, kchunk);
   float2* part = nullptr;
   BLWS_TRY(ctx->get(BUF_TC_PART, (size_t)splits * npad * tiles * kOzBM * sizeof(float2), (void**)&part));
   OzJobs jobs;
   memset(&jobs, 0, sizeof(jobs));
   OzJob& J = jobs.job[0];
-  BLWS_TRY(oz_encode(ctx, &J.a, da, M, K, ldk, kOzBM));
-  BLWS_TRY(oz_encode(ctx, &J.b, db, npad, K, ldk, kOzBN));
+  BLWS_TRY(oz_encode(ctx, &J.a, da, M, M, K, ldk, kOzBM));
+  // op(B) columns past N: zero digits from the copy's out-of-bounds fill
+  BLWS_TRY(oz_encode(ctx, &J.b, db, N, npad, K, ldk, kOzBN));
   J.ea = ea;
   J.eb = eb;
   J.part = part;
@@ -608,8 +682,9 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
   oz_kernel<<<jobs.blocks0, kOzThreads, smem, s>>>(jobs);
   BLWS_CHECK_LAUNCH(ctx);
   const size_t tot = (size_t)M * N;
-  oz_reduce<<<std::min(ceil_div((long long)tot, 256), ctx->sms * 8), 256, 0, s>>>(
-      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta, sym && M == N && beta == 0.0 ? 1 : 0);
+  const int G = oz_lanes(ctx->sms, tot, splits);
+  oz_reduce<<<(int)std::min<size_t>((tot * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
+      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta, sym && M == N && beta == 0.0 ? 1 : 0, G);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }

