@@ -483,17 +483,22 @@ blws_status oz_encode(Ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int
 size_t oz_smem_bytes() { return (size_t)kOzStages * kOzS * (kOzBM + kOzBN) * kOzBK * 2 + 1024; }
 
 // Split of K for a product of `units` (row tile, column group) CTAs over
-// `kblocks` K blocks with `share` SMs: the split count that minimises waves x
-// (K blocks per CTA + a fixed CTA overhead of about two K blocks), fewest
-// splits on ties.  Splits fall on K-block boundaries; each split still sums
+// `kblocks` K blocks with `share` SMs (one CTA per SM): the split count that
+// minimises waves x (K blocks per CTA + a fixed CTA overhead), fewest splits on
+// ties.  The overhead -- tensor-memory allocation, pipeline fill, the drain
+// and the 64 KB store of the partial sums -- was measured at about eight K
+// blocks of MMAs (2000 x 2000 product: 4 splits, 256 CTAs, 81 us; 7 splits,
+// 448 CTAs, 91 us).  Splits fall on K-block boundaries; each split still sums
 // its terms 256 at a time.
+constexpr int kOzCtaOverhead = 8;
+
 int oz_pick_splits(int share, int units, int kblocks) {
   share = std::max(share, 1);
   int best = 1;
   long long best_cost = -1;
   for (int sp = 1; sp <= std::min(kblocks, 256); ++sp) {
     const long long waves = ceil_div((long long)units * sp, share);
-    const long long cost = waves * (ceil_div(kblocks, sp) + 2);
+    const long long cost = waves * (ceil_div(kblocks, sp) + kOzCtaOverhead);
     if (best_cost < 0 || cost < best_cost) {
       best_cost = cost;
       best = sp;
@@ -566,13 +571,16 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   memset(&jobs, 0, sizeof(jobs));
   int splits[2], kchunk[2];
   size_t off[2], total = 0;
-  // the SMs are shared between the two products in proportion to their work
-  // (a tall W gives one product few row tiles and a long K: it needs the split)
+  // both products run in one launch: with equal K (a square W) one split count
+  // for both, against all the SMs; otherwise the SMs are shared in proportion
+  // to their work (a tall W gives one product few row tiles and a long K)
   const double work0 = (double)tiles[0] * ceil_div(Ks[0], kOzBK), work1 = (double)tiles[1] * ceil_div(Ks[1], kOzBK);
   for (int t = 0; t < 2; ++t) {
     const int kblocks = ceil_div(Ks[t], kOzBK);
-    const int share = (int)std::lround(ctx->sms * (t ? work1 : work0) / (work0 + work1));
-    const int sp = oz_pick_splits(share, tiles[t] * ngroups, kblocks);
+    const int sp = Ks[0] == Ks[1]
+                       ? oz_pick_splits(ctx->sms, (tiles[0] + tiles[1]) * ngroups, kblocks)
+                       : oz_pick_splits((int)std::lround(ctx->sms * (t ? work1 : work0) / (work0 + work1)),
+                                        tiles[t] * ngroups, kblocks);
     kchunk[t] = ceil_div(kblocks, sp) * kOzBK;
     splits[t] = ceil_div(Ks[t], kchunk[t]);
     off[t] = total;

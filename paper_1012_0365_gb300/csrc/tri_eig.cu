@@ -569,10 +569,6 @@ constexpr int kTriRowsThreads = BLWS_TRI_ROWS_THREADS;  // threads per CTA (a mu
 template <int kCl>
 __host__ __device__ constexpr int rows_per_cta(int n) { return (n + kCl - 1) / kCl; }
 
-template <int kCl>
-int rows_smem_bytes(int n) {
-  return n * (int)sizeof(float4) + rows_per_cta<kCl>(n) * (n + 1) * (int)sizeof(float);
-}
 
 // smallest cluster whose share of the full matrix fits one CTA (0: none)
 inline int rows_cluster(int n) {
@@ -609,10 +605,154 @@ __device__ __forceinline__ P* rows_remote(P* p, int r) {
   }
 }
 
+// Shared memory of the kernel below: the vectors (n float4), p of the local
+// rows, and the rows themselves -- sized for the larger of the cluster phase
+// (R rows of n) and the single-CTA phase (a trailing block of at most
+// kRowsSwitchM squared).
+constexpr int kRowsSwitchM = 232;
+
+template <int kCl>
+int rows_smem_bytes(int n) {
+  const int R = rows_per_cta<kCl>(n);
+  const int S = kCl > 1 ? std::min(n, kRowsSwitchM) : 0;
+  return n * (int)sizeof(float4) + std::max(R, S) * (int)sizeof(float) +
+         std::max(R * n, S * S) * (int)sizeof(float);
+}
+
+// One Householder step k over the rows this CTA holds, KC CTAs taking part.
+// Local row l is global row i = base + l KC + rank, stored at A + l ldA, and
+// element (i, j) of it at (A + l ldA)[j - base] (only j >= k + 1 > base is
+// touched).  sh_part has KC entries.
+template <int KC>
+__device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int base, float* A, int ldA,
+                                          float4* cv, float* pb, float* red, float* sh_part, float* sh_tau,
+                                          float* __restrict__ V, float* __restrict__ dv, float* __restrict__ ev,
+                                          float* __restrict__ tauv) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  // (1) row k: pending update, reflector into every CTA
+  const int lk = (k - base) / KC;
+  if (rank == (k - base) % KC && wid == lk % nw) {
+    float* row = A + (size_t)lk * ldA - base;
+    const float4 qk = cv[k];
+    float ssq = 0.0f;
+    for (int j = k + lane; j < n; j += 32) {
+      const float4 q = cv[j];
+      const float a = row[j] - sym_upd(qk, q);
+      row[j] = a;
+      if (j >= k + 2) ssq = fmaf(a, a, ssq);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
+    __syncwarp();
+    const float alpha = row[k + 1];
+    float tau = 0.0f, beta = alpha, vscale = 0.0f;
+    if (ssq > 0.0f) {
+      // the serial part of the step: a correctly rounded reciprocal and one
+      // fast quotient (2 ulp) keep it short; the FP32 stage is refined in
+      // FP64 afterwards
+      const float nrm = sqrtf(fmaf(alpha, alpha, ssq));
+      beta = alpha >= 0.0f ? -nrm : nrm;
+      tau = __fdividef(beta - alpha, beta);
+      vscale = __frcp_rn(alpha - beta);
+    }
+    if (lane == 0) {
+      dv[k] = row[k];
+      ev[k] = beta;
+      tauv[k] = tau;
+#pragma unroll
+      for (int r = 0; r < KC; ++r) *rows_remote<KC>(sh_tau, r) = tau;
+    }
+    for (int j = k + 1 + lane; j < n; j += 32) {
+      const float v = j == k + 1 ? 1.0f : (tau != 0.0f ? row[j] * vscale : 0.0f);
+#pragma unroll
+      for (int r = 0; r < KC; ++r) rows_remote<KC>(cv, r)[j].z = v;
+    }
+  }
+  rows_sync<KC>();
+  // (2) trailing rows: pending update and p_i = tau a_i . v, two rows per pass
+  const float tau = *sh_tau;
+  const int l0 = (k - base + KC - rank) / KC;  // first local row with a global index > k
+  float pvw = 0.0f;                            // this warp's sum of p_i v_i
+  for (int l = l0 + ((wid - l0 % nw) + nw) % nw; l < R; l += 2 * nw) {
+    const int i0 = base + l * KC + rank, i1 = base + (l + nw) * KC + rank;
+    if (i0 >= n) break;
+    const bool two = l + nw < R && i1 < n;
+    float* r0 = A + (size_t)l * ldA - base;
+    float* r1 = A + (size_t)(l + nw) * ldA - base;
+    const float4 q0 = cv[i0];
+    const float4 q1 = two ? cv[i1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float s0 = 0.0f, s1 = 0.0f;
+    if (two) {
+#pragma unroll 2
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const float4 q = cv[j];
+        const float a0 = r0[j] - sym_upd(q0, q);
+        const float a1 = r1[j] - sym_upd(q1, q);
+        r0[j] = a0;
+        r1[j] = a1;
+        s0 = fmaf(a0, q.z, s0);
+        s1 = fmaf(a1, q.z, s1);
+      }
+    } else {
+#pragma unroll 2
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const float4 q = cv[j];
+        const float a0 = r0[j] - sym_upd(q0, q);
+        r0[j] = a0;
+        s0 = fmaf(a0, q.z, s0);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const float p0 = tau * s0, p1 = tau * s1;
+    if (lane == 0) {
+      pb[l] = p0;
+      if (two) pb[l + nw] = p1;
+    }
+    pvw = fmaf(p0, q0.z, pvw);
+    if (two) pvw = fmaf(p1, q1.z, pvw);
+  }
+  if (lane == 0) red[wid] = pvw;
+  __syncthreads();
+  if (wid == 0) {
+    float t = lane < nw ? red[lane] : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane < KC) rows_remote<KC>(sh_part, lane)[rank] = t;
+  }
+  rows_sync<KC>();
+  // (3) K and the next pending pair (v_i, w_i) of the local rows, into every CTA
+  float K = 0.0f;
+#pragma unroll
+  for (int r = 0; r < KC; ++r) K += sh_part[r];
+  K *= 0.5f * tau;
+  for (int l = l0 + tid; l < R; l += blockDim.x) {
+    const int i = base + l * KC + rank;
+    if (i >= n) break;
+    const float v = cv[i].z;
+    const float2 vw = make_float2(v, pb[l] - K * v);
+#pragma unroll
+    for (int r = 0; r < KC; ++r) *reinterpret_cast<float2*>(&rows_remote<KC>(cv, r)[i]) = vw;
+  }
+  // reflector k out to global memory, off the serial step: CTA r writes the
+  // indices i = r (mod KC) (zero above k + 1, v_{k+1} = 1)
+  for (int i = rank + KC * tid; i < n; i += KC * (int)blockDim.x) V[i + (size_t)k * n] = i > k ? cv[i].z : 0.0f;
+  rows_sync<KC>();
+}
+
+// The reduction by rows.  kCl > 1: the cluster phase runs while the trailing
+// block is larger than kRowsSwitchM; then every CTA writes its trailing rows to
+// `stage` (global, at least kRowsSwitchM^2 floats), CTA 0 gathers the block
+// (rows and columns ks .. n-1) into its own shared memory and finishes alone,
+// with block barriers instead of cluster barriers, and the other CTAs leave.
 template <int kCl>
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kTriRowsThreads)
 tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, float* __restrict__ dv,
-                float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ tscale) {
+                float* __restrict__ ev, float* __restrict__ tauv, float* __restrict__ tscale,
+                float* __restrict__ stage) {
   extern __shared__ float4 smr[];
   __shared__ float red[32];
   __shared__ double redd[32];
@@ -622,9 +762,10 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
   int rank = 0;
   if constexpr (kCl > 1) rank = (int)cg::this_cluster().block_rank();
   const int R = rows_per_cta<kCl>(n);
+  const int S = kCl > 1 ? min(n, kRowsSwitchM) : 0;
   float4* cv = smr;                                   // x, y: pending update; z: reflector
   float* pb = reinterpret_cast<float*>(cv + n);       // p_i of the local rows
-  float* A = pb + R;                                  // local row l at A + l n
+  float* A = pb + max(R, S);                          // the rows
   // scale: largest |T_ij| over the lower triangle (every CTA finds the same)
   double mx = 0.0;
   for (int j = wid; j < n; j += nw) {
@@ -651,134 +792,44 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
   }
   for (int t = tid; t < n; t += blockDim.x) cv[t] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   rows_sync<kCl>();  // every CTA running and initialised before any remote write
-  for (int k = 0; k + 2 < n; ++k) {
-    // (1) row k: pending update, reflector into every CTA
-    const int lk = k / kCl;
-    if (rank == k % kCl && wid == lk % nw) {
-      float* row = A + (size_t)lk * n;
-      const float4 qk = cv[k];
-      float ssq = 0.0f;
-      for (int j = k + lane; j < n; j += 32) {
-        const float4 q = cv[j];
-        const float a = row[j] - sym_upd(qk, q);
-        row[j] = a;
-        if (j >= k + 2) ssq = fmaf(a, a, ssq);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, o);
-      __syncwarp();
-      const float alpha = row[k + 1];
-      float tau = 0.0f, beta = alpha, vscale = 0.0f;
-      if (ssq > 0.0f) {
-        // this step is the serial part of the reduction: a correctly rounded
-        // reciprocal and one fast quotient (2 ulp) keep it short; the FP32
-        // stage is refined in FP64 afterwards
-        const float nrm = sqrtf(fmaf(alpha, alpha, ssq));
-        beta = alpha >= 0.0f ? -nrm : nrm;
-        tau = __fdividef(beta - alpha, beta);
-        vscale = __frcp_rn(alpha - beta);
-      }
-      if (lane == 0) {
-        dv[k] = row[k];
-        ev[k] = beta;
-        tauv[k] = tau;
-#pragma unroll
-        for (int r = 0; r < kCl; ++r) *rows_remote<kCl>(&sh_tau, r) = tau;
-      }
-      for (int j = k + 1 + lane; j < n; j += 32) {
-        const float v = j == k + 1 ? 1.0f : (tau != 0.0f ? row[j] * vscale : 0.0f);
-#pragma unroll
-        for (int r = 0; r < kCl; ++r) rows_remote<kCl>(cv, r)[j].z = v;
-      }
-    }
-    rows_sync<kCl>();
-    // (2) trailing rows: pending update and p_i = tau a_i . v, two rows per pass
-    const float tau = sh_tau;
-    const int l0 = (k + kCl - rank) / kCl;  // first local row with a global index > k
-    float pvw = 0.0f;                       // this warp's sum of p_i v_i
-    for (int l = l0 + ((wid - l0 % nw) + nw) % nw; l < R; l += 2 * nw) {
-      const int i0 = l * kCl + rank, i1 = (l + nw) * kCl + rank;
-      if (i0 >= n) break;
-      const bool two = l + nw < R && i1 < n;
-      float* r0 = A + (size_t)l * n;
-      float* r1 = A + (size_t)(l + nw) * n;
-      const float4 q0 = cv[i0];
-      const float4 q1 = two ? cv[i1] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      float s0 = 0.0f, s1 = 0.0f;
-      if (two) {
-#pragma unroll 2
-        for (int j = k + 1 + lane; j < n; j += 32) {
-          const float4 q = cv[j];
-          const float a0 = r0[j] - sym_upd(q0, q);
-          const float a1 = r1[j] - sym_upd(q1, q);
-          r0[j] = a0;
-          r1[j] = a1;
-          s0 = fmaf(a0, q.z, s0);
-          s1 = fmaf(a1, q.z, s1);
-        }
-      } else {
-#pragma unroll 2
-        for (int j = k + 1 + lane; j < n; j += 32) {
-          const float4 q = cv[j];
-          const float a0 = r0[j] - sym_upd(q0, q);
-          r0[j] = a0;
-          s0 = fmaf(a0, q.z, s0);
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-      }
-      const float p0 = tau * s0, p1 = tau * s1;
-      if (lane == 0) {
-        pb[l] = p0;
-        if (two) pb[l + nw] = p1;
-      }
-      pvw = fmaf(p0, q0.z, pvw);
-      if (two) pvw = fmaf(p1, q1.z, pvw);
-    }
-    if (lane == 0) red[wid] = pvw;
-    __syncthreads();
-    if (wid == 0) {
-      float t = lane < nw ? red[lane] : 0.0f;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane < kCl) rows_remote<kCl>(sh_part, lane)[rank] = t;
-    }
-    rows_sync<kCl>();
-    // (3) K and the next pending pair (v_i, w_i) of the local rows, into every CTA
-    float K = 0.0f;
-#pragma unroll
-    for (int r = 0; r < kCl; ++r) K += sh_part[r];
-    K *= 0.5f * tau;
-    for (int l = l0 + tid; l < R; l += blockDim.x) {
+  const int ks = kCl > 1 ? n - S : n;  // first step of the single-CTA phase
+  int k = 0;
+  for (; k + 2 < n && k < ks; ++k)
+    rows_step<kCl>(k, n, rank, R, 0, A, n, cv, pb, red, sh_part, &sh_tau, V, dv, ev, tauv);
+  int fbase = 0, fld = n;  // layout of the rows for the last 2 x 2 block
+  if constexpr (kCl > 1) {
+    // gather the trailing block (m0 = n - ks rows and columns) into CTA 0
+    const int m0 = n - ks;
+    for (int l = wid; l < R; l += nw) {
       const int i = l * kCl + rank;
       if (i >= n) break;
-      const float v = cv[i].z;
-      const float2 vw = make_float2(v, pb[l] - K * v);
-#pragma unroll
-      for (int r = 0; r < kCl; ++r) *reinterpret_cast<float2*>(&rows_remote<kCl>(cv, r)[i]) = vw;
+      if (i < ks) continue;
+      const float* row = A + (size_t)l * n;
+      for (int j = ks + lane; j < n; j += 32) stage[(size_t)(i - ks) * m0 + (j - ks)] = row[j];
     }
-    // reflector k out to global memory, off the serial step: CTA r writes the
-    // indices i = r (mod kCl) (zero above k + 1, v_{k+1} = 1)
-    for (int i = rank + kCl * (int)tid; i < n; i += kCl * (int)blockDim.x)
-      V[i + (size_t)k * n] = i > k ? cv[i].z : 0.0f;
+    __threadfence();
     rows_sync<kCl>();
+    if (rank != 0) return;  // no remote access follows
+    __threadfence();
+    for (int e = tid; e < m0 * m0; e += blockDim.x) A[e] = stage[e];
+    __syncthreads();
+    for (; k + 2 < n; ++k) rows_step<1>(k, n, 0, m0, ks, A, m0, cv, pb, red, sh_part, &sh_tau, V, dv, ev, tauv);
+    fbase = ks;
+    fld = m0;
   }
-  // the last 2 x 2 block receives the last pending update
+  // the last 2 x 2 block receives the last pending update (one CTA holds it:
+  // CTA 0 after the gather, or the only one)
   if (tid == 0) {
     if (n >= 2) {
       const int a = n - 2, b = n - 1;
       const float4 qa = cv[a], qb = cv[b];
-      if (rank == a % kCl) {
-        const float* ra = A + (size_t)(a / kCl) * n;
-        dv[a] = ra[a] - sym_upd(qa, qa);
-        ev[a] = ra[b] - sym_upd(qa, qb);
-        tauv[a] = 0.0f;
-      }
-      if (rank == b % kCl) dv[b] = A[(size_t)(b / kCl) * n + b] - sym_upd(qb, qb);
-    } else if (rank == 0) {
+      const float* ra = A + (size_t)(a - fbase) * fld - fbase;
+      const float* rb = A + (size_t)(b - fbase) * fld - fbase;
+      dv[a] = ra[a] - sym_upd(qa, qa);
+      ev[a] = ra[b] - sym_upd(qa, qb);
+      tauv[a] = 0.0f;
+      dv[b] = rb[b] - sym_upd(qb, qb);
+    } else {
       dv[0] = A[0];
     }
   }
@@ -1303,13 +1354,13 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(fail, 0, sizeof(int), s));
   if (kc == 1)
-    tri_rows_kernel<1><<<1, kTriRowsThreads, rows_smem_bytes<1>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<1><<<1, kTriRowsThreads, rows_smem_bytes<1>(n), s>>>(n, T, V, dv, ev, tauv, tscale, Y);
   else if (kc == 2)
-    tri_rows_kernel<2><<<2, kTriRowsThreads, rows_smem_bytes<2>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<2><<<2, kTriRowsThreads, rows_smem_bytes<2>(n), s>>>(n, T, V, dv, ev, tauv, tscale, Y);
   else if (kc == 4)
-    tri_rows_kernel<4><<<4, kTriRowsThreads, rows_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<4><<<4, kTriRowsThreads, rows_smem_bytes<4>(n), s>>>(n, T, V, dv, ev, tauv, tscale, Y);
   else if (kc == 8)
-    tri_rows_kernel<8><<<8, kTriRowsThreads, rows_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, tscale);
+    tri_rows_kernel<8><<<8, kTriRowsThreads, rows_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, tscale, Y);
   else if (on_cluster && cl8)
     tri_reduce_cluster_kernel<8><<<8, kTriThreads, cl_smem_bytes<8>(n), s>>>(n, T, V, dv, ev, tauv, part, tscale);
   else if (on_cluster)
