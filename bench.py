@@ -33,6 +33,7 @@ WORKLOADS = {
     "rpca_200x200_r10": (200, 200, 10, 0.05),
 }
 DEFAULT = "rpca_2000x2000_r100"
+WORKLOAD_MN = {k: v[0] * v[1] for k, v in WORKLOADS.items()}
 PRECISIONS = {"fp64": 0, "mixed": 1, "fp64tc": 2}
 MC_WORKLOADS = {
     # name: (m, n, rank, observed fraction)
@@ -58,9 +59,11 @@ LEG_KEY = {"fp64": "fp64_dfma", "mixed": "mixed_precision", "fp64tc": "fp64_tens
 # MMAs (FP64-equivalent mode), 3 TF32 MMAs (mixed mode); 2 flops each
 TENSOR_MMAS = {"fp64tc": 28, "mixed": 3}
 # DRAM bytes (read + write) of one launch of the digit-plane kernel for the
-# 2000 x 2000 product at b = 101, from one ncu capture (filled in below when
-# a capture of the current kernel exists; None otherwise)
-OZ_TRAFFIC = {}
+# 2000 x 2000 product at b = 101 (2 K splits, 128 CTAs), from one ncu capture of
+# the current kernel (bench.py --profile-apply --precision fp64tc)
+OZ_TRAFFIC = {"rpca_2000x2000_r100": 120576256 + 3564544}
+OZ_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one oz_kernel launch of blws_apply "
+                     "(b=101), bench.py --profile-apply --precision fp64tc")
 
 
 def measured_peaks():
@@ -76,17 +79,35 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
 
 
-def roofline(torch, mode, ms, launches, work, clocks, workload, b):
+def steady_state(records):
+    """The products of the largest size among the timed ones (the full block
+    width the solves reach; the small products of the norm estimate and of the
+    first iterations are left out): (count, mean ms, work each)."""
+    if not records:
+        return 0, 0.0, 0.0
+    w0 = max(w for _, w in records)
+    ts = [t for t, w in records if w == w0]
+    return len(ts), float(np.mean(ts)), w0
+
+
+def roofline(torch, mode, ms, launches, work, clocks, workload, b, records=None):
     """Roofline object of the dominant kernel, the product with W~ (step a2),
-    from the device time the library's event timing measured over the timed
-    solves (ms over `launches` products doing `work` multiply-adds)."""
+    from the device times the library's event timing measured around each of
+    them in the timed solves: the full-size products (b = the widest block the
+    solves reach), with the rate over all products (the smaller ones of the
+    first iterations and of the norm estimate included) beside it."""
     if not launches or ms <= 0:
         return None
+    all_tflops = 2.0 * work / (ms / 1e3) / 1e12  # FP64-equivalent rate over every product
+    n_ss, ms_ss, w_ss = steady_state(records)
+    if n_ss:
+        launches, work, ms = n_ss, w_ss * n_ss, ms_ss * n_ss
+        b = int(round(w_ss / (2.0 * WORKLOAD_MN[workload])))
     per = ms / launches / 1e3  # seconds per product
     if mode == "fp64":
         peak, sms, mhz = fp64_peak_gflops(torch, clocks.get("sm_max_mhz"))
         achieved = 2.0 * work / launches / per / 1e9
-        return {"kernel": "gemm_f64 x 2 (P = [W X_v; W^T X_u], b=%d at the end)" % b, "bound": "alu",
+        return {"kernel": "gemm_f64 x 2 (P = [W X_v; W^T X_u], b=%d)" % b, "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "GFLOP/s", "frac": achieved / peak,
                 "traffic": APPLY_TRAFFIC.get(workload) if b == 101 else None,
                 "traffic_source": APPLY_TRAFFIC_SOURCE if b == 101 else None,
@@ -102,12 +123,14 @@ def roofline(torch, mode, ms, launches, work, clocks, workload, b):
     kern = "oz_kernel (digit-plane products, both halves of P in one launch)" if mode == "fp64tc" else \
         "tc_tf32x3_kernel (split-TF32 products, both halves of P in one launch)"
     tr = OZ_TRAFFIC.get(workload) if mode == "fp64tc" and b == 101 else None
-    return {"kernel": kern + ", b=%d at the end" % b, "bound": "tensor", "achieved": achieved, "peak": peak,
+    return {"kernel": kern + ", b=%d" % b, "bound": "tensor", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": tr,
+            "traffic_source": OZ_TRAFFIC_SOURCE if tr else None,
             "launches": launches, "us_per_launch": per * 1e6,
             "algorithmic": "%d x 2 x (2 m n b) %s tensor flops per product (b unpadded)"
                            % (mmas, "bf16" if mode == "fp64tc" else "tf32"),
             "fp64_equivalent_tflops": 2.0 * work / launches / per / 1e12,
+            "all_products_fp64_equivalent_tflops": all_tflops,
             "peak_source": "bf16 sustained %s%s" % (pk["source"], ", x 0.5 for tf32 (nominal ratio)"
                                                      if mode == "mixed" else "")}
 
@@ -797,6 +820,7 @@ def main():
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
     apply_ms, apply_n, apply_work = ctx.timing_stop()
+    apply_recs = ctx.timing_records()
     launches = ctx.launches - launches0
     clocks = sampler.stop()
     total_ms = max_over_ranks(dist, float(np.sum(step_ms)), "cuda")
@@ -817,7 +841,7 @@ def main():
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_val = job_rate(ws, 1, max_over_ranks(dist, float(np.mean(e2e_ms)), "cuda"))
     roof = roofline(torch, args.headline, apply_ms, apply_n, apply_work, clocks, args.workload,
-                    info["rank"] + 1)
+                    info["rank"] + 1, apply_recs)
 
     # ---- the other precision modes, each as a sub-object ----
     legs = {}
@@ -838,6 +862,7 @@ def main():
                 ev1.synchronize()
                 ms2.append(ev0.elapsed_time(ev1))
             a_ms, a_n, a_work = c2.timing_stop()
+            a_recs = c2.timing_records()
             kept[mode] = (A.clone(), E.clone())
             legs[mode] = {
                 "value": job_rate(ws, args.steps, max_over_ranks(dist, float(np.sum(ms2)), "cuda")),
@@ -846,7 +871,8 @@ def main():
                 "dtype": MODE_DTYPE[mode], "iters": i2["iters"], "mixed_iters": i2["mixed_iters"],
                 "residual": i2["residual"],
                 "relerr_vs_planted": float(torch.linalg.norm(A - torch.from_numpy(L0).cuda()) / np.linalg.norm(L0)),
-                "roofline": roofline(torch, mode, a_ms, a_n, a_work, clocks, args.workload, i2["rank"] + 1)}
+                "roofline": roofline(torch, mode, a_ms, a_n, a_work, clocks, args.workload, i2["rank"] + 1,
+                                     a_recs)}
 
     if rank != 0:
         if dist:

@@ -274,6 +274,10 @@ blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double
  * per product; timing is off by default. */
 blws_status blws_timing_start(blws_ctx* ctx);
 blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, double* work);
+/* The per-product records of the last blws_timing_stop, in launch order:
+ * ms[i] (device time) and work[i] (2 m n b) for i < min(cap, count), host
+ * arrays (either may be NULL).  Returns the count. */
+size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work);
 
 /* Self-test of the bounded waits (no counterpart in the paper).  Every wait
  * of the tensor-core kernels (a TMA copy or an MMA that should complete) is

@@ -21,7 +21,8 @@ EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_st
            "blws_svt", "blws_evd", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
            "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
-           "blws_csc_mirror", "blws_gemm", "blws_wait_probe", "blws_timing_start", "blws_timing_stop")
+           "blws_csc_mirror", "blws_gemm", "blws_wait_probe", "blws_timing_start", "blws_timing_stop",
+           "blws_timing_records")
 
 
 class BlwsConfig(ctypes.Structure):
@@ -131,11 +132,13 @@ def load():
     lib.blws_wait_probe.argtypes = [vp, ctypes.c_uint, vp]
     lib.blws_timing_start.argtypes = [vp]
     lib.blws_timing_stop.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(cd)]
+    lib.blws_timing_records.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(cd), ctypes.POINTER(cd)]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
     lib.blws_launch_count.restype = ctypes.c_uint64
     lib.blws_request_bytes.restype = ctypes.c_size_t
+    lib.blws_timing_records.restype = ctypes.c_size_t
     _lib = lib
     return lib
 
@@ -334,6 +337,13 @@ class Context:
         if st != OK:
             self._raise(st, "blws_timing_stop")
         return ms.value, int(n.value), work.value
+
+    def timing_records(self):
+        """Per-product (device ms, multiply-adds) of the last timing_stop."""
+        k = int(load().blws_timing_records(self._h, 0, None, None))
+        ms, w = (ctypes.c_double * max(k, 1))(), (ctypes.c_double * max(k, 1))()
+        load().blws_timing_records(self._h, k, ms, w)
+        return [(ms[i], w[i]) for i in range(k)]
 
     def wait_probe(self, polls=256, stream=None):
         """Run the bounded-wait self-test; returns its status (ETIMEOUT expected)."""

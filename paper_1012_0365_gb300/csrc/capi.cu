@@ -71,11 +71,19 @@ blws_status Ctx::time_begin(cudaStream_t s) {
   if (tused == tcap) {  // grow the event pool (between products, not in a kernel's way)
     const size_t ncap = tcap ? 2 * tcap : 256;
     cudaEvent_t* n = new (std::nothrow) cudaEvent_t[2 * ncap];
-    if (!n) return fail(BLWS_ENOMEM, "timing events");
+    double* w = new (std::nothrow) double[ncap];
+    if (!n || !w) {
+      delete[] n;
+      delete[] w;
+      return fail(BLWS_ENOMEM, "timing events");
+    }
     for (size_t i = 0; i < 2 * tcap; ++i) n[i] = tev[i];
+    for (size_t i = 0; i < tcap; ++i) w[i] = tw[i];
     for (size_t i = 2 * tcap; i < 2 * ncap; ++i) BLWS_TRY_CUDA(this, cudaEventCreate(&n[i]));
     delete[] tev;
+    delete[] tw;
     tev = n;
+    tw = w;
     tcap = ncap;
   }
   BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused], s));
@@ -85,6 +93,7 @@ blws_status Ctx::time_begin(cudaStream_t s) {
 blws_status Ctx::time_end(cudaStream_t s, double work) {
   if (!timing) return BLWS_OK;
   BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused + 1], s));
+  tw[tused] = work;
   ++tused;
   twork += work;
   return BLWS_OK;
@@ -197,6 +206,9 @@ blws_status blws_destroy(blws_ctx* ctx) {
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
   for (size_t i = 0; i < 2 * ctx->tcap; ++i) cudaEventDestroy(ctx->tev[i]);
   delete[] ctx->tev;
+  delete[] ctx->tw;
+  delete[] ctx->trec_ms;
+  delete[] ctx->trec_w;
   delete ctx;
   return BLWS_OK;
 }
@@ -511,18 +523,37 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
   ctx->timing = false;
   BLWS_TRY(bind_device(ctx));
   double total = 0.0;
+  delete[] ctx->trec_ms;
+  delete[] ctx->trec_w;
+  ctx->trec_ms = new (std::nothrow) double[ctx->tused + 1];
+  ctx->trec_w = new (std::nothrow) double[ctx->tused + 1];
+  ctx->trec_n = 0;
+  if (!ctx->trec_ms || !ctx->trec_w) return ctx->fail(BLWS_ENOMEM, "timing records");
   for (size_t i = 0; i < ctx->tused; ++i) {
     BLWS_TRY_CUDA(ctx, cudaEventSynchronize(ctx->tev[2 * i + 1]));
     float t = 0.0f;
     BLWS_TRY_CUDA(ctx, cudaEventElapsedTime(&t, ctx->tev[2 * i], ctx->tev[2 * i + 1]));
     total += t;
+    ctx->trec_ms[i] = t;
+    ctx->trec_w[i] = ctx->tw[i];
   }
+  ctx->trec_n = ctx->tused;
   *ms = total;
   *launches = ctx->tused;
   *work = ctx->twork;
   ctx->tused = 0;
   ctx->twork = 0.0;
   return BLWS_OK;
+}
+
+size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work) {
+  if (!ctx) return 0;
+  const size_t k = std::min(cap, ctx->trec_n);
+  for (size_t i = 0; i < k; ++i) {
+    if (ms) ms[i] = ctx->trec_ms[i];
+    if (work) work[i] = ctx->trec_w[i];
+  }
+  return ctx->trec_n;
 }
 
 blws_status blws_wait_probe(blws_ctx* ctx, unsigned polls, void* stream) {

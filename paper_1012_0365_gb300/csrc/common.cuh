@@ -111,8 +111,12 @@ struct Ctx {
   // kernel(s) of each product, and the work m n b it did
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // 2 * tcap events
+  double* tw = nullptr;         // work of each timed product (tcap)
   size_t tcap = 0, tused = 0;
   double twork = 0.0;
+  double* trec_ms = nullptr;    // per-product times of the last blws_timing_stop
+  double* trec_w = nullptr;
+  size_t trec_n = 0;
   // events around one product's kernels (no-ops unless timing is on)
   blws_status time_begin(cudaStream_t s);
   blws_status time_end(cudaStream_t s, double work);

@@ -217,7 +217,7 @@ __global__ void thresholds(int r, const double* __restrict__ sigma, double eps, 
 
 }  // namespace
 
-blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* out_host) {
+blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* out_host, double stable) {
   // block Lanczos from a seeded block, restarted from its own Ritz vectors
   // (warm start) until the leading Ritz value stops moving
   const int p = std::min(op.m, op.n), N = op.m + op.n;
@@ -247,7 +247,7 @@ blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* 
     BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, sig, sizeof(double), cudaMemcpyDeviceToHost, s));
     BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     cur = ctx->host_pinned[0];
-    if (fabs(cur - prev) <= 1e-14 * fabs(cur)) break;
+    if (fabs(cur - prev) <= stable * fabs(cur)) break;
     prev = cur;
   }
   *out_host = cur;
@@ -306,7 +306,22 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   Dop.W = D;
   Dop.ldw = ld;
   double norm_two = 0.0;
-  BLWS_TRY(spectral_norm(ctx, s, Dop, &norm_two));
+  // ||D||_2 with FP64-equivalent products where the context has them (and in
+  // the mixed mode, whose TF32 products could not resolve it to 1e-13): the
+  // digit planes of D are built once for all its passes
+  const bool norm_oz = ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->cfg.precision == BLWS_PREC_MIXED;
+  OzPlanes Dr{}, Dc{};
+  if (norm_oz) {
+    BLWS_TRY(oz_alloc(ctx, m, n, &Dr, &Dc));
+    BLWS_TRY(oz_planes_from_rows(ctx, s, D, ld, m, n, Dr));
+    BLWS_TRY(oz_planes_from_cols(ctx, s, D, ld, 0, m, n, Dc));
+    Dop.Or = &Dr;
+    Dop.Oc = &Dc;
+    ctx->oz_tail = true;  // the block products of the norm estimate too (reset below)
+  }
+  const blws_status nst = spectral_norm(ctx, s, Dop, &norm_two, norm_oz ? 1e-13 : 1e-14);
+  ctx->oz_tail = false;
+  BLWS_TRY(nst);
   info->norm_two = norm_two;
   const double J = std::max(norm_two, d_inf / lam);
   double mu = p.mu0 > 0 ? p.mu0 : 1.25 / norm_two;
