@@ -80,12 +80,16 @@ def measured_peaks():
 
 
 def steady_state(records):
-    """The products of the largest size among the timed ones (the full block
-    width the solves reach; the small products of the norm estimate and of the
-    first iterations are left out): (count, mean ms, work each)."""
+    """The products of the size that takes the most device time among the
+    timed ones (the steady block width of the solves; the small products of
+    the norm estimate and the wider ones of the first iterations are left
+    out): (count, mean ms, work each)."""
     if not records:
         return 0, 0.0, 0.0
-    w0 = max(w for _, w in records)
+    tot = {}
+    for t, w in records:
+        tot[w] = tot.get(w, 0.0) + t
+    w0 = max(tot, key=lambda w: (tot[w], w))
     ts = [t for t, w in records if w == w0]
     return len(ts), float(np.mean(ts)), w0
 
@@ -93,9 +97,10 @@ def steady_state(records):
 def roofline(torch, mode, ms, launches, work, clocks, workload, b, records=None):
     """Roofline object of the dominant kernel, the product with W~ (step a2),
     from the device times the library's event timing measured around each of
-    them in the timed solves: the full-size products (b = the widest block the
-    solves reach), with the rate over all products (the smaller ones of the
-    first iterations and of the norm estimate included) beside it."""
+    them in the timed solves: the products of the block width that takes the
+    most of the kernel's time (b = 101 on the 2000 x 2000 workload), with the
+    rate over all products (the norm estimate's and the first iterations'
+    included) beside it."""
     if not launches or ms <= 0:
         return None
     all_tflops = 2.0 * work / (ms / 1e3) / 1e12  # FP64-equivalent rate over every product

@@ -167,13 +167,11 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
     put_sym_block<<<ceil_div((long long)b * b, 256), 256, 0, s>>>(b, Mtmp, T, kb, l * b);
     BLWS_CHECK_LAUNCH(ctx);
     if (l == k - 1) break;
-    const double* Ml = T + (size_t)l * b + (size_t)l * b * kb;
-    BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl, N, Ml, kb, 1.0, P, N, f32));
-    if (l > 0) {
-      const double* Bt = T + (size_t)(l - 1) * b + (size_t)l * b * kb;  // B_{l-1}^T block
-      BLWS_TRY(gemm(ctx, s, false, false, N, b, b, -1.0, Xl - (size_t)b * N, N, Bt, kb, 1.0, P, N,
-                    f32));
-    }
+    // R_l = P_l - X_l M_l - X_{l-1} B_{l-1}^T as one product: [X_{l-1} X_l] are
+    // adjacent blocks of Q and [B_{l-1}^T; M_l] adjacent blocks of T's column l
+    const int c0r = l > 0 ? l - 1 : l;
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, (l + 1 - c0r) * b, -1.0, Q + (size_t)c0r * b * N, N,
+                  T + (size_t)c0r * b + (size_t)l * b * kb, kb, 1.0, P, N, f32));
     // second projection against the recurrence's blocks (all blocks when cold)
     const int c0 = a.cold ? 0 : std::max(l - 1, 0);
     const int cols = (l + 1 - c0) * b;

@@ -75,6 +75,16 @@ struct PairTable {
   }
 };
 
+// (hi, lo) += (v.x, v.y) for double-FP32 values: Knuth's TwoSum on the high
+// words, the low words and the rounding error added to lo
+__device__ __forceinline__ void df_add(float& hi, float& lo, float2 v) {
+  const float s = hi + v.x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (v.x - bb);
+  hi = s;
+  lo += err + v.y;
+}
+
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
   // (hi, lo) += v with the rounding error of hi + v kept in lo (Knuth's TwoSum)
   const float s = hi + v;
@@ -276,10 +286,35 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
 // exponent E with max |v| < 2^E (0 for an all-zero vector)
 __device__ __forceinline__ int scale_exp(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
 
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so the splitting and the
+// recombination keep FP64 arithmetic out of their per-element work: maxima
+// are taken on the bit patterns of |v| (for non-negative doubles the integer
+// order is the numeric order), powers of two are built from their bits, and
+// sums of (hi, lo) partials are double-FP32.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// scale_exp of the double whose |bits| are b (the largest magnitude of a row)
+__device__ __forceinline__ int scale_exp_bits(unsigned long long b) {
+  const int be = (int)(b >> 52);
+  if (be > 0) return be - 1022;  // normal: ilogb + 1
+  return b ? scale_exp(__longlong_as_double((long long)b)) : 0;
+}
+
+// 2^e as a double, exactly (normal range), else through ldexp
+__device__ __forceinline__ double pow2(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(1023 + e) << 52) : ldexp(1.0, e);
+}
+
 // balanced base-128 digits of x = v 2^-E (|x| < 1): M = rint(x 2^(7S)),
-// digits from the least significant: d = ((M + 64) mod 128) - 64
+// digits from the least significant: d = ((M + 64) mod 128) - 64.  The
+// scaling by a power of two is exact (one multiply); M is rounded to nearest,
+// ties to even.
 __device__ __forceinline__ void digits(double v, int E, int (&a)[kOzS]) {
-  long long M = llrint(ldexp(v, 7 * kOzS - E));
+  const int sh = 7 * kOzS - E;
+  const double x = (sh >= -1022 && sh <= 1023) ? v * pow2(sh) : ldexp(v, sh);
+  long long M = __double2ll_rn(x);
 #pragma unroll
   for (int t = kOzS - 1; t >= 1; --t) {
     const long long d = ((M + 64) & 127) - 64;
@@ -296,19 +331,19 @@ __device__ __forceinline__ void digits(double v, int E, int (&a)[kOzS]) {
 constexpr int kOzNoExp = -4000;
 
 __global__ void oz_row_scales(int m, int n, const double* __restrict__ A, int lda, int* E) {
-  __shared__ double t[32][33];
+  __shared__ unsigned long long t[32][33];
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   for (int jj = ty; jj < 32; jj += 8) {
     const int i = i0 + tx, j = j0 + jj;
-    t[jj][tx] = (i < m && j < n) ? fabs(A[i + (size_t)j * lda]) : 0.0;
+    t[jj][tx] = (i < m && j < n) ? abs_bits(A[i + (size_t)j * lda]) : 0ull;
   }
   __syncthreads();
   if (ty == 0) {
-    double mx = 0.0;
+    unsigned long long mx = 0ull;
 #pragma unroll 8
-    for (int jj = 0; jj < 32; ++jj) mx = fmax(mx, t[jj][tx]);
-    if (mx > 0.0 && i0 + tx < m) atomicMax(&E[i0 + tx], scale_exp(mx));
+    for (int jj = 0; jj < 32; ++jj) mx = max(mx, t[jj][tx]);
+    if (mx && i0 + tx < m) atomicMax(&E[i0 + tx], scale_exp_bits(mx));
   }
 }
 
@@ -325,23 +360,23 @@ __global__ void oz_fill(int n, int v, int* E) {
 __global__ void __launch_bounds__(256)
 oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __restrict__ A, int lda,
                int row0, int chunks, int* E, __nv_bfloat16* planes) {
-  __shared__ double red[8];
+  __shared__ unsigned long long red[8];
   __shared__ int e_sh;
   const size_t plane = (size_t)plane_rows * ld;
   const int span = (ld + chunks - 1) / chunks;
   for (int item = blockIdx.x; item < rows * chunks; item += gridDim.x) {
     const int r = item / chunks, c = item % chunks;
     const double* col = A + row0 + (size_t)r * lda;
-    double mx = 0.0;
-    for (int k = threadIdx.x; k < inner; k += blockDim.x) mx = fmax(mx, fabs(col[k]));
+    unsigned long long mx = 0ull;
+    for (int k = threadIdx.x; k < inner; k += blockDim.x) mx = max(mx, abs_bits(col[k]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double m2 = 0.0;
-      for (int w = 0; w < (int)blockDim.x / 32; ++w) m2 = fmax(m2, red[w]);
-      e_sh = scale_exp(m2);
+      unsigned long long m2 = 0ull;
+      for (int w = 0; w < (int)blockDim.x / 32; ++w) m2 = max(m2, red[w]);
+      e_sh = scale_exp_bits(m2);
       if (c == 0) E[r] = e_sh;
     }
     __syncthreads();
@@ -405,7 +440,7 @@ __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const fl
   const size_t span = (total * G + nth - 1) / nth * nth;
   for (size_t t = tid; t < span; t += nth) {
     const size_t e = t / G;
-    double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;  // double-FP32 sum of the (hi, lo) partials
     int rr = 0, jj = 0;
     if (e < total) {
       const int r = (int)(e % M), j = (int)(e / M);
@@ -420,17 +455,19 @@ __global__ void oz_reduce(int M, int N, int npad, int splits, int Mpad, const fl
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = src[(size_t)(z + u * G) * zs];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc += (double)v[u].x + (double)v[u].y;
+        for (int u = 0; u < 4; ++u) df_add(hi, lo, v[u]);
       }
-      for (; z < splits; z += G) {
-        const float2 v = src[(size_t)z * zs];
-        acc += (double)v.x + (double)v.y;
-      }
+      for (; z < splits; z += G) df_add(hi, lo, src[(size_t)z * zs]);
     }
-    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+      df_add(hi, lo, make_float2(oh, ol));
+    }
     if (q == 0 && e < total) {
       const int r = (int)(e % M), j = (int)(e / M);
-      const double v = ldexp(acc, ea[rr] + eb[jj]);
+      const int e2 = ea[rr] + eb[jj];
+      const double sum = (double)hi + (double)lo;
+      const double v = (e2 >= -1022 && e2 <= 1023) ? sum * pow2(e2) : ldexp(sum, e2);
       double* c = P + r + (size_t)j * ldp;
       *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
     }
