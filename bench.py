@@ -538,8 +538,12 @@ def run_batch(args):
     probs = [syn.rpca_problem(s["m"], s["n"], s["rank"], s["frac"], seed=s["seed"]) for s in specs]
     Ds = [blws.colmajor(torch.from_numpy(p[0])) for p in probs]
     prec = PRECISIONS[args.precision]
-    srv = blws.Server(workers=args.workers, precision=prec)
-    for t in [srv.submit_rpca(D, tol=args.tol) for D in Ds[:args.workers]]:  # warm the workers up
+    srv = blws.Server(workers=args.workers, precision=prec, grid_sms=args.grid_sms,
+                      graphs=args.graphs, tune=args.tune)
+    # warm-up: the workers' first solves; with the autotuner, every instance once
+    # (each size bucket is timed the first time it is met, outside the timed region)
+    warm = Ds if args.tune else Ds[:args.workers]
+    for t in [srv.submit_rpca(D, tol=args.tol) for D in warm]:
         srv.wait(t)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -552,7 +556,7 @@ def run_batch(args):
            for (A, _, _), p in zip(outs, probs)]
     ok = sum(1 for _, _, i in outs if i["status"] == 0)
     # one at a time, one context, on a sample of the same instances
-    ctx = blws.Context(k=args.k, precision=prec)
+    ctx = blws.Context(k=args.k, precision=prec, graphs=args.graphs, tune=args.tune)
     sample = min(len(Ds), 32)
     for D in Ds[:2]:
         ctx.rpca_solve(D, tol=args.tol)
@@ -567,6 +571,8 @@ def run_batch(args):
             "n_gpus": 1, "higher_is_better": True, "dtype": ["f64", "mixed", "f64 (tensor-core digits)"][prec],
             "data": "synthetic",
             "config": {"workload": "rpca_batch_%d_uneven_100_1000" % len(Ds), "workers": args.workers,
+                       "grid_sms": args.grid_sms, "graphs": args.graphs, "tune": args.tune,
+                       "tuned_buckets": blws.Context.tune_count(),
                        "tol": args.tol, "k": args.k},
             "wall_s": wall, "solved_ok": ok, "relerr_vs_planted": {"median": float(np.median(rel)),
                                                                    "max": float(np.max(rel))},
@@ -735,6 +741,12 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 1.0, 1.5])
     ap.add_argument("--workers", type=int, default=16)
+    ap.add_argument("--grid-sms", type=int, default=0,
+                    help="SMs each worker context sizes its grids for (0: all)")
+    ap.add_argument("--graphs", type=int, default=1, choices=(0, 1),
+                    help="replay CUDA graphs of the outer-iteration phases (1, default) or launch directly")
+    ap.add_argument("--tune", type=int, default=1, choices=(0, 1),
+                    help="batch leg: product tiles from the timed autotuner (1, default) or the fixed rule")
     args = ap.parse_args()
     ws, rank = dist_env()
 

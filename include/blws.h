@@ -87,6 +87,29 @@ typedef struct {
                      blocks from a seeded Gaussian block, full
                      reorthogonalisation), the random-start block Lanczos the
                      paper compares against.  Variants for ablations. */
+  int grid_sms;   /* SMs the context sizes its grids and K splits for: 0
+                     (default) all of the device's SMs.  A smaller share lets
+                     solves on concurrent streams run side by side instead of
+                     each filling the GPU in turn (the server's workers). */
+  int graphs;     /* 1 (default): rpca_solve captures the two phases of an
+                     outer iteration (the block steps up to the eigen-solver's
+                     device stage; the Ritz lift and fused epilogue) in CUDA
+                     graphs and replays them with one launch each while their
+                     launches repeat (once the predicted rank settles); 0:
+                     every kernel is launched directly.  The same kernels run
+                     with the same arguments either way: results are
+                     bit-identical.  The environment variable BLWS_GRAPH=0 at
+                     context creation turns it off. */
+  int tune;       /* 0 (default): FP64 / FP32 CUDA-core products take their
+                     tile shape and K split from a fixed rule (least padding,
+                     about 8 CTAs per SM).  1: from a timed autotuner -- the
+                     first product of each size bucket (every dimension rounded
+                     up to a quarter octave) times every (tile, split) pair
+                     and keeps the fastest unless the rule is within 5%.
+                     Choices are process-wide; with the environment variable
+                     BLWS_TUNE_FILE set they are read from and appended to
+                     that file.  Products differ from the rule's in rounding
+                     only (the split-K sums are grouped differently). */
 } blws_config;
 
 /* Fill *cfg with the defaults above.  Never fails for a non-NULL cfg. */
@@ -99,6 +122,16 @@ blws_status blws_destroy(blws_ctx* ctx);
 
 /* Number of kernels this context has launched so far (host counter, exact). */
 uint64_t blws_launch_count(const blws_ctx* ctx);
+
+/* CUDA graphs of this context so far (blws_config.graphs): phases captured
+ * and phase replays (each replay launched the captured kernels with one graph
+ * launch; blws_launch_count counts those kernels too).  Either pointer may be
+ * NULL.  Never fails for a non-NULL ctx. */
+blws_status blws_graph_stats(const blws_ctx* ctx, uint64_t* captures, uint64_t* replays);
+
+/* Size buckets the product autotuner (blws_config.tune) holds in this
+ * process, read from BLWS_TUNE_FILE or measured.  Never fails. */
+size_t blws_tune_count(void);
 
 /* Text of a status code (static string). */
 const char* blws_status_str(blws_status s);

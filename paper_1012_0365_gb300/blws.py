@@ -17,7 +17,7 @@ PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 
 # every symbol include/blws.h declares
 EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_str",
-           "blws_last_error", "blws_launch_count", "blws_apply", "blws_apply_noalloc",
+           "blws_last_error", "blws_launch_count", "blws_graph_stats", "blws_tune_count", "blws_apply", "blws_apply_noalloc",
            "blws_svt", "blws_evd", "rpca_params_default", "rpca_solve", "mc_params_default", "mc_solve",
            "blws_server_config_default", "blws_server_create", "blws_request_bytes",
            "blws_server_submit", "blws_server_wait", "blws_server_stats_get", "blws_server_destroy",
@@ -28,7 +28,8 @@ EXPORTS = ("blws_config_default", "blws_create", "blws_destroy", "blws_status_st
 class BlwsConfig(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("k_cold", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("device", ctypes.c_int), ("start", ctypes.c_int),
-                ("warm", ctypes.c_int)]
+                ("warm", ctypes.c_int), ("grid_sms", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("tune", ctypes.c_int)]
 
 
 class BlwsOp(ctypes.Structure):
@@ -120,6 +121,8 @@ def load():
     lib.mc_solve.argtypes = [vp, ci, ci, ci, vp, vp, vp, ctypes.POINTER(McParams), ci, vp, vp, vp,
                              ctypes.POINTER(McInfo), vp]
     lib.blws_launch_count.argtypes = [vp]
+    lib.blws_graph_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
+    lib.blws_graph_stats.restype = ctypes.c_int
     lib.blws_server_config_default.argtypes = [ctypes.POINTER(ServerConfig)]
     lib.blws_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ServerConfig)]
     lib.blws_request_bytes.argtypes = [ctypes.POINTER(Request), ci]
@@ -137,6 +140,8 @@ def load():
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
     lib.blws_launch_count.restype = ctypes.c_uint64
+    lib.blws_tune_count.argtypes = []
+    lib.blws_tune_count.restype = ctypes.c_size_t
     lib.blws_request_bytes.restype = ctypes.c_size_t
     lib.blws_timing_records.restype = ctypes.c_size_t
     _lib = lib
@@ -200,12 +205,14 @@ def apply_noalloc(W, X, P, stream=None):
 class Context:
     """Owns a blws_ctx (workspace, generator state) bound to one device."""
 
-    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0, start=0, warm=1):
+    def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0, start=0, warm=1,
+                 grid_sms=0, graphs=1, tune=0):
         lib = load()
         cfg = BlwsConfig()
         lib.blws_config_default(ctypes.byref(cfg))
         cfg.k, cfg.k_cold, cfg.seed, cfg.device = k, k_cold, seed, device
-        cfg.precision, cfg.start, cfg.warm = precision, start, warm
+        cfg.precision, cfg.start, cfg.warm, cfg.grid_sms = precision, start, warm, grid_sms
+        cfg.graphs, cfg.tune = graphs, tune
         h = ctypes.c_void_p()
         st = lib.blws_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:
@@ -228,6 +235,19 @@ class Context:
     def launches(self):
         """Kernels launched through this context so far."""
         return int(load().blws_launch_count(self._h))
+
+    @staticmethod
+    def tune_count():
+        """Size buckets the product autotuner holds in this process."""
+        return int(load().blws_tune_count())
+
+    def graph_stats(self):
+        """(phases captured, phase replays) of this context's CUDA graphs."""
+        c, r = ctypes.c_uint64(), ctypes.c_uint64()
+        st = load().blws_graph_stats(self._h, ctypes.byref(c), ctypes.byref(r))
+        if st != OK:
+            raise BlwsError(st, "blws_graph_stats")
+        return int(c.value), int(r.value)
 
     def _raise(self, st, what):
         raise BlwsError(st, "%s: %s" % (what, load().blws_last_error(self._h).decode()))
@@ -445,12 +465,14 @@ class Server:
     (0: 70% of the free memory).  Tensors handed to submit_* are kept alive
     here until wait() returns their result."""
 
-    def __init__(self, workers=8, hbm_budget=0, k=3, k_cold=4, seed=0x5EED, device=0, precision=0):
+    def __init__(self, workers=8, hbm_budget=0, k=3, k_cold=4, seed=0x5EED, device=0, precision=0,
+                 grid_sms=0, graphs=1, tune=0):
         lib = load()
         cfg = ServerConfig()
         lib.blws_server_config_default(ctypes.byref(cfg))
         cfg.workers, cfg.hbm_budget = workers, hbm_budget
         cfg.cfg.k, cfg.cfg.k_cold, cfg.cfg.seed, cfg.cfg.device, cfg.cfg.precision = k, k_cold, seed, device, precision
+        cfg.cfg.grid_sms, cfg.cfg.graphs, cfg.cfg.tune = grid_sms, graphs, tune
         h = ctypes.c_void_p()
         st = lib.blws_server_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:

@@ -70,10 +70,12 @@ __global__ void put_offdiag_block(int b, const double* __restrict__ B, double* T
   }
 }
 
-// sigma[0:r] = lam[0:r]; count = #{sigma_t > eps}
-__global__ void ritz_values(int r, const double* __restrict__ lam, double eps, double* sigma,
-                            int* count) {
+// sigma[0:r] = lam[0:r]; count = #{sigma_t > eps}; eps from device memory
+// when eps_dev is set (a replayed graph's per-iteration threshold)
+__global__ void ritz_values(int r, const double* __restrict__ lam, double eps,
+                            const double* __restrict__ eps_dev, double* sigma, int* count) {
   __shared__ int cnt;
+  if (eps_dev) eps = *eps_dev;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   int c = 0;
@@ -124,8 +126,7 @@ blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax) {
   return BLWS_OK;
 }
 
-blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a,
-                     double* U, int ldu, double* V, int ldv, double* sigma, int* count_dev) {
+blws_status blws_run_a(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a) {
   const int m = op.m, n = op.sym ? 0 : op.n, N = m + n;
   const int w = a.w, g = a.G ? a.g : 0;
   const int b = std::max(a.r, w + g);
@@ -183,7 +184,43 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
                                                                        l * b);
     BLWS_CHECK_LAUNCH(ctx);
   }
-  BLWS_TRY(sym_eig(ctx, s, kb, T, lam, Z, a.eps));
+  return sym_eig_start(ctx, s, kb, T, lam, Z);
+}
+
+namespace {
+struct RunDims {
+  int b, kb;
+  double *Q, *T, *Z, *lam;
+};
+blws_status run_dims(Ctx* ctx, const Operator& op, const BlwsArgs& a, RunDims* d) {
+  const int N = op.m + (op.sym ? 0 : op.n);
+  d->b = std::max(a.r, a.w + (a.G ? a.g : 0));
+  d->kb = a.k * d->b;
+  BLWS_TRY(ctx->get(BUF_Q, (size_t)N * d->kb, &d->Q));
+  BLWS_TRY(ctx->get(BUF_T, (size_t)3 * d->kb * d->kb + 2 * d->kb + (size_t)d->b * d->b * 2 + 64, &d->T));
+  d->Z = d->T + (size_t)d->kb * d->kb;
+  d->lam = d->Z + (size_t)d->kb * d->kb;
+  return BLWS_OK;
+}
+}  // namespace
+
+blws_status blws_run_mid(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a) {
+  RunDims d;
+  BLWS_TRY(run_dims(ctx, op, a, &d));
+  return sym_eig_finish(ctx, s, d.kb, d.T, d.lam, d.Z, a.eps);
+}
+
+blws_status blws_run_b(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a, double* U,
+                       int ldu, double* V, int ldv, double* sigma, int* count_dev,
+                       const double* eps_dev) {
+  const int m = op.m, n = op.sym ? 0 : op.n, N = m + n;
+  RunDims d;
+  BLWS_TRY(run_dims(ctx, op, a, &d));
+  const int kb = d.kb;
+  double* Q = d.Q;
+  double* Z = d.Z;
+  double* lam = d.lam;
+  const bool f32 = a.mixed;
   if (op.sym) {
     BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, 1.0, Q, N, Z, kb, 0.0, U, ldu, f32));
   } else {
@@ -191,9 +228,17 @@ blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArg
     BLWS_TRY(gemm(ctx, s, false, false, m, a.r, kb, r2, Q, N, Z, kb, 0.0, U, ldu, f32));
     BLWS_TRY(gemm(ctx, s, false, false, n, a.r, kb, r2, Q + m, N, Z, kb, 0.0, V, ldv, f32));
   }
-  ritz_values<<<1, 256, 0, s>>>(a.r, lam, a.eps, sigma, count_dev);
+  ritz_values<<<1, 256, 0, s>>>(a.r, lam, a.eps, eps_dev, sigma, count_dev);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
+}
+
+blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a,
+                     double* U, int ldu, double* V, int ldv, double* sigma, int* count_dev) {
+  BLWS_TRY(blws_run_a(ctx, s, op, a));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  BLWS_TRY(blws_run_mid(ctx, s, op, a));
+  return blws_run_b(ctx, s, op, a, U, ldu, V, ldv, sigma, count_dev, nullptr);
 }
 
 }  // namespace blws

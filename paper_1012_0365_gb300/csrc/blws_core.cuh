@@ -68,5 +68,16 @@ blws_status blws_reserve(Ctx* ctx, int m, int n, int bmax, int kmax);
 // Ritz vectors of W itself, sigma its r largest Ritz values, V is not written.
 blws_status blws_run(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a, double* U,
                      int ldu, double* V, int ldv, double* sigma, int* count_dev);
+// blws_run in three stages around its one synchronisation: (a) the start
+// block, the k block steps and the device stage of the EVD of T_k; then, with
+// s synchronised, (mid) the EVD's host stage; then (b) the Ritz lift and the
+// count.  Stages a and b never wait on the host, so each can be captured in a
+// CUDA graph; eps_dev (nullable) supplies the threshold of the count from
+// device memory instead of a.eps.
+blws_status blws_run_a(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a);
+blws_status blws_run_mid(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a);
+blws_status blws_run_b(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsArgs& a, double* U,
+                       int ldu, double* V, int ldv, double* sigma, int* count_dev,
+                       const double* eps_dev);
 
 }  // namespace blws

@@ -9,6 +9,7 @@
 #include <new>
 
 #include "mc_kernels.cuh"
+#include "graph.cuh"
 #include "solver.cuh"
 
 namespace blws {
@@ -41,6 +42,11 @@ blws_status Ctx::smem_limit(SmemAttr which, const void* func, int bytes) {
 blws_status Ctx::get(Buf b, size_t bytes, void** out) {
   if (bytes == 0) bytes = 256;
   if (bytes > cap[b]) {
+    if (capturing) {  // growth would synchronise: the phase runs directly instead
+      capture_broken = true;
+      return fail(BLWS_ECUDA, "workspace buffer %d must grow inside a graph capture", (int)b);
+    }
+    ++gen;
     if (buf[b]) {
       // growth happens between solver phases; make sure nothing still uses it
       if (sole_stream)
@@ -68,6 +74,14 @@ blws_status Ctx::get(Buf b, size_t bytes, void** out) {
 
 blws_status Ctx::time_begin(cudaStream_t s) {
   if (!timing) return BLWS_OK;
+  if (capturing) {  // events of the graph: recorded by every replay, read after it
+    TimedPair t{nullptr, nullptr, 0.0};
+    BLWS_TRY_CUDA(this, cudaEventCreate(&t.e0));
+    BLWS_TRY_CUDA(this, cudaEventCreate(&t.e1));
+    cap_ev.push_back(t);
+    BLWS_TRY_CUDA(this, cudaEventRecordWithFlags(t.e0, s, cudaEventRecordExternal));
+    return BLWS_OK;
+  }
   if (tused == tcap) {  // grow the event pool (between products, not in a kernel's way)
     const size_t ncap = tcap ? 2 * tcap : 256;
     cudaEvent_t* n = new (std::nothrow) cudaEvent_t[2 * ncap];
@@ -92,6 +106,11 @@ blws_status Ctx::time_begin(cudaStream_t s) {
 
 blws_status Ctx::time_end(cudaStream_t s, double work) {
   if (!timing) return BLWS_OK;
+  if (capturing) {
+    cap_ev.back().work = work;
+    BLWS_TRY_CUDA(this, cudaEventRecordWithFlags(cap_ev.back().e1, s, cudaEventRecordExternal));
+    return BLWS_OK;
+  }
   BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused + 1], s));
   tw[tused] = work;
   ++tused;
@@ -104,6 +123,8 @@ blws_status Ctx::trim() {
     BLWS_TRY_CUDA(this, cudaStreamSynchronize(sole_stream));
   else
     BLWS_TRY_CUDA(this, cudaDeviceSynchronize());
+  free_graphs();
+  ++gen;
   for (int b = 0; b < BUF_COUNT_; ++b) {
     if (b == BUF_SCAL || !buf[b]) continue;
     BLWS_TRY_CUDA(this, cudaFree(buf[b]));
@@ -154,6 +175,9 @@ blws_status blws_config_default(blws_config* cfg) {
   cfg->device = 0;
   cfg->start = 0;
   cfg->warm = 1;
+  cfg->grid_sms = 0;
+  cfg->graphs = 1;
+  cfg->tune = 0;
   return BLWS_OK;
 }
 
@@ -165,7 +189,8 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   if (cfg) c = *cfg;
   if (c.k < 1 || c.k_cold < 1 ||
       (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED && c.precision != BLWS_PREC_FP64_TC) ||
-      (c.start != 0 && c.start != 1) || (c.warm != 0 && c.warm != 1))
+      (c.start != 0 && c.start != 1) || (c.warm != 0 && c.warm != 1) || c.grid_sms < 0 ||
+      (c.graphs != 0 && c.graphs != 1) || (c.tune != 0 && c.tune != 1))
     return BLWS_EINVAL;
   blws_ctx* ctx = new (std::nothrow) blws_ctx();
   if (!ctx) return BLWS_ENOMEM;
@@ -173,12 +198,14 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   ctx->device = c.device;
   if (const char* ev = std::getenv("BLWS_EIG")) ctx->eig_route = std::strcmp(ev, "jacobi") == 0 ? 1 : 0;
   if (const char* ev = std::getenv("BLWS_TRI")) ctx->tri_route = std::strcmp(ev, "packed") == 0 ? 1 : 0;
+  ctx->graphs_on = c.graphs == 1;
+  if (const char* ev = std::getenv("BLWS_GRAPH")) ctx->graphs_on = ctx->graphs_on && std::strcmp(ev, "0") != 0;
   blws_status st = bind_device(ctx);
   cudaDeviceProp prop;
   if (st == BLWS_OK && cudaGetDeviceProperties(&prop, ctx->device) != cudaSuccess) st = BLWS_ECUDA;
   if (st == BLWS_OK && prop.major < 10) st = BLWS_ENOTSUP;
   if (st == BLWS_OK) {
-    ctx->sms = prop.multiProcessorCount;
+    ctx->sms = c.grid_sms > 0 ? std::min(c.grid_sms, prop.multiProcessorCount) : prop.multiProcessorCount;
     ctx->smem_optin = prop.sharedMemPerBlockOptin;
     if (cudaMallocHost(&ctx->host_pinned, 64 * sizeof(double)) != cudaSuccess) st = BLWS_ENOMEM;
   }
@@ -201,9 +228,15 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
 blws_status blws_destroy(blws_ctx* ctx) {
   if (!ctx) return BLWS_OK;
   cudaSetDevice(ctx->device);
+  if (ctx->gstream) cudaStreamSynchronize(ctx->gstream);
+  ctx->free_graphs();
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->gfork) cudaEventDestroy(ctx->gfork);
+  if (ctx->gjoin) cudaEventDestroy(ctx->gjoin);
   for (int b = 0; b < blws::BUF_COUNT_; ++b)
     if (ctx->buf[b]) cudaFree(ctx->buf[b]);
   if (ctx->host_pinned) cudaFreeHost(ctx->host_pinned);
+  if (ctx->host_eig) cudaFreeHost(ctx->host_eig);
   for (size_t i = 0; i < 2 * ctx->tcap; ++i) cudaEventDestroy(ctx->tev[i]);
   delete[] ctx->tev;
   delete[] ctx->tw;
@@ -230,6 +263,13 @@ const char* blws_status_str(blws_status s) {
 const char* blws_last_error(const blws_ctx* ctx) { return ctx ? ctx->last_error : ""; }
 
 uint64_t blws_launch_count(const blws_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+blws_status blws_graph_stats(const blws_ctx* ctx, uint64_t* captures, uint64_t* replays) {
+  if (!ctx) return BLWS_EINVAL;
+  if (captures) *captures = ctx->graph_captures;
+  if (replays) *replays = ctx->graph_replays;
+  return BLWS_OK;
+}
 
 static blws_status make_operator(blws_ctx* ctx, const blws_op* W, cudaStream_t s,
                                  blws::Operator* op) {
@@ -515,6 +555,9 @@ blws_status blws_timing_start(blws_ctx* ctx) {
   ctx->timing = true;
   ctx->tused = 0;
   ctx->twork = 0.0;
+  ctx->pending_ev.clear();
+  ctx->graph_ms.clear();
+  ctx->graph_w.clear();
   return BLWS_OK;
 }
 
@@ -522,11 +565,13 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
   if (!ctx || !ms || !launches || !work) return BLWS_EINVAL;
   ctx->timing = false;
   BLWS_TRY(bind_device(ctx));
+  BLWS_TRY(blws::graph_harvest(ctx));  // products timed inside replayed graphs
+  const size_t ng = ctx->graph_ms.size();
   double total = 0.0;
   delete[] ctx->trec_ms;
   delete[] ctx->trec_w;
-  ctx->trec_ms = new (std::nothrow) double[ctx->tused + 1];
-  ctx->trec_w = new (std::nothrow) double[ctx->tused + 1];
+  ctx->trec_ms = new (std::nothrow) double[ctx->tused + ng + 1];
+  ctx->trec_w = new (std::nothrow) double[ctx->tused + ng + 1];
   ctx->trec_n = 0;
   if (!ctx->trec_ms || !ctx->trec_w) return ctx->fail(BLWS_ENOMEM, "timing records");
   for (size_t i = 0; i < ctx->tused; ++i) {
@@ -537,12 +582,21 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
     ctx->trec_ms[i] = t;
     ctx->trec_w[i] = ctx->tw[i];
   }
-  ctx->trec_n = ctx->tused;
+  double gwork = 0.0;
+  for (size_t i = 0; i < ng; ++i) {
+    total += ctx->graph_ms[i];
+    gwork += ctx->graph_w[i];
+    ctx->trec_ms[ctx->tused + i] = ctx->graph_ms[i];
+    ctx->trec_w[ctx->tused + i] = ctx->graph_w[i];
+  }
+  ctx->trec_n = ctx->tused + ng;
   *ms = total;
-  *launches = ctx->tused;
-  *work = ctx->twork;
+  *launches = ctx->tused + ng;
+  *work = ctx->twork + gwork;
   ctx->tused = 0;
   ctx->twork = 0.0;
+  ctx->graph_ms.clear();
+  ctx->graph_w.clear();
   return BLWS_OK;
 }
 

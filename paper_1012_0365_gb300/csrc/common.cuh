@@ -7,6 +7,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/blws.h"
 
 namespace blws {
@@ -72,7 +74,22 @@ enum Buf {
   BUF_OZ_G,      // FP64-equivalent general products: digit planes of both operands
   BUF_RPCA_A,    // RPCA, FP64-equivalent and mixed modes: A = U diag(theta) V^T as a product (m x n)
   BUF_TC_G,      // mixed precision: TF32 planes of both operands of a general product
+  BUF_TUNE,      // GEMM autotuner: scratch operands of the shape being timed
   BUF_COUNT_
+};
+
+// A CUDA graph of one solver phase, replayed while the phase's launches are
+// unchanged (the key lists everything the launches depend on).
+struct TimedPair {
+  cudaEvent_t e0, e1;
+  double work;
+};
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long nlaunch = 0;   // kernels in the graph
+  std::vector<TimedPair> ev;        // timed products inside it (timing on)
+  unsigned long long last_use = 0;
 };
 
 struct Ctx {
@@ -126,6 +143,31 @@ struct Ctx {
   // tridiagonal reduction: 0 by rows on a cluster where it fits, 1 the packed
   // kernels (environment BLWS_TRI=packed at context creation)
   int tri_route = 0;
+  // ---- CUDA graphs of the outer-iteration phases (graph.cu) ----
+  // replay on (blws_config.graphs, environment BLWS_GRAPH=0 turns it off)
+  bool graphs_on = false;
+  // a phase is being captured: workspace growth is refused (it would have to
+  // synchronise) and breaks the capture, which then runs directly
+  bool capturing = false;
+  bool capture_broken = false;
+  // bumped whenever a workspace buffer moves: keys hold it, so a graph never
+  // outlives the addresses it was captured with
+  unsigned long long gen = 0;
+  unsigned long long graph_clock = 0;
+  unsigned long long graph_replays = 0, graph_captures = 0;
+  std::vector<GraphEntry> graphs;
+  std::vector<std::vector<uint64_t>> seen;  // keys met once (captured on the second meeting)
+  cudaStream_t gstream = nullptr;          // stream the graphs run on
+  cudaEvent_t gfork = nullptr, gjoin = nullptr;
+  std::vector<TimedPair> cap_ev;           // timed products of the capture in progress
+  std::vector<TimedPair> pending_ev;       // timed products of replays not yet read
+  std::vector<double> graph_ms, graph_w;   // their times and work, once read
+  // pinned host copies of the eigen-solver's results for its host stage
+  // (eigenvalues, group ids and tops, refinement width, failure flag)
+  void* host_eig = nullptr;
+  size_t host_eig_cap = 0;
+  blws_status host_eig_get(size_t bytes);
+  void free_graphs();
   unsigned long long tri_fallbacks = 0;  // tridiagonal stage results replaced by Jacobi
   // device bytes the workspace holds now
   size_t held_bytes() const {
@@ -154,6 +196,9 @@ enum Slot {
   SLOT_AUX2 = 7,
   SLOT_TCERR = 8,      // int: a tensor-core kernel's bounded wait ran out
   SLOT_TRIFAIL = 9,    // int: the tridiagonal route met a group it cannot orthonormalise
+  SLOT_EPS = 10,       // per-iteration scalars read by the kernels of a replayed
+  SLOT_MU = 11,        //   graph: threshold eps = 1 / mu, mu, and the next mu
+  SLOT_MU_NEXT = 12,
   SLOT_MAX = 16
 };
 

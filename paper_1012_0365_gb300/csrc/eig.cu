@@ -668,41 +668,70 @@ __global__ void gather_cols(int rows, int cols, const double* __restrict__ In,
 
 }  // namespace
 
-blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
-                    double eps) {
+// layout of the pinned host copies: eigenvalues (n), group ids and tops (2n
+// ints), then the refinement width and the failure flag
+size_t eig_host_bytes(int n) { return sizeof(double) * n + sizeof(int) * 2 * (size_t)n + 2 * sizeof(double); }
+
+blws_status eig_copy_back(Ctx* ctx, cudaStream_t s, int n, const double* lam, const int* dgrp,
+                          const double* scal) {
+  char* h = static_cast<char*>(ctx->host_eig);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h, lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + sizeof(double) * n, dgrp, sizeof(int) * 2 * n,
+                                     cudaMemcpyDeviceToHost, s));
+  double* tail = reinterpret_cast<double*>(h + sizeof(double) * n + sizeof(int) * 2 * (size_t)n);
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(tail, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(tail + 1, scal + SLOT_TRIFAIL, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return BLWS_OK;
+}
+
+blws_status sym_eig_start(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z) {
   if (n <= 0) return BLWS_OK;
   double* scal;
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
   const bool tri_enabled = ctx->eig_route != 1;
   int* dgrp = nullptr;  // sorted group ids and group tops of the tridiagonal stage (n ints, n floats)
   BLWS_TRY(ctx->get(BUF_EIG_GRP, (size_t)2 * n, &dgrp));
+  BLWS_TRY(ctx->host_eig_get(eig_host_bytes(n)));
   BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2, true,
                          tri_enabled ? reinterpret_cast<int*>(scal + SLOT_TRIFAIL) : nullptr, dgrp));
+  return eig_copy_back(ctx, s, n, lam, dgrp, scal);
+}
+
+blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                    double eps) {
+  if (n <= 0) return BLWS_OK;
+  BLWS_TRY(sym_eig_start(ctx, s, n, T, lam, Z));
+  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+  return sym_eig_finish(ctx, s, n, T, lam, Z, eps);
+}
+
+blws_status sym_eig_finish(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                           double eps) {
+  if (n <= 0) return BLWS_OK;
+  double* scal;
+  BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
+  const bool tri_enabled = ctx->eig_route != 1;
+  int* dgrp = nullptr;
+  BLWS_TRY(ctx->get(BUF_EIG_GRP, (size_t)2 * n, &dgrp));
   // Second level for clusters: eigenvalues closer than the refinement width d
   // are only resolved as a joint subspace, with values accurate to ~d (the
   // FP32 stage's absolute accuracy, ~1e-7 ||T||).  Where that could change
   // the count above eps or a threshold sigma - eps, the cluster is solved
   // again on its own: K = (X_C^T T X_C - mu I) / scale has O(1) entries, so
   // the same two-stage solver resolves it to ~1e-7 of the cluster's width.
-  double* h = ctx->host_pinned;
-  std::vector<double> hl(n);
-  std::vector<int> hg(2 * (size_t)n);
-  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hg.data(), dgrp, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
-  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 32, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 33, scal + SLOT_TRIFAIL, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-  if (tri_enabled && (*reinterpret_cast<const int*>(h + 33) != 0 || !std::isfinite(h[32]))) {
+  char* hb = static_cast<char*>(ctx->host_eig);
+  const double* hl = reinterpret_cast<const double*>(hb);
+  const int* hg = reinterpret_cast<const int*>(hb + sizeof(double) * n);
+  const double* htail = reinterpret_cast<const double*>(hb + sizeof(double) * n + sizeof(int) * 2 * (size_t)n);
+  if (tri_enabled && (*reinterpret_cast<const int*>(htail + 1) != 0 || !std::isfinite(htail[0]))) {
     // the FP32 tridiagonal stage met a group it could not orthonormalise or a
     // solve it could not normalise: Jacobi instead
     ++ctx->tri_fallbacks;
     BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2, true, nullptr, dgrp));
-    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hl.data(), lam, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
-    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(hg.data(), dgrp, sizeof(int) * 2 * n, cudaMemcpyDeviceToHost, s));
-    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(h + 32, scal + SLOT_AUX2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    BLWS_TRY(eig_copy_back(ctx, s, n, lam, dgrp, scal));
     BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
   }
-  const double d = h[32];
+  const double d = htail[0];
   if (!(d > 0.0)) return BLWS_OK;
   // Clusters: runs of sorted values closer than d, joined with the groups of
   // the tridiagonal stage (whose columns are a basis of the group's
@@ -712,7 +741,7 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
   // by 1e-5 ||T|| (the FP32 stage's accuracy with room to spare), bounds it.
   // A cluster is solved again when it can reach above eps - 3d.
   const double tnorm = std::max(std::fabs(hl[0]), std::fabs(hl[n - 1]));
-  const float* htop = reinterpret_cast<const float*>(hg.data() + n);
+  const float* htop = reinterpret_cast<const float*>(hg + n);
   struct Cl { int i, j; double mu, scale; };
   std::vector<Cl> cl;
   int n2 = 0;

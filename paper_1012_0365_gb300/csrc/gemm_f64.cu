@@ -6,7 +6,13 @@
 // per 256-thread CTA; when the tile count cannot fill the GPU the K range is
 // split and the partial sums are reduced in a fixed order (deterministic, no
 // atomics).
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
 #include <mutex>
 
 #include "ops.cuh"
@@ -148,16 +154,13 @@ __global__ void splitk_reduce(int M, int N, int splits, int G, double alpha, con
 // in FP64 by the split-K reduction)
 constexpr int kF32MaxChunk = 256;
 
+// target: CTAs the K split aims for (0: no split beyond the FP32 chunk rule)
 template <typename CT, bool TA, bool TB, int BM, int BN>
 blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha,
                          const double* A, int lda, const double* B, int ldb, double beta,
-                         double* C, int ldc, bool sym) {
+                         double* C, int ldc, bool sym, int target) {
   const int tm = ceil_div(M, BM), tn = ceil_div(N, BN);
   const int tiles = tm * tn;
-  // DFMA-bound: balance the SMs.  About 8 CTAs per SM (of which ~4 are
-  // resident at once) keeps the tail of the last wave under ~1/8 of the run;
-  // the inner dimension is split (chunks >= 32) until that many CTAs exist.
-  const int target = 8 * ctx->sms;
   int splits = 1;
   if (tiles < target && K > 2 * kBK) {
     splits = ceil_div(target, tiles);
@@ -185,14 +188,13 @@ blws_status launch_tiles(Ctx* ctx, cudaStream_t s, int M, int N, int K, double a
   return BLWS_OK;
 }
 
+constexpr int kShapes[5][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}, {32, 8}};
+
 // The tile shape that wastes the fewest FMAs on padding (the DFMA pipe, not
 // shared-memory traffic, bounds every shape here); ties go to the earlier,
 // larger tile.  32 x 8 serves block widths just above a multiple of 16
 // (b = 101 pads to 104 instead of 112).
-template <typename CT, bool TA, bool TB>
-blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
-                   int lda, const double* B, int ldb, double beta, double* C, int ldc, bool sym) {
-  static constexpr int kShapes[5][2] = {{64, 64}, {64, 32}, {128, 16}, {16, 16}, {32, 8}};
+int padding_tile(int M, int N) {
   int best = 0;
   long long best_work = -1;
   for (int t = 0; t < 5; ++t) {
@@ -203,13 +205,180 @@ blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, 
       best_work = work;
     }
   }
-  switch (best) {
-    case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
-    case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
-    case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
-    case 3: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
-    default: return launch_tiles<CT, TA, TB, 32, 8>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
+  return best;
+}
+
+// DFMA-bound: balance the SMs.  The fixed rule aims for about 8 CTAs per SM
+// (of which ~4 are resident at once), which keeps the tail of the last wave
+// under ~1/8 of the run; the inner dimension is split (chunks >= 32) until
+// that many CTAs exist.  The autotuner picks among 0, 2, 4 and 8 per SM.
+int split_target(const Ctx* ctx, int q) { return q == 0 ? 0 : (1 << q) * ctx->sms; }
+constexpr int kDefaultSplit = 3;
+
+template <typename CT, bool TA, bool TB>
+blws_status launch_choice(Ctx* ctx, cudaStream_t s, int tile, int target, int M, int N, int K,
+                          double alpha, const double* A, int lda, const double* B, int ldb,
+                          double beta, double* C, int ldc, bool sym) {
+  switch (tile) {
+    case 0: return launch_tiles<CT, TA, TB, 64, 64>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, target);
+    case 1: return launch_tiles<CT, TA, TB, 64, 32>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, target);
+    case 2: return launch_tiles<CT, TA, TB, 128, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, target);
+    case 3: return launch_tiles<CT, TA, TB, 16, 16>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, target);
+    default: return launch_tiles<CT, TA, TB, 32, 8>(ctx, s, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym, target);
   }
+}
+
+// ------------------------------------------------------------ autotuner --
+// With blws_config.tune, the tile shape and the K split of each product come
+// from timing every (shape, split) pair on the product's own dimensions the
+// first time a size bucket is met: each dimension is rounded up on a ladder
+// of quarter-octaves (exact up to 32), so one measurement serves the products
+// within ~25% of it.  Choices are process-wide (per SM count), kept in memory
+// and, when the environment variable BLWS_TUNE_FILE names a file, read from it
+// at first use and appended to it as they are made, so later processes start
+// tuned.  A choice is kept unless it beats the fixed rule by 5%, so timing
+// noise does not move products off the rule for nothing.  Inside a graph
+// capture no timing can run: an untuned bucket there breaks the capture, and
+// the phase runs directly (and tunes).
+struct TuneKey {
+  int v[8];
+  bool operator<(const TuneKey& o) const {
+    for (int i = 0; i < 8; ++i)
+      if (v[i] != o.v[i]) return v[i] < o.v[i];
+    return false;
+  }
+};
+struct TuneChoice {
+  int tile, split;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+int tune_bucket(int x) {
+  if (x <= 32) return x;
+  int p = 32;
+  while (2 * p < x) p *= 2;  // p < x <= 2p
+  const int step = p / 4;
+  return ceil_div(x, step) * step;
+}
+
+TuneKey tune_key(const Ctx* ctx, int ct_bytes, bool ta, bool tb, bool sym, int M, int N, int K) {
+  return TuneKey{{ctx->sms, ct_bytes, ta, tb, sym, tune_bucket(M), tune_bucket(N), tune_bucket(K)}};
+}
+
+// (the mutex is held)
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("BLWS_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneChoice c;
+  while (std::fscanf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", &k.v[0], &k.v[1], &k.v[2], &k.v[3],
+                     &k.v[4], &k.v[5], &k.v[6], &k.v[7], &c.tile, &c.split) == 10)
+    if (c.tile >= 0 && c.tile < 5 && c.split >= 0 && c.split <= 3) g_tune[k] = c;
+  std::fclose(f);
+}
+
+bool tune_lookup(const TuneKey& k, TuneChoice* c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+void tune_store(const TuneKey& k, const TuneChoice& c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  if (!g_tune.emplace(k, c).second) return;  // another context tuned it first
+  const char* path = std::getenv("BLWS_TUNE_FILE");
+  if (!path || !*path) return;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", k.v[0], k.v[1], k.v[2], k.v[3], k.v[4],
+                 k.v[5], k.v[6], k.v[7], c.tile, c.split);
+    std::fclose(f);
+  }
+}
+
+template <typename CT, bool TA, bool TB>
+blws_status tune_shape(Ctx* ctx, cudaStream_t s, int M, int N, int K, bool sym, const TuneKey& key,
+                       TuneChoice* out) {
+  const int lda = TA ? K : M, ldb = TB ? N : K;
+  const size_t na = (size_t)lda * (TA ? M : K), nb = (size_t)ldb * (TB ? K : N), nc = (size_t)M * N;
+  double* w = nullptr;
+  BLWS_TRY(ctx->get(BUF_TUNE, na + nb + nc, &w));
+  BLWS_TRY_CUDA(ctx, cudaMemsetAsync(w, 0, sizeof(double) * (na + nb + nc), s));
+  const double* A = w;
+  const double* B = w + na;
+  double* C = w + na + nb;
+  cudaEvent_t e0, e1;
+  BLWS_TRY_CUDA(ctx, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return ctx->fail(BLWS_ECUDA, "autotuner events");
+  }
+  const TuneChoice rule{padding_tile(M, N), kDefaultSplit};
+  TuneChoice best = rule;
+  float best_ms = -1.0f, rule_ms = -1.0f;
+  blws_status st = BLWS_OK;
+  for (int t = 0; t < 5 && st == BLWS_OK; ++t)
+    for (int q = 0; q <= 3 && st == BLWS_OK; ++q) {
+      const int target = split_target(ctx, q);
+      // one launch to warm up, three timed
+      st = launch_choice<CT, TA, TB>(ctx, s, t, target, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, M, sym);
+      if (st != BLWS_OK) break;
+      if (cudaEventRecord(e0, s) != cudaSuccess) st = ctx->fail(BLWS_ECUDA, "autotuner event");
+      for (int r = 0; r < 3 && st == BLWS_OK; ++r)
+        st = launch_choice<CT, TA, TB>(ctx, s, t, target, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, M, sym);
+      if (st != BLWS_OK) break;
+      float ms = 0.0f;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = ctx->fail(BLWS_ECUDA, "autotuner timing");
+        break;
+      }
+      if (t == rule.tile && q == rule.split) rule_ms = ms;
+      if (best_ms < 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best = TuneChoice{t, q};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BLWS_TRY(st);
+  if (!(best_ms < 0.95f * rule_ms)) best = rule;
+  tune_store(key, best);
+  *out = best;
+  return BLWS_OK;
+}
+
+size_t tune_count() {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  return g_tune.size();
+}
+
+template <typename CT, bool TA, bool TB>
+blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, const double* A,
+                   int lda, const double* B, int ldb, double beta, double* C, int ldc, bool sym) {
+  TuneChoice c{padding_tile(M, N), kDefaultSplit};
+  if (ctx->cfg.tune) {
+    const TuneKey key = tune_key(ctx, (int)sizeof(CT), TA, TB, sym, M, N, K);
+    if (!tune_lookup(key, &c)) {
+      if (ctx->capturing) {
+        ctx->capture_broken = true;
+        return ctx->fail(BLWS_ECUDA, "untuned product shape inside a graph capture");
+      }
+      BLWS_TRY((tune_shape<CT, TA, TB>(ctx, s, M, N, K, sym, key, &c)));
+    }
+  }
+  return launch_choice<CT, TA, TB>(ctx, s, c.tile, split_target(ctx, c.split), M, N, K, alpha, A, lda, B,
+                                   ldb, beta, C, ldc, sym);
 }
 
 // ------------------------------------------------------------ reductions --
@@ -490,3 +659,5 @@ extern "C" blws_status blws_apply_noalloc(const double* W, int m, int n, int ldw
     return BLWS_ECUDA;
   return BLWS_OK;
 }
+
+extern "C" size_t blws_tune_count(void) { return blws::tune_count(); }

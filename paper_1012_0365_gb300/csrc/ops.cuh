@@ -44,6 +44,14 @@ blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, i
 // resolution) are re-solved on their own (see eig.cu).  Synchronises s once.
 blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
                     double eps);
+// sym_eig in two stages around the synchronisation: the device stage (no
+// host wait; it ends with copies of what the host stage reads into pinned
+// host memory), then, once s has been synchronised, the host stage (the
+// fallback and the cluster re-solve, which launch and synchronise only when
+// they apply).  sym_eig = sym_eig_start, synchronise, sym_eig_finish.
+blws_status sym_eig_start(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z);
+blws_status sym_eig_finish(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
+                           double eps);
 
 // FP32 eigenvectors of T (n x n FP64, symmetric) by the tridiagonal route
 // (tri_eig.cu): X (n x n FP64, ld n) receives them, columns in increasing

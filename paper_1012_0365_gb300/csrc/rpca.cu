@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "blws_core.cuh"
+#include "graph.cuh"
 #include "solver.cuh"
 
 namespace blws {
@@ -45,8 +46,12 @@ rpca_epilogue(int m, int n, int ld, const double* __restrict__ U, int ldu,
               const int* __restrict__ count_ptr, const double* __restrict__ D,
               const double* __restrict__ Ein, double* __restrict__ Eout, double* __restrict__ Y,
               double* __restrict__ Wout, double* __restrict__ Aout, double mu, double mu_next,
-              double lam, double* __restrict__ part) {
+              double lam, double* __restrict__ part, const double* __restrict__ dyn) {
   __shared__ CT Us[kEpBK][kEpBM + 1];
+  if (dyn) {  // this iteration's mu and next mu from device memory (replayed graphs)
+    mu = dyn[1];
+    mu_next = dyn[2];
+  }
   __shared__ CT Vs[kEpBK][kEpBN + 1];
   __shared__ double red[256];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -211,8 +216,17 @@ __global__ void scale_columns(int m, int r, const double* __restrict__ U, const 
     Us[e] = U[e] * th[e / m];
 }
 
-__global__ void thresholds(int r, const double* __restrict__ sigma, double eps, double* th) {
+__global__ void thresholds(int r, const double* __restrict__ sigma, double eps,
+                           const double* __restrict__ eps_dev, double* th) {
+  if (eps_dev) eps = *eps_dev;
   for (int t = threadIdx.x; t < r; t += blockDim.x) th[t] = fmax(sigma[t] - eps, 0.0);
+}
+
+// the per-iteration scalars a replayed graph reads: eps, mu, next mu
+__global__ void set_scalars(double* slot, double eps, double mu, double mu_next) {
+  slot[0] = eps;
+  slot[1] = mu;
+  slot[2] = mu_next;
 }
 
 }  // namespace
@@ -401,8 +415,6 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       a.k = std::max(1, std::min(k, N / std::max(sv, w)));
     }
     if (mixed) {
-      BLWS_TRY(tc_planes_from_rows(ctx, s, W, ld, m, n, Wr));
-      BLWS_TRY(tc_planes_from_cols(ctx, s, W, ld, 0, m, n, Wc));
       Wop.Wr = &Wr;
       Wop.Wc = &Wc;
       a.mixed = true;
@@ -410,44 +422,74 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     } else {
       Wop.Wr = Wop.Wc = nullptr;
     }
-    if (fp64tc) {  // FP64-equivalent digit planes of this iteration's W
-      BLWS_TRY(oz_planes_from_rows(ctx, s, W, ld, m, n, Or));
-      BLWS_TRY(oz_planes_from_cols(ctx, s, W, ld, 0, m, n, Oc));
+    if (fp64tc) {
       Wop.Or = &Or;
       Wop.Oc = &Oc;
     }
-    BLWS_TRY(blws_run(ctx, s, Wop, a, Uw, m, Vw, n, sig, count_dev));
-    thresholds<<<1, 256, 0, s>>>(sv, sig, eps, th);
-    BLWS_CHECK_LAUNCH(ctx);
+    const int bw = std::max(a.r, a.w);
+    // phase 1: this iteration's planes of W, the start block, the k block
+    // steps and the device stage of the EVD of T_k
+    GraphKey ka;
+    ka.u(0x52504341u).u(1).u(m).u(n).u(ld).p(W).u(mixed).u(fp64tc).u(a.r).u(a.k).u(a.w);
+    ka.u(a.cold).u(a.standard).p(Uw).p(Vw).u(ctx->cfg.seed);
+    ka.u(a.cold || bw > a.w ? a.draw : 0u);  // the generator stream matters only for drawn columns
+    BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) -> blws_status {
+      if (mixed) {
+        BLWS_TRY(tc_planes_from_rows(ctx, q, W, ld, m, n, Wr));
+        BLWS_TRY(tc_planes_from_cols(ctx, q, W, ld, 0, m, n, Wc));
+      }
+      if (fp64tc) {  // FP64-equivalent digit planes of this iteration's W
+        BLWS_TRY(oz_planes_from_rows(ctx, q, W, ld, m, n, Or));
+        BLWS_TRY(oz_planes_from_cols(ctx, q, W, ld, 0, m, n, Oc));
+      }
+      return blws_run_a(ctx, q, Wop, a);
+    }));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    BLWS_TRY(graph_harvest(ctx));
+    BLWS_TRY(blws_run_mid(ctx, s, Wop, a));  // the EVD's host stage
     const double mu_next = std::min(mu * p.rho, mu_bar);
+    set_scalars<<<1, 1, 0, s>>>(scal + SLOT_EPS, eps, mu, mu_next);
+    BLWS_CHECK_LAUNCH(ctx);
+    const double* dyn = scal + SLOT_EPS;
     // FP64-equivalent mode: A = (U diag(theta)) V^T over the sv computed pairs
     // (theta is zero past the count) as a digit-plane product, when it is
     // large enough for gemm to route it there
     // mixed mode: the same product from split TF32 operands on the tensor cores
     const bool pre = (fp64tc && sv >= 64) || (mixed && sv >= 16 && std::min(m, n) >= 16);
-    if (pre) {
-      double* Us = nullptr;
-      BLWS_TRY(ctx->get(BUF_P2, (size_t)m * sv, &Us));  // CholeskyQR scratch, free here
-      scale_columns<<<std::min(ceil_div((long long)m * sv, 256), ctx->sms * 8), 256, 0, s>>>(
-          m, sv, Uw, th, Us);
+    // phase 2: Ritz lift, count, thresholds, the fused epilogue and its
+    // residual norm, copied back with the count
+    GraphKey kb2;
+    kb2.u(0x52504341u).u(2).u(m).u(n).u(ld).u(mixed).u(fp64tc).u(a.r).u(a.k).u(a.w).u(pre);
+    kb2.p(Uw).p(Vw).p(sig).p(D).p(Ecur).p(Enext).p(Y).p(W).p(Apre).d(lam).p(zpart).u(nparts);
+    BLWS_TRY(graph_phase(ctx, s, kb2, [&](cudaStream_t q) -> blws_status {
+      BLWS_TRY(blws_run_b(ctx, q, Wop, a, Uw, m, Vw, n, sig, count_dev, dyn));
+      thresholds<<<1, 256, 0, q>>>(sv, sig, eps, dyn, th);
       BLWS_CHECK_LAUNCH(ctx);
-      BLWS_TRY(gemm(ctx, s, false, true, m, n, sv, 1.0, Us, m, Vw, n, 0.0, Apre, ld, mixed));
-      rpca_epilogue<EP_PRE, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
-                                                          Ecur, Enext, Y, W, Apre, mu, mu_next,
-                                                          lam, zpart);
-    } else if (mixed)
-      rpca_epilogue<EP_ITER, float><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
-                                                          Ecur, Enext, Y, W, nullptr, mu, mu_next,
-                                                          lam, zpart);
-    else
-      rpca_epilogue<EP_ITER, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
-                                                           Ecur, Enext, Y, W, nullptr, mu, mu_next,
-                                                           lam, zpart);
-    BLWS_CHECK_LAUNCH(ctx);
-    reduce_sum<<<1, 256, 0, s>>>(nparts, zpart, scal + SLOT_NORM);
-    BLWS_CHECK_LAUNCH(ctx);
-    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
-                                       cudaMemcpyDeviceToHost, s));
+      if (pre) {
+        double* Us = nullptr;
+        BLWS_TRY(ctx->get(BUF_P2, (size_t)m * sv, &Us));  // CholeskyQR scratch, free here
+        scale_columns<<<std::min(ceil_div((long long)m * sv, 256), ctx->sms * 8), 256, 0, q>>>(
+            m, sv, Uw, th, Us);
+        BLWS_CHECK_LAUNCH(ctx);
+        BLWS_TRY(gemm(ctx, q, false, true, m, n, sv, 1.0, Us, m, Vw, n, 0.0, Apre, ld, mixed));
+        rpca_epilogue<EP_PRE, double><<<egrid, 256, 0, q>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                            Ecur, Enext, Y, W, Apre, mu, mu_next,
+                                                            lam, zpart, dyn);
+      } else if (mixed)
+        rpca_epilogue<EP_ITER, float><<<egrid, 256, 0, q>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                            Ecur, Enext, Y, W, nullptr, mu, mu_next,
+                                                            lam, zpart, dyn);
+      else
+        rpca_epilogue<EP_ITER, double><<<egrid, 256, 0, q>>>(m, n, ld, Uw, m, th, Vw, n, count_dev, D,
+                                                             Ecur, Enext, Y, W, nullptr, mu, mu_next,
+                                                             lam, zpart, dyn);
+      BLWS_CHECK_LAUNCH(ctx);
+      reduce_sum<<<1, 256, 0, q>>>(nparts, zpart, scal + SLOT_NORM);
+      BLWS_CHECK_LAUNCH(ctx);
+      BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
+                                         cudaMemcpyDeviceToHost, q));
+      return BLWS_OK;
+    }));
     BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     svp = *reinterpret_cast<int*>(ctx->host_pinned + SLOT_COUNT);
     const double z2 = ctx->host_pinned[SLOT_NORM];
@@ -481,7 +523,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   // outputs: A = U diag(th) V^T of the last SVT; E = the E of that iteration
   rpca_epilogue<EP_FINAL, double><<<egrid, 256, 0, s>>>(m, n, ld, Uw, m, th, Vw, n, count_dev,
                                                         nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                        A, 0.0, 1.0, 0.0, nullptr);
+                                                        A, 0.0, 1.0, 0.0, nullptr, nullptr);
   BLWS_CHECK_LAUNCH(ctx);
   if (Ecur != E) {
     BLWS_TRY_CUDA(ctx, cudaMemcpy2DAsync(E, sizeof(double) * ld, Ecur, sizeof(double) * ld,
