@@ -79,18 +79,27 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "source": "of fallback"}
 
 
-def steady_state(records):
-    """The products of the size that takes the most device time among the
-    timed ones (the steady block width of the solves; the small products of
-    the norm estimate and the wider ones of the first iterations are left
-    out): (count, mean ms, work each)."""
-    if not records:
+# kernel kind of the mode's products with W~ (blws_timing_records): FP64 DFMA,
+# split TF32, digit planes.  The mixed mode's refinement tail and every mode's
+# norm estimate of the tensor-core modes run digit-plane products too; the
+# roofline is the mode's own kernel's.
+MODE_KIND = {"fp64": 0, "mixed": 1, "fp64tc": 2}
+
+
+def steady_state(records, kind=None, work=None):
+    """The timed products of the given kernel kind at the solves' steady block
+    width: those of work `work` (2 m n b at the final b) when there are any,
+    else the size that takes the most device time (the small products of the
+    norm estimate and the wider ones of the first iterations are left out):
+    (count, mean ms, work each)."""
+    recs = [(t, w) for t, w, k in records or [] if kind is None or k == kind]
+    if not recs:
         return 0, 0.0, 0.0
     tot = {}
-    for t, w in records:
+    for t, w in recs:
         tot[w] = tot.get(w, 0.0) + t
-    w0 = max(tot, key=lambda w: (tot[w], w))
-    ts = [t for t, w in records if w == w0]
+    w0 = work if work in tot else max(tot, key=lambda w: (tot[w], w))
+    ts = [t for t, w in recs if w == w0]
     return len(ts), float(np.mean(ts)), w0
 
 
@@ -104,7 +113,7 @@ def roofline(torch, mode, ms, launches, work, clocks, workload, b, records=None)
     if not launches or ms <= 0:
         return None
     all_tflops = 2.0 * work / (ms / 1e3) / 1e12  # FP64-equivalent rate over every product
-    n_ss, ms_ss, w_ss = steady_state(records)
+    n_ss, ms_ss, w_ss = steady_state(records, MODE_KIND[mode], 2.0 * WORKLOAD_MN[workload] * b)
     if n_ss:
         launches, work, ms = n_ss, w_ss * n_ss, ms_ss * n_ss
         b = int(round(w_ss / (2.0 * WORKLOAD_MN[workload])))
@@ -300,7 +309,7 @@ def run_mc(args):
     cols = torch.from_numpy(P["cols"]).cuda()
     vals = torch.from_numpy(P["vals"]).cuda()
     prec = PRECISIONS[args.precision]
-    ctx = blws.Context(k=args.k, precision=prec)
+    ctx = blws.Context(k=args.k, precision=prec, tune=args.tune)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     max_rank = 4 * r
@@ -746,7 +755,7 @@ def main():
     ap.add_argument("--graphs", type=int, default=1, choices=(0, 1),
                     help="replay CUDA graphs of the outer-iteration phases (1, default) or launch directly")
     ap.add_argument("--tune", type=int, default=1, choices=(0, 1),
-                    help="batch leg: product tiles from the timed autotuner (1, default) or the fixed rule")
+                    help="CUDA-core product tiles from the timed autotuner (1, default) or the fixed rule")
     args = ap.parse_args()
     ws, rank = dist_env()
 
@@ -786,7 +795,7 @@ def main():
     Ah = torch.empty((n, m), dtype=torch.float64).pin_memory()
     Eh = torch.empty((n, m), dtype=torch.float64).pin_memory()
     head = PRECISIONS[args.headline]
-    ctx = blws.Context(k=args.k, device=local_rank, precision=head)
+    ctx = blws.Context(k=args.k, device=local_rank, precision=head, graphs=args.graphs, tune=args.tune)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -794,7 +803,8 @@ def main():
         return (c or ctx).rpca_solve(Dg, tol=args.tol, A=A, E=E)
 
     if args.profile_solve or args.profile_apply:
-        ctx = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[args.precision])
+        ctx = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[args.precision],
+                           graphs=args.graphs, tune=args.tune)
         if args.profile_solve:
             l0 = ctx.launches
             _, _, info = solve()
@@ -864,7 +874,8 @@ def main():
     legs = {}
     if not args.no_mixed:
         for mode in [x for x in ("fp64", "mixed", "fp64tc") if x != args.headline]:
-            c2 = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[mode])
+            c2 = blws.Context(k=args.k, device=local_rank, precision=PRECISIONS[mode], graphs=args.graphs,
+                              tune=args.tune)
             for _ in range(args.warmup):
                 solve(c2)
             ms2 = []
@@ -913,7 +924,7 @@ def main():
         extra["mc"]["steps"], extra["mc"]["warmup"] = sub.steps, sub.warmup
         extra["mc"]["oracle_parity"] = mc_oracle_parity(torch)
         sub = argparse.Namespace(**vars(args))
-        sub.precision, sub.batch_count, sub.workers = "fp64", 256, 16
+        sub.precision, sub.batch_count, sub.workers = "fp64tc", 256, 16
         bl = run_batch(sub)
         extra["batch"] = {k: bl[k] for k in ("value", "unit", "config", "solved_ok", "relerr_vs_planted",
                                              "latency_ms", "sequential", "speedup_vs_sequential")}
@@ -946,6 +957,7 @@ def main():
                    "tol": args.tol, "k": args.k, "precision": args.headline,
                    "arithmetic": MODE_DTYPE[args.headline],
                    "l2": "flushed between steps (512 MB write)",
+                   "graphs": args.graphs, "tune": args.tune,
                    "parallelism": "replicas" if ws > 1 else "single"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "max": float(lat.max())},

@@ -307,10 +307,13 @@ blws_status blws_gemm(blws_ctx* ctx, int ta, int tb, int M, int N, int K, double
  * per product; timing is off by default. */
 blws_status blws_timing_start(blws_ctx* ctx);
 blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, double* work);
-/* The per-product records of the last blws_timing_stop, in launch order:
- * ms[i] (device time) and work[i] (2 m n b) for i < min(cap, count), host
- * arrays (either may be NULL).  Returns the count. */
-size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work);
+/* The per-product records of the last blws_timing_stop: ms[i] (device
+ * time), work[i] (2 m n b) and kind[i] (the kernel that computed it: 0 FP64
+ * DFMA GEMMs, 1 split-TF32 tensor-core products, 2 BF16 digit-plane
+ * tensor-core products) for i < min(cap, count), host arrays (any may be
+ * NULL); products launched directly come first, in launch order, then those
+ * timed inside replayed CUDA graphs.  Returns the count. */
+size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work, int* kind);
 
 /* Self-test of the bounded waits (no counterpart in the paper).  Every wait
  * of the tensor-core kernels (a TMA copy or an MMA that should complete) is

@@ -135,7 +135,8 @@ def load():
     lib.blws_wait_probe.argtypes = [vp, ctypes.c_uint, vp]
     lib.blws_timing_start.argtypes = [vp]
     lib.blws_timing_stop.argtypes = [vp, ctypes.POINTER(cd), ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(cd)]
-    lib.blws_timing_records.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(cd), ctypes.POINTER(cd)]
+    lib.blws_timing_records.argtypes = [vp, ctypes.c_size_t, ctypes.POINTER(cd), ctypes.POINTER(cd),
+                                        ctypes.POINTER(ctypes.c_int)]
     for f in EXPORTS:
         if f not in ("blws_status_str", "blws_last_error"):
             getattr(lib, f).restype = ci
@@ -358,12 +359,16 @@ class Context:
             self._raise(st, "blws_timing_stop")
         return ms.value, int(n.value), work.value
 
+    # kernel kinds of the timed products
+    KIND_FP64, KIND_TF32, KIND_DIGITS = 0, 1, 2
+
     def timing_records(self):
-        """Per-product (device ms, multiply-adds) of the last timing_stop."""
-        k = int(load().blws_timing_records(self._h, 0, None, None))
+        """Per-product (device ms, multiply-adds, kernel kind) of the last timing_stop."""
+        k = int(load().blws_timing_records(self._h, 0, None, None, None))
         ms, w = (ctypes.c_double * max(k, 1))(), (ctypes.c_double * max(k, 1))()
-        load().blws_timing_records(self._h, k, ms, w)
-        return [(ms[i], w[i]) for i in range(k)]
+        kd = (ctypes.c_int * max(k, 1))()
+        load().blws_timing_records(self._h, k, ms, w, kd)
+        return [(ms[i], w[i], kd[i]) for i in range(k)]
 
     def wait_probe(self, polls=256, stream=None):
         """Run the bounded-wait self-test; returns its status (ETIMEOUT expected)."""

@@ -101,7 +101,7 @@ blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double*
     BLWS_TRY(ctx->time_begin(s));
     BLWS_TRY(gemm(ctx, s, false, false, m, b, n, 1.0, op.W, op.ldw, X + m, ldx, 0.0, P, ldp));
     BLWS_TRY(gemm(ctx, s, true, false, n, b, m, 1.0, op.W, op.ldw, X, ldx, 0.0, P + m, ldp));
-    return ctx->time_end(s, 2.0 * m * n * b);
+    return ctx->time_end(s, 2.0 * m * n * b, 0);
   }
   return apply_sparse(ctx, s, op, X, ldx, b, P, ldp);
 }

@@ -75,7 +75,7 @@ blws_status Ctx::get(Buf b, size_t bytes, void** out) {
 blws_status Ctx::time_begin(cudaStream_t s) {
   if (!timing) return BLWS_OK;
   if (capturing) {  // events of the graph: recorded by every replay, read after it
-    TimedPair t{nullptr, nullptr, 0.0};
+    TimedPair t{nullptr, nullptr, 0.0, 0};
     BLWS_TRY_CUDA(this, cudaEventCreate(&t.e0));
     BLWS_TRY_CUDA(this, cudaEventCreate(&t.e1));
     cap_ev.push_back(t);
@@ -86,33 +86,42 @@ blws_status Ctx::time_begin(cudaStream_t s) {
     const size_t ncap = tcap ? 2 * tcap : 256;
     cudaEvent_t* n = new (std::nothrow) cudaEvent_t[2 * ncap];
     double* w = new (std::nothrow) double[ncap];
-    if (!n || !w) {
+    int* kk = new (std::nothrow) int[ncap];
+    if (!n || !w || !kk) {
       delete[] n;
       delete[] w;
+      delete[] kk;
       return fail(BLWS_ENOMEM, "timing events");
     }
     for (size_t i = 0; i < 2 * tcap; ++i) n[i] = tev[i];
-    for (size_t i = 0; i < tcap; ++i) w[i] = tw[i];
+    for (size_t i = 0; i < tcap; ++i) {
+      w[i] = tw[i];
+      kk[i] = tk[i];
+    }
     for (size_t i = 2 * tcap; i < 2 * ncap; ++i) BLWS_TRY_CUDA(this, cudaEventCreate(&n[i]));
     delete[] tev;
     delete[] tw;
+    delete[] tk;
     tev = n;
     tw = w;
+    tk = kk;
     tcap = ncap;
   }
   BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused], s));
   return BLWS_OK;
 }
 
-blws_status Ctx::time_end(cudaStream_t s, double work) {
+blws_status Ctx::time_end(cudaStream_t s, double work, int kind) {
   if (!timing) return BLWS_OK;
   if (capturing) {
     cap_ev.back().work = work;
+    cap_ev.back().kind = kind;
     BLWS_TRY_CUDA(this, cudaEventRecordWithFlags(cap_ev.back().e1, s, cudaEventRecordExternal));
     return BLWS_OK;
   }
   BLWS_TRY_CUDA(this, cudaEventRecord(tev[2 * tused + 1], s));
   tw[tused] = work;
+  tk[tused] = kind;
   ++tused;
   twork += work;
   return BLWS_OK;
@@ -240,8 +249,10 @@ blws_status blws_destroy(blws_ctx* ctx) {
   for (size_t i = 0; i < 2 * ctx->tcap; ++i) cudaEventDestroy(ctx->tev[i]);
   delete[] ctx->tev;
   delete[] ctx->tw;
+  delete[] ctx->tk;
   delete[] ctx->trec_ms;
   delete[] ctx->trec_w;
+  delete[] ctx->trec_k;
   delete ctx;
   return BLWS_OK;
 }
@@ -558,6 +569,7 @@ blws_status blws_timing_start(blws_ctx* ctx) {
   ctx->pending_ev.clear();
   ctx->graph_ms.clear();
   ctx->graph_w.clear();
+  ctx->graph_kind.clear();
   return BLWS_OK;
 }
 
@@ -570,10 +582,12 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
   double total = 0.0;
   delete[] ctx->trec_ms;
   delete[] ctx->trec_w;
+  delete[] ctx->trec_k;
   ctx->trec_ms = new (std::nothrow) double[ctx->tused + ng + 1];
   ctx->trec_w = new (std::nothrow) double[ctx->tused + ng + 1];
+  ctx->trec_k = new (std::nothrow) int[ctx->tused + ng + 1];
   ctx->trec_n = 0;
-  if (!ctx->trec_ms || !ctx->trec_w) return ctx->fail(BLWS_ENOMEM, "timing records");
+  if (!ctx->trec_ms || !ctx->trec_w || !ctx->trec_k) return ctx->fail(BLWS_ENOMEM, "timing records");
   for (size_t i = 0; i < ctx->tused; ++i) {
     BLWS_TRY_CUDA(ctx, cudaEventSynchronize(ctx->tev[2 * i + 1]));
     float t = 0.0f;
@@ -581,6 +595,7 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
     total += t;
     ctx->trec_ms[i] = t;
     ctx->trec_w[i] = ctx->tw[i];
+    ctx->trec_k[i] = ctx->tk[i];
   }
   double gwork = 0.0;
   for (size_t i = 0; i < ng; ++i) {
@@ -588,6 +603,7 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
     gwork += ctx->graph_w[i];
     ctx->trec_ms[ctx->tused + i] = ctx->graph_ms[i];
     ctx->trec_w[ctx->tused + i] = ctx->graph_w[i];
+    ctx->trec_k[ctx->tused + i] = ctx->graph_kind[i];
   }
   ctx->trec_n = ctx->tused + ng;
   *ms = total;
@@ -597,15 +613,17 @@ blws_status blws_timing_stop(blws_ctx* ctx, double* ms, uint64_t* launches, doub
   ctx->twork = 0.0;
   ctx->graph_ms.clear();
   ctx->graph_w.clear();
+  ctx->graph_kind.clear();
   return BLWS_OK;
 }
 
-size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work) {
+size_t blws_timing_records(const blws_ctx* ctx, size_t cap, double* ms, double* work, int* kind) {
   if (!ctx) return 0;
   const size_t k = std::min(cap, ctx->trec_n);
   for (size_t i = 0; i < k; ++i) {
     if (ms) ms[i] = ctx->trec_ms[i];
     if (work) work[i] = ctx->trec_w[i];
+    if (kind) kind[i] = ctx->trec_k[i];
   }
   return ctx->trec_n;
 }

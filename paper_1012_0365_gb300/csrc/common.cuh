@@ -83,6 +83,7 @@ enum Buf {
 struct TimedPair {
   cudaEvent_t e0, e1;
   double work;
+  int kind;  // 0 FP64 DFMA, 1 split TF32, 2 digit planes
 };
 struct GraphEntry {
   std::vector<uint64_t> key;
@@ -129,14 +130,16 @@ struct Ctx {
   bool timing = false;
   cudaEvent_t* tev = nullptr;   // 2 * tcap events
   double* tw = nullptr;         // work of each timed product (tcap)
+  int* tk = nullptr;            // its kernel kind (tcap)
   size_t tcap = 0, tused = 0;
   double twork = 0.0;
   double* trec_ms = nullptr;    // per-product times of the last blws_timing_stop
   double* trec_w = nullptr;
+  int* trec_k = nullptr;
   size_t trec_n = 0;
   // events around one product's kernels (no-ops unless timing is on)
   blws_status time_begin(cudaStream_t s);
-  blws_status time_end(cudaStream_t s, double work);
+  blws_status time_end(cudaStream_t s, double work, int kind);
   // a mixed-precision solve in its refinement tail: FP64 products go to the
   // FP64-equivalent digit-plane kernels as in a BLWS_PREC_FP64_TC context
   bool oz_tail = false;
@@ -162,6 +165,7 @@ struct Ctx {
   std::vector<TimedPair> cap_ev;           // timed products of the capture in progress
   std::vector<TimedPair> pending_ev;       // timed products of replays not yet read
   std::vector<double> graph_ms, graph_w;   // their times and work, once read
+  std::vector<int> graph_kind;
   // pinned host copies of the eigen-solver's results for its host stage
   // (eigenvalues, group ids and tops, refinement width, failure flag)
   void* host_eig = nullptr;

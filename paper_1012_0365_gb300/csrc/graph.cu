@@ -126,6 +126,7 @@ blws_status graph_harvest(Ctx* ctx) {
     BLWS_TRY_CUDA(ctx, cudaEventElapsedTime(&ms, t.e0, t.e1));
     ctx->graph_ms.push_back(ms);
     ctx->graph_w.push_back(t.work);
+    ctx->graph_kind.push_back(t.kind);
   }
   ctx->pending_ev.clear();
   return BLWS_OK;

@@ -423,7 +423,7 @@ blws_status tc_dual_apply(Ctx* ctx, cudaStream_t s, const TcPlanes& Wr, const Tc
     case 192: BLWS_TRY((launch_tc<192, 2>(ctx, s, jobs, blocks))); break;
     default: BLWS_TRY((launch_tc<256, 2>(ctx, s, jobs, blocks))); break;
   }
-  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b));
+  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b, 1));
   for (int t = 0; t < 2; ++t) {
     const size_t total = (size_t)Ms[t] * b;
     if (total == 0) continue;

@@ -654,7 +654,7 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   BLWS_TRY(ctx->time_begin(s));
   oz_kernel<<<blocks, kOzThreads, bytes, s>>>(jobs);
   BLWS_CHECK_LAUNCH(ctx);
-  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b));
+  BLWS_TRY(ctx->time_end(s, 2.0 * m * n * b, 2));
   for (int t = 0; t < 2; ++t) {
     const size_t tot = (size_t)Ms[t] * b;
     const int G = oz_lanes(ctx->sms, tot, splits[t]);

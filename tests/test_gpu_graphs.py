@@ -89,7 +89,7 @@ def test_graph_timing_records_match_direct(torch_mod):
         ms, n, work = c.timing_stop()
         recs = c.timing_records()
         assert n == len(recs) and n > 0 and ms > 0.0
-        out.append(sorted(w for _, w in recs))
+        out.append(sorted((w, kd) for _, w, kd in recs))
     assert out[0] == out[1]
     assert g.graph_stats()[1] > 0
 
