@@ -110,6 +110,17 @@ typedef struct {
                      BLWS_TUNE_FILE set they are read from and appended to
                      that file.  Products differ from the rule's in rounding
                      only (the split-K sums are grouped differently). */
+  double guard;   /* Ritz-residual guard of rpca_solve and mc_solve: 0
+                     (default) off.  > 0: every BLWS call also forms the
+                     residual of its last block, whose Gram matrix gives each
+                     Ritz pair's residual ||W~ y - theta y|| (the block Lanczos
+                     relation); when a pair above the threshold has a residual
+                     above guard x the largest Ritz value, the call is run
+                     again from the same start with one more block, at most
+                     twice per outer iteration (rpca_info / mc_info .restarts
+                     counts them).  A guard against inaccurate partial SVDs
+                     in rank-growth transients; it costs one residual product
+                     and one Gram matrix per call. */
 } blws_config;
 
 /* Fill *cfg with the defaults above.  Never fails for a non-NULL cfg. */
@@ -353,6 +364,7 @@ typedef struct {
   double norm_two;  /* the estimate of ||D||_2 used for mu0 and Y0 */
   int status;       /* BLWS_OK or BLWS_ENOCONV */
   int mixed_iters;  /* iterations that ran with mixed products */
+  int restarts;     /* BLWS calls repeated with one more block (blws_config.guard) */
 } rpca_info;
 
 blws_status rpca_params_default(rpca_params* p);
@@ -389,6 +401,7 @@ typedef struct {
   double residual;  /* observed relative residual at exit */
   double norm_two;  /* the estimate of ||P_Omega M||_2 */
   int status;
+  int restarts;     /* BLWS calls repeated with one more block (blws_config.guard) */
 } mc_info;
 
 blws_status mc_params_default(mc_params* p);

@@ -29,7 +29,7 @@ class BlwsConfig(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("k_cold", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("device", ctypes.c_int), ("start", ctypes.c_int),
                 ("warm", ctypes.c_int), ("grid_sms", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("tune", ctypes.c_int)]
+                ("tune", ctypes.c_int), ("guard", ctypes.c_double)]
 
 
 class BlwsOp(ctypes.Structure):
@@ -50,7 +50,7 @@ class RpcaParams(ctypes.Structure):
 class RpcaInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rank", ctypes.c_int), ("nnzE", ctypes.c_int64),
                 ("residual", ctypes.c_double), ("norm_two", ctypes.c_double),
-                ("status", ctypes.c_int), ("mixed_iters", ctypes.c_int)]
+                ("status", ctypes.c_int), ("mixed_iters", ctypes.c_int), ("restarts", ctypes.c_int)]
 
 
 class McParams(ctypes.Structure):
@@ -62,7 +62,7 @@ class McParams(ctypes.Structure):
 
 class McInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("rank", ctypes.c_int), ("residual", ctypes.c_double),
-                ("norm_two", ctypes.c_double), ("status", ctypes.c_int)]
+                ("norm_two", ctypes.c_double), ("status", ctypes.c_int), ("restarts", ctypes.c_int)]
 
 
 class ServerConfig(ctypes.Structure):
@@ -207,13 +207,13 @@ class Context:
     """Owns a blws_ctx (workspace, generator state) bound to one device."""
 
     def __init__(self, k=3, k_cold=4, seed=0x5EED, device=0, precision=0, start=0, warm=1,
-                 grid_sms=0, graphs=1, tune=0):
+                 grid_sms=0, graphs=1, tune=0, guard=0.0):
         lib = load()
         cfg = BlwsConfig()
         lib.blws_config_default(ctypes.byref(cfg))
         cfg.k, cfg.k_cold, cfg.seed, cfg.device = k, k_cold, seed, device
         cfg.precision, cfg.start, cfg.warm, cfg.grid_sms = precision, start, warm, grid_sms
-        cfg.graphs, cfg.tune = graphs, tune
+        cfg.graphs, cfg.tune, cfg.guard = graphs, tune, guard
         h = ctypes.c_void_p()
         st = lib.blws_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:
@@ -431,7 +431,7 @@ class Context:
             self._raise(st, "rpca_solve")
         out = {"iters": info.iters, "rank": info.rank, "nnzE": info.nnzE,
                "residual": info.residual, "norm_two": info.norm_two, "status": info.status,
-               "mixed_iters": info.mixed_iters}
+               "mixed_iters": info.mixed_iters, "restarts": info.restarts}
         if tr is not None:
             k = min(trace, info.iters)
             out["trace"] = [(tr[3 * i], int(tr[3 * i + 1]), int(tr[3 * i + 2])) for i in range(k)]
@@ -460,7 +460,7 @@ class Context:
         r = info.rank
         return U[:, :r], th[:r], V[:, :r], {"iters": info.iters, "rank": r,
                                             "residual": info.residual, "norm_two": info.norm_two,
-                                            "status": info.status}
+                                            "status": info.status, "restarts": info.restarts}
 
 
 class Server:
@@ -471,13 +471,13 @@ class Server:
     here until wait() returns their result."""
 
     def __init__(self, workers=8, hbm_budget=0, k=3, k_cold=4, seed=0x5EED, device=0, precision=0,
-                 grid_sms=0, graphs=1, tune=0):
+                 grid_sms=0, graphs=1, tune=0, guard=0.0):
         lib = load()
         cfg = ServerConfig()
         lib.blws_server_config_default(ctypes.byref(cfg))
         cfg.workers, cfg.hbm_budget = workers, hbm_budget
         cfg.cfg.k, cfg.cfg.k_cold, cfg.cfg.seed, cfg.cfg.device, cfg.cfg.precision = k, k_cold, seed, device, precision
-        cfg.cfg.grid_sms, cfg.cfg.graphs, cfg.cfg.tune = grid_sms, graphs, tune
+        cfg.cfg.grid_sms, cfg.cfg.graphs, cfg.cfg.tune, cfg.cfg.guard = grid_sms, graphs, tune, guard
         h = ctypes.c_void_p()
         st = lib.blws_server_create(ctypes.byref(h), ctypes.byref(cfg))
         if st != OK:

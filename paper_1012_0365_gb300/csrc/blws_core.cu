@@ -88,6 +88,36 @@ __global__ void ritz_values(int r, const double* __restrict__ lam, double eps,
   if (threadIdx.x == 0) *count = cnt;
 }
 
+// The guard's measure.  Y = G Z_last (G = R_k^T R_k, b x b; Z_last the last
+// block's rows of the first r eigenvectors of T_k): rho_j^2 = Z_last(:, j) .
+// Y(:, j) is ||R_k Z_last(:, j)||^2, the squared residual ||W~ y_j -
+// theta_j y_j|| of Ritz pair j (block Lanczos relation W~ Q_k = Q_k T_k +
+// R_k E_k^T).  *out = max over the pairs with theta_j > eps of rho_j /
+// |theta_1| (0 when there is none).  One CTA, a warp per pair.
+__global__ void ritz_residual(int b, int r, const double* __restrict__ Zl, int ldz,
+                              const double* __restrict__ Y, int ldy, const double* __restrict__ lam,
+                              double eps, const double* __restrict__ eps_dev, double* out) {
+  __shared__ double red[32];
+  if (eps_dev) eps = *eps_dev;
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = blockDim.x / 32;
+  const double top = fabs(lam[0]);
+  double worst = 0.0;
+  for (int j = warp; j < r; j += nw) {
+    double acc = 0.0;
+    for (int i = lane; i < b; i += 32) acc = fma(Zl[i + (size_t)j * ldz], Y[i + (size_t)j * ldy], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lam[j] > eps && top > 0.0) worst = fmax(worst, sqrt(fmax(acc, 0.0)) / top);
+  }
+  if (lane == 0) red[warp] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double w = 0.0;
+    for (int q = 0; q < nw; ++q) w = fmax(w, red[q]);
+    *out = w;
+  }
+}
+
 }  // namespace
 
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,
@@ -184,7 +214,34 @@ blws_status blws_run_a(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsA
                                                                        l * b);
     BLWS_CHECK_LAUNCH(ctx);
   }
-  return sym_eig_start(ctx, s, kb, T, lam, Z);
+  if (a.guard) {
+    // the residual of the last block (the recurrence's product with no QR
+    // after it) and its Gram matrix
+    const int l = k - 1, c0r = l > 0 ? l - 1 : l;
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, (l + 1 - c0r) * b, -1.0, Q + (size_t)c0r * b * N, N,
+                  T + (size_t)c0r * b + (size_t)l * b * kb, kb, 1.0, P, N, f32));
+    double* Gk = nullptr;
+    BLWS_TRY(ctx->get(BUF_GUARD, (size_t)b * b + (size_t)b * a.r, &Gk));
+    BLWS_TRY(gemm_sym(ctx, s, true, false, b, N, 1.0, P, N, P, N, Gk, b, f32));
+  }
+  BLWS_TRY(sym_eig_start(ctx, s, kb, T, lam, Z));
+  if (a.guard) {
+    double* Gk = nullptr;
+    BLWS_TRY(ctx->get(BUF_GUARD, (size_t)b * b + (size_t)b * a.r, &Gk));
+    double* Yg = Gk + (size_t)b * b;
+    const double* Zl = Z + (size_t)(k - 1) * b;  // rows (k-1) b .. k b - 1
+    BLWS_TRY(gemm(ctx, s, false, false, b, a.r, b, 1.0, Gk, b, Zl, kb, 0.0, Yg, b));
+    ritz_residual<<<1, 256, 0, s>>>(b, a.r, Zl, kb, Yg, b, lam, a.eps, a.eps_dev, scal + SLOT_GUARD);
+    BLWS_CHECK_LAUNCH(ctx);
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(sym_eig_host_extra(ctx, kb), scal + SLOT_GUARD, sizeof(double),
+                                       cudaMemcpyDeviceToHost, s));
+  }
+  return BLWS_OK;
+}
+
+double blws_guard_ratio(Ctx* ctx, const BlwsArgs& a) {
+  const int b = std::max(a.r, a.w + (a.G ? a.g : 0));
+  return *sym_eig_host_extra(ctx, a.k * b);
 }
 
 namespace {

@@ -52,7 +52,16 @@ struct BlwsArgs {
   bool mixed = false;        // tall products in FP32 arithmetic (eigen-solver and
                              // Cholesky factorisations stay FP64)
   bool standard = false;     // warm columns [U0; 0] instead of [U0; V0] / sqrt(2)
+  // Ritz-residual guard: stage (a) also forms the residual of the last block
+  // and writes the largest ||W~ y - theta y|| / theta_1 over the pairs above
+  // the threshold (read from eps_dev, device) to the pinned host copy the
+  // eigen-solver's host stage reads (blws_guard_ratio)
+  bool guard = false;
+  const double* eps_dev = nullptr;
 };
+
+// the guard's ratio of the last stage (a) with a.guard, once s is synchronised
+double blws_guard_ratio(Ctx* ctx, const BlwsArgs& a);
 
 // P = W~ X: P[0:m] = W X[m:m+n], P[m:m+n] = W^T X[0:m]  (sym: P = W X, m rows)
 blws_status apply_op(Ctx* ctx, cudaStream_t s, const Operator& op, const double* X, int ldx, int b,

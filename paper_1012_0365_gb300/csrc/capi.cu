@@ -187,6 +187,7 @@ blws_status blws_config_default(blws_config* cfg) {
   cfg->grid_sms = 0;
   cfg->graphs = 1;
   cfg->tune = 0;
+  cfg->guard = 0.0;
   return BLWS_OK;
 }
 
@@ -199,7 +200,8 @@ blws_status blws_create(blws_ctx** out, const blws_config* cfg) {
   if (c.k < 1 || c.k_cold < 1 ||
       (c.precision != BLWS_PREC_FP64 && c.precision != BLWS_PREC_MIXED && c.precision != BLWS_PREC_FP64_TC) ||
       (c.start != 0 && c.start != 1) || (c.warm != 0 && c.warm != 1) || c.grid_sms < 0 ||
-      (c.graphs != 0 && c.graphs != 1) || (c.tune != 0 && c.tune != 1))
+      (c.graphs != 0 && c.graphs != 1) || (c.tune != 0 && c.tune != 1) ||
+      !(c.guard >= 0.0))
     return BLWS_EINVAL;
   blws_ctx* ctx = new (std::nothrow) blws_ctx();
   if (!ctx) return BLWS_ENOMEM;

@@ -75,6 +75,7 @@ enum Buf {
   BUF_RPCA_A,    // RPCA, FP64-equivalent and mixed modes: A = U diag(theta) V^T as a product (m x n)
   BUF_TC_G,      // mixed precision: TF32 planes of both operands of a general product
   BUF_TUNE,      // GEMM autotuner: scratch operands of the shape being timed
+  BUF_GUARD,     // Ritz-residual guard: Gram matrix of the last block residual, and R^T R Z
   BUF_COUNT_
 };
 
@@ -203,6 +204,7 @@ enum Slot {
   SLOT_EPS = 10,       // per-iteration scalars read by the kernels of a replayed
   SLOT_MU = 11,        //   graph: threshold eps = 1 / mu, mu, and the next mu
   SLOT_MU_NEXT = 12,
+  SLOT_GUARD = 13,     // largest Ritz residual of a pair above eps, relative to the top Ritz value
   SLOT_MAX = 16
 };
 

@@ -672,6 +672,10 @@ __global__ void gather_cols(int rows, int cols, const double* __restrict__ In,
 // ints), then the refinement width and the failure flag
 size_t eig_host_bytes(int n) { return sizeof(double) * n + sizeof(int) * 2 * (size_t)n + 2 * sizeof(double); }
 
+double* sym_eig_host_extra(Ctx* ctx, int n) {
+  return reinterpret_cast<double*>(static_cast<char*>(ctx->host_eig) + eig_host_bytes(n));
+}
+
 blws_status eig_copy_back(Ctx* ctx, cudaStream_t s, int n, const double* lam, const int* dgrp,
                           const double* scal) {
   char* h = static_cast<char*>(ctx->host_eig);
@@ -691,7 +695,7 @@ blws_status sym_eig_start(Ctx* ctx, cudaStream_t s, int n, const double* T, doub
   const bool tri_enabled = ctx->eig_route != 1;
   int* dgrp = nullptr;  // sorted group ids and group tops of the tridiagonal stage (n ints, n floats)
   BLWS_TRY(ctx->get(BUF_EIG_GRP, (size_t)2 * n, &dgrp));
-  BLWS_TRY(ctx->host_eig_get(eig_host_bytes(n)));
+  BLWS_TRY(ctx->host_eig_get(eig_host_bytes(n) + sizeof(double)));
   BLWS_TRY(sym_eig_level(ctx, s, n, T, lam, Z, scal + SLOT_AUX2, true,
                          tri_enabled ? reinterpret_cast<int*>(scal + SLOT_TRIFAIL) : nullptr, dgrp));
   return eig_copy_back(ctx, s, n, lam, dgrp, scal);

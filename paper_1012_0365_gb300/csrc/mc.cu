@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "graph.cuh"
 #include "mc_kernels.cuh"
 #include "solver.cuh"
 
@@ -32,9 +33,14 @@ __global__ void scale_copy(int nnz, double a, const double* __restrict__ x, doub
     y[e] = a * x[e];
 }
 
-__global__ void thresholds_mc(int r, const double* __restrict__ sigma, double tau, double* th) {
+__global__ void thresholds_mc(int r, const double* __restrict__ sigma, double tau,
+                              const double* __restrict__ tau_dev, double* th) {
+  if (tau_dev) tau = *tau_dev;
   for (int t = threadIdx.x; t < r; t += blockDim.x) th[t] = fmax(sigma[t] - tau, 0.0);
 }
+
+// the threshold a replayed graph reads (tau changes in the proximal form)
+__global__ void set_tau(double* slot, double tau) { *slot = tau; }
 
 __global__ void check_finite(int nnz, const double* __restrict__ v, int* flag) {
   int bad = 0;
@@ -60,6 +66,7 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
   info->residual = 0.0;
   info->norm_two = 0.0;
   info->status = BLWS_OK;
+  info->restarts = 0;
   BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(Uout, sizeof(double) * m, 0, sizeof(double) * m, max_rank, s));
   BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(Vout, sizeof(double) * n, 0, sizeof(double) * n, max_rank, s));
   BLWS_TRY_CUDA(ctx, cudaMemsetAsync(thout, 0, sizeof(double) * max_rank, s));
@@ -166,10 +173,37 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
         a.w = w;
         a.k = std::max(1, std::min(k, N / std::max(sk, w)));
       }
-      // the warm block is read before U, V are overwritten, so in place is safe
-      BLWS_TRY(blws_run(ctx, s, Wop, a, Uw, m, Vw, n, sig, count_dev));
-      BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
-                                         cudaMemcpyDeviceToHost, s));
+      // the warm block is read before U, V are overwritten, so in place is safe.
+      // Two graph phases around the eigen-solver's host stage (graph.cuh): the
+      // block steps, then the Ritz lift and count with the count copied back
+      const int bw = std::max(a.r, a.w);
+      set_tau<<<1, 1, 0, s>>>(scal + SLOT_EPS, tau);
+      BLWS_CHECK_LAUNCH(ctx);
+      a.guard = ctx->cfg.guard > 0.0;
+      a.eps_dev = scal + SLOT_EPS;
+      // with the Ritz-residual guard, an inaccurate call runs again from the
+      // same start with one more block (at most twice)
+      for (int extra = 0;; ++extra) {
+        GraphKey ka;
+        ka.u(0x4D43u).u(1).u(m).u(n).u(nnz).p(rowptr).p(colidx).p(Wop.val).p(colptr).p(rowidx).p(perm);
+        ka.u(Wop.rl).p(Wop.Ul).p(Wop.sl).p(Wop.Vl).u(a.r).u(a.k).u(a.w).u(a.cold).u(a.standard).u(a.mixed);
+        ka.p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard).u(a.cold || bw > a.w ? a.draw : 0u);
+        BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) { return blws_run_a(ctx, q, Wop, a); }));
+        BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+        BLWS_TRY(graph_harvest(ctx));
+        if (!a.guard || extra == 2 || (a.k + 1) * bw > N || !(blws_guard_ratio(ctx, a) > ctx->cfg.guard)) break;
+        ++a.k;
+        ++info->restarts;
+      }
+      BLWS_TRY(blws_run_mid(ctx, s, Wop, a));
+      GraphKey kb;
+      kb.u(0x4D43u).u(2).u(m).u(n).u(a.r).u(a.k).u(a.w).u(a.mixed).p(Uw).p(Vw).p(sig);
+      BLWS_TRY(graph_phase(ctx, s, kb, [&](cudaStream_t q) -> blws_status {
+        BLWS_TRY(blws_run_b(ctx, q, Wop, a, Uw, m, Vw, n, sig, count_dev, scal + SLOT_EPS));
+        BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, scal, sizeof(double) * SLOT_MAX,
+                                           cudaMemcpyDeviceToHost, q));
+        return BLWS_OK;
+      }));
       BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
       c = *reinterpret_cast<int*>(ctx->host_pinned + SLOT_COUNT);
       if (*reinterpret_cast<int*>(ctx->host_pinned + SLOT_TCERR))
@@ -181,11 +215,17 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
     }
     if (c > max_rank)
       return ctx->fail(BLWS_EINVAL, "mc_solve: rank %d exceeds max_rank %d", c, max_rank);
-    thresholds_mc<<<1, 256, 0, s>>>(w, sig, tau, th);
-    BLWS_CHECK_LAUNCH(ctx);
-    // SDDMM on Omega: residual and update of the sparse values
-    BLWS_TRY(sddmm(ctx, s, m, n, c, rowptr, colidx, vals, Uw, m, th, Vw, n, delta, prox ? 1 : 0, y,
-                   scal + SLOT_NORM, Ut, Vt));
+    // thresholds and the SDDMM on Omega (residual and update of the sparse
+    // values): a third graph phase
+    GraphKey kc;
+    kc.u(0x4D43u).u(3).u(m).u(n).u(nnz).u(c).u(w).p(rowptr).p(colidx).p(vals).p(Uw).p(Vw).p(sig);
+    kc.p(y).p(Ut).p(Vt).d(delta).u(prox);
+    BLWS_TRY(graph_phase(ctx, s, kc, [&](cudaStream_t q) -> blws_status {
+      thresholds_mc<<<1, 256, 0, q>>>(w, sig, tau, scal + SLOT_EPS, th);
+      BLWS_CHECK_LAUNCH(ctx);
+      return sddmm(ctx, q, m, n, c, rowptr, colidx, vals, Uw, m, th, Vw, n, delta, prox ? 1 : 0, y,
+                   scal + SLOT_NORM, Ut, Vt);
+    }));
     double dx = 0.0, xnorm = 0.0;
     if (prox) {
       // ||X_{k+1} - X_k||_F^2 = sum th^2 + sum th_prev^2 - 2 tr(th U^T Up th_prev Vp^T V)

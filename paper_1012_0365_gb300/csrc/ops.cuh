@@ -50,6 +50,9 @@ blws_status sym_eig(Ctx* ctx, cudaStream_t s, int n, const double* T, double* la
 // fallback and the cluster re-solve, which launch and synchronise only when
 // they apply).  sym_eig = sym_eig_start, synchronise, sym_eig_finish.
 blws_status sym_eig_start(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z);
+// one double after the host copies of sym_eig_start (n): for a caller's own
+// value copied back with them
+double* sym_eig_host_extra(Ctx* ctx, int n);
 blws_status sym_eig_finish(Ctx* ctx, cudaStream_t s, int n, const double* T, double* lam, double* Z,
                            double eps);
 

@@ -308,6 +308,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   info->residual = 0.0;
   info->status = BLWS_OK;
   info->mixed_iters = 0;
+  info->restarts = 0;
   if (d_norm == 0.0) {  // D = 0: A = E = 0
     BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(A, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
     BLWS_TRY_CUDA(ctx, cudaMemset2DAsync(E, sizeof(double) * ld, 0, sizeof(double) * m, n, s));
@@ -427,30 +428,39 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       Wop.Oc = &Oc;
     }
     const int bw = std::max(a.r, a.w);
-    // phase 1: this iteration's planes of W, the start block, the k block
-    // steps and the device stage of the EVD of T_k
-    GraphKey ka;
-    ka.u(0x52504341u).u(1).u(m).u(n).u(ld).p(W).u(mixed).u(fp64tc).u(a.r).u(a.k).u(a.w);
-    ka.u(a.cold).u(a.standard).p(Uw).p(Vw).u(ctx->cfg.seed);
-    ka.u(a.cold || bw > a.w ? a.draw : 0u);  // the generator stream matters only for drawn columns
-    BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) -> blws_status {
-      if (mixed) {
-        BLWS_TRY(tc_planes_from_rows(ctx, q, W, ld, m, n, Wr));
-        BLWS_TRY(tc_planes_from_cols(ctx, q, W, ld, 0, m, n, Wc));
-      }
-      if (fp64tc) {  // FP64-equivalent digit planes of this iteration's W
-        BLWS_TRY(oz_planes_from_rows(ctx, q, W, ld, m, n, Or));
-        BLWS_TRY(oz_planes_from_cols(ctx, q, W, ld, 0, m, n, Oc));
-      }
-      return blws_run_a(ctx, q, Wop, a);
-    }));
-    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
-    BLWS_TRY(graph_harvest(ctx));
-    BLWS_TRY(blws_run_mid(ctx, s, Wop, a));  // the EVD's host stage
     const double mu_next = std::min(mu * p.rho, mu_bar);
     set_scalars<<<1, 1, 0, s>>>(scal + SLOT_EPS, eps, mu, mu_next);
     BLWS_CHECK_LAUNCH(ctx);
     const double* dyn = scal + SLOT_EPS;
+    a.guard = ctx->cfg.guard > 0.0;
+    a.eps_dev = dyn;
+    // phase 1: this iteration's planes of W, the start block, the k block
+    // steps and the device stage of the EVD of T_k.  With the Ritz-residual
+    // guard, a call whose pairs above eps are not yet accurate is run again
+    // from the same start with one more block (at most twice)
+    for (int extra = 0;; ++extra) {
+      GraphKey ka;
+      ka.u(0x52504341u).u(1).u(m).u(n).u(ld).p(W).u(mixed).u(fp64tc).u(a.r).u(a.k).u(a.w);
+      ka.u(a.cold).u(a.standard).p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard);
+      ka.u(a.cold || bw > a.w ? a.draw : 0u);  // the generator stream matters only for drawn columns
+      BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) -> blws_status {
+        if (mixed) {
+          BLWS_TRY(tc_planes_from_rows(ctx, q, W, ld, m, n, Wr));
+          BLWS_TRY(tc_planes_from_cols(ctx, q, W, ld, 0, m, n, Wc));
+        }
+        if (fp64tc) {  // FP64-equivalent digit planes of this iteration's W
+          BLWS_TRY(oz_planes_from_rows(ctx, q, W, ld, m, n, Or));
+          BLWS_TRY(oz_planes_from_cols(ctx, q, W, ld, 0, m, n, Oc));
+        }
+        return blws_run_a(ctx, q, Wop, a);
+      }));
+      BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+      BLWS_TRY(graph_harvest(ctx));
+      if (!a.guard || extra == 2 || (a.k + 1) * bw > N || !(blws_guard_ratio(ctx, a) > ctx->cfg.guard)) break;
+      ++a.k;
+      ++info->restarts;
+    }
+    BLWS_TRY(blws_run_mid(ctx, s, Wop, a));  // the EVD's host stage
     // FP64-equivalent mode: A = (U diag(theta)) V^T over the sv computed pairs
     // (theta is zero past the count) as a digit-plane product, when it is
     // large enough for gemm to route it there

@@ -570,13 +570,34 @@ template <int kCl>
 __host__ __device__ constexpr int rows_per_cta(int n) { return (n + kCl - 1) / kCl; }
 
 
-// smallest cluster whose share of the full matrix fits one CTA (0: none)
+// Shared memory of the kernel below: the vectors (n float4), p of the local
+// rows, and the rows themselves -- sized for the larger of the cluster phase
+// (R rows of n) and the single-CTA phase (a trailing block of at most
+// kRowsSwitchM squared).  The cluster phase runs while the trailing block is
+// wider than kRowsSwitchM, on at least BLWS_TRI_MIN_CL CTAs.  Measured in the
+// 2000 x 2000 rank-100 FP64-equivalent solve (T_k of 303): 96 and 4 CTAs took
+// 135.8-136.0 ms per solve, 232 on the 2 CTAs whose shares fit 139.9 ms, the
+// other pairs tried (32-160, 2-8 CTAs) in between.
+#ifndef BLWS_TRI_SWITCH_M
+#define BLWS_TRI_SWITCH_M 96
+#endif
+constexpr int kRowsSwitchM = BLWS_TRI_SWITCH_M;
+static_assert(kRowsSwitchM >= 2, "the single-CTA phase holds at least the last 2 x 2 block");
+#ifndef BLWS_TRI_MIN_CL
+#define BLWS_TRI_MIN_CL 4
+#endif
+
+// CTAs of the reduction by rows: the smallest cluster whose share of the full
+// matrix fits one CTA (0: none), and at least BLWS_TRI_MIN_CL when a cluster
+// phase runs at all (n above the switch point)
 inline int rows_cluster(int n) {
-  if (n <= kRowsMaxN1) return 1;
-  if (n <= kRowsMaxN2) return 2;
-  if (n <= kRowsMaxN4) return 4;
-  if (n <= kRowsMaxN8) return 8;
-  return 0;
+  int c = 0;
+  if (n <= kRowsMaxN1) c = 1;
+  else if (n <= kRowsMaxN2) c = 2;
+  else if (n <= kRowsMaxN4) c = 4;
+  else if (n <= kRowsMaxN8) c = 8;
+  if (c && n > kRowsSwitchM) c = std::max(c, BLWS_TRI_MIN_CL);
+  return c;
 }
 
 // the pending rank-2 term pv_i pw_j + pw_i pv_j of element (i, j), rounded the
@@ -604,12 +625,6 @@ __device__ __forceinline__ P* rows_remote(P* p, int r) {
     return p;
   }
 }
-
-// Shared memory of the kernel below: the vectors (n float4), p of the local
-// rows, and the rows themselves -- sized for the larger of the cluster phase
-// (R rows of n) and the single-CTA phase (a trailing block of at most
-// kRowsSwitchM squared).
-constexpr int kRowsSwitchM = 232;
 
 template <int kCl>
 int rows_smem_bytes(int n) {

@@ -102,3 +102,49 @@ def test_graphs_off_by_environment(torch_mod, monkeypatch):
     run(ctx, torch_mod, D, tol=1e-8)
     run(ctx, torch_mod, D, tol=1e-8)
     assert ctx.graph_stats() == (0, 0)
+
+
+@pytest.mark.parametrize("variant,m,n,r,sdr,seed,kw", [
+    (0, 300, 300, 10, 6, 0, {"tol": 1e-6}),
+    (0, 257, 190, 5, 5, 1, {"tol": 1e-6}),
+    (1, 120, 120, 4, 6, 3, {"tol": 1e-3, "max_rank": 120}),  # continuation: tau moves
+])
+def test_mc_graphs_bit_identical_to_direct_launches(torch_mod, variant, m, n, r, sdr, seed, kw):
+    """The matrix-completion solver's three phases (block steps; Ritz lift and
+    count; thresholds and SDDMM) replayed as graphs: the same factors as with
+    direct launches, for the SVT host and the proximal form (whose tau moves)."""
+    from paper_1012_0365_gb300 import blws
+    P = syn.mc_problem(m, n, r, sdr * r * (m + n - r) / (m * n), seed=seed)
+    out = []
+    for graphs in (1, 0):
+        ctx = blws.Context(graphs=graphs)
+        U, th, V, info = ctx.mc_solve(m, n, torch_mod.from_numpy(P["rowptr"]).cuda(),
+                                      torch_mod.from_numpy(P["cols"]).cuda(),
+                                      torch_mod.from_numpy(P["vals"]).cuda(),
+                                      max_rank=kw.get("max_rank", 60), variant=variant, tol=kw["tol"],
+                                      max_iter=3000, allow_noconv=True)
+        torch_mod.cuda.synchronize()
+        out.append((U.cpu().numpy(), th.cpu().numpy(), V.cpu().numpy(), info, ctx.graph_stats()))
+    (Ug, tg, Vg, ig, sg), (Ud, td, Vd, idd, sd) = out
+    assert (ig["status"], ig["iters"], ig["rank"]) == (idd["status"], idd["iters"], idd["rank"])
+    assert ig["iters"] > 10
+    assert np.array_equal(Ug, Ud) and np.array_equal(tg, td) and np.array_equal(Vg, Vd)
+    assert sg[1] > 0 and sd == (0, 0)
+
+
+def test_guard_off_threshold_is_bit_identical_and_forced_restarts_match_oracle(torch_mod):
+    """The Ritz-residual guard only adds work on dead buffers until it fires:
+    with a threshold no pair reaches, a solve is bit-identical to one without
+    it; with a threshold every pair exceeds, each call runs again with up to
+    two more blocks, and the solve still reaches the oracle's optimum."""
+    from paper_1012_0365_gb300 import blws
+    D = syn.rpca_problem(220, 180, 9, 0.05, amp=50.0, seed=7)[0]
+    A0, E0, i0 = run(blws.Context(), torch_mod, D, tol=1e-10)
+    A1, E1, i1 = run(blws.Context(guard=1e6), torch_mod, D, tol=1e-10)
+    assert i1["restarts"] == 0 and i0["restarts"] == 0
+    assert np.array_equal(A0, A1) and np.array_equal(E0, E1)
+    A2, E2, i2 = run(blws.Context(guard=1e-300), torch_mod, D, tol=1e-10)
+    assert i2["restarts"] >= i2["iters"]
+    ref = oracle.rpca_ialm_full(D, tol=1e-10)
+    assert np.linalg.norm(A2 - ref["A"]) / np.linalg.norm(ref["A"]) < 1e-6
+    assert np.linalg.norm(E2 - ref["E"]) / np.linalg.norm(ref["E"]) < 1e-6
