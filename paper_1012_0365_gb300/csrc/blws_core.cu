@@ -204,7 +204,7 @@ blws_status blws_run_a(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsA
     BLWS_TRY(gemm(ctx, s, false, false, N, b, (l + 1 - c0r) * b, -1.0, Q + (size_t)c0r * b * N, N,
                   T + (size_t)c0r * b + (size_t)l * b * kb, kb, 1.0, P, N, f32));
     // second projection against the recurrence's blocks (all blocks when cold)
-    const int c0 = a.cold ? 0 : std::max(l - 1, 0);
+    const int c0 = a.cold || a.reorth ? 0 : std::max(l - 1, 0);
     const int cols = (l + 1 - c0) * b;
     const double* base = Q + (size_t)c0 * b * N;
     BLWS_TRY(gemm(ctx, s, true, false, cols, b, N, 1.0, base, N, P, N, 0.0, C, cols, f32));

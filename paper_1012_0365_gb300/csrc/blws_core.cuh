@@ -58,6 +58,10 @@ struct BlwsArgs {
   // eigen-solver's host stage reads (blws_guard_ratio)
   bool guard = false;
   const double* eps_dev = nullptr;
+  // second projection of every residual against all earlier blocks, as on a
+  // cold start (a call repeated by the guard with more blocks: the local
+  // recurrence loses orthogonality to converged directions as k grows)
+  bool reorth = false;
 };
 
 // the guard's ratio of the last stage (a) with a.guard, once s is synchronised

@@ -187,12 +187,13 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
         GraphKey ka;
         ka.u(0x4D43u).u(1).u(m).u(n).u(nnz).p(rowptr).p(colidx).p(Wop.val).p(colptr).p(rowidx).p(perm);
         ka.u(Wop.rl).p(Wop.Ul).p(Wop.sl).p(Wop.Vl).u(a.r).u(a.k).u(a.w).u(a.cold).u(a.standard).u(a.mixed);
-        ka.p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard).u(a.cold || bw > a.w ? a.draw : 0u);
+        ka.p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard).u(a.reorth).u(a.cold || bw > a.w ? a.draw : 0u);
         BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) { return blws_run_a(ctx, q, Wop, a); }));
         BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
         BLWS_TRY(graph_harvest(ctx));
         if (!a.guard || extra == 2 || (a.k + 1) * bw > N || !(blws_guard_ratio(ctx, a) > ctx->cfg.guard)) break;
         ++a.k;
+        a.reorth = true;
         ++info->restarts;
       }
       BLWS_TRY(blws_run_mid(ctx, s, Wop, a));

@@ -441,7 +441,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     for (int extra = 0;; ++extra) {
       GraphKey ka;
       ka.u(0x52504341u).u(1).u(m).u(n).u(ld).p(W).u(mixed).u(fp64tc).u(a.r).u(a.k).u(a.w);
-      ka.u(a.cold).u(a.standard).p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard);
+      ka.u(a.cold).u(a.standard).p(Uw).p(Vw).u(ctx->cfg.seed).u(a.guard).u(a.reorth);
       ka.u(a.cold || bw > a.w ? a.draw : 0u);  // the generator stream matters only for drawn columns
       BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) -> blws_status {
         if (mixed) {
@@ -458,6 +458,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       BLWS_TRY(graph_harvest(ctx));
       if (!a.guard || extra == 2 || (a.k + 1) * bw > N || !(blws_guard_ratio(ctx, a) > ctx->cfg.guard)) break;
       ++a.k;
+      a.reorth = true;
       ++info->restarts;
     }
     BLWS_TRY(blws_run_mid(ctx, s, Wop, a));  // the EVD's host stage
