@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "ops.cuh"
+#include "tune.cuh"
 
 namespace blws {
 
@@ -240,69 +241,9 @@ blws_status launch_choice(Ctx* ctx, cudaStream_t s, int tile, int target, int M,
 // noise does not move products off the rule for nothing.  Inside a graph
 // capture no timing can run: an untuned bucket there breaks the capture, and
 // the phase runs directly (and tunes).
-struct TuneKey {
-  int v[8];
-  bool operator<(const TuneKey& o) const {
-    for (int i = 0; i < 8; ++i)
-      if (v[i] != o.v[i]) return v[i] < o.v[i];
-    return false;
-  }
-};
-struct TuneChoice {
-  int tile, split;
-};
-std::mutex g_tune_mutex;
-std::map<TuneKey, TuneChoice> g_tune;
-bool g_tune_loaded = false;
-
-int tune_bucket(int x) {
-  if (x <= 32) return x;
-  int p = 32;
-  while (2 * p < x) p *= 2;  // p < x <= 2p
-  const int step = p / 4;
-  return ceil_div(x, step) * step;
-}
-
 TuneKey tune_key(const Ctx* ctx, int ct_bytes, bool ta, bool tb, bool sym, int M, int N, int K) {
-  return TuneKey{{ctx->sms, ct_bytes, ta, tb, sym, tune_bucket(M), tune_bucket(N), tune_bucket(K)}};
-}
-
-// (the mutex is held)
-void tune_load() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
-  const char* path = std::getenv("BLWS_TUNE_FILE");
-  if (!path || !*path) return;
-  FILE* f = std::fopen(path, "r");
-  if (!f) return;
-  TuneKey k;
-  TuneChoice c;
-  while (std::fscanf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", &k.v[0], &k.v[1], &k.v[2], &k.v[3],
-                     &k.v[4], &k.v[5], &k.v[6], &k.v[7], &c.tile, &c.split) == 10)
-    if (c.tile >= 0 && c.tile < 5 && c.split >= 0 && c.split <= 3) g_tune[k] = c;
-  std::fclose(f);
-}
-
-bool tune_lookup(const TuneKey& k, TuneChoice* c) {
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  tune_load();
-  auto it = g_tune.find(k);
-  if (it == g_tune.end()) return false;
-  *c = it->second;
-  return true;
-}
-
-void tune_store(const TuneKey& k, const TuneChoice& c) {
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  tune_load();
-  if (!g_tune.emplace(k, c).second) return;  // another context tuned it first
-  const char* path = std::getenv("BLWS_TUNE_FILE");
-  if (!path || !*path) return;
-  if (FILE* f = std::fopen(path, "a")) {
-    std::fprintf(f, "gemm %d %d %d %d %d %d %d %d %d %d\n", k.v[0], k.v[1], k.v[2], k.v[3], k.v[4],
-                 k.v[5], k.v[6], k.v[7], c.tile, c.split);
-    std::fclose(f);
-  }
+  return TuneKey{{ctx->sms, ct_bytes == 8 ? kTuneF64 : kTuneF32, ta, tb, sym, tune_bucket(M), tune_bucket(N),
+                  tune_bucket(K)}};
 }
 
 template <typename CT, bool TA, bool TB>
@@ -342,7 +283,7 @@ blws_status tune_shape(Ctx* ctx, cudaStream_t s, int M, int N, int K, bool sym, 
         st = ctx->fail(BLWS_ECUDA, "autotuner timing");
         break;
       }
-      if (t == rule.tile && q == rule.split) rule_ms = ms;
+      if (t == rule.a && q == rule.b) rule_ms = ms;
       if (best_ms < 0.0f || ms < best_ms) {
         best_ms = ms;
         best = TuneChoice{t, q};
@@ -355,12 +296,6 @@ blws_status tune_shape(Ctx* ctx, cudaStream_t s, int M, int N, int K, bool sym, 
   tune_store(key, best);
   *out = best;
   return BLWS_OK;
-}
-
-size_t tune_count() {
-  std::lock_guard<std::mutex> lock(g_tune_mutex);
-  tune_load();
-  return g_tune.size();
 }
 
 template <typename CT, bool TA, bool TB>
@@ -377,7 +312,7 @@ blws_status gemm_t(Ctx* ctx, cudaStream_t s, int M, int N, int K, double alpha, 
       BLWS_TRY((tune_shape<CT, TA, TB>(ctx, s, M, N, K, sym, key, &c)));
     }
   }
-  return launch_choice<CT, TA, TB>(ctx, s, c.tile, split_target(ctx, c.split), M, N, K, alpha, A, lda, B,
+  return launch_choice<CT, TA, TB>(ctx, s, c.a, split_target(ctx, c.b), M, N, K, alpha, A, lda, B,
                                    ldb, beta, C, ldc, sym);
 }
 
@@ -659,5 +594,72 @@ extern "C" blws_status blws_apply_noalloc(const double* W, int m, int n, int ldw
     return BLWS_ECUDA;
   return BLWS_OK;
 }
+
+// ------------------------------------------------------ autotuner table --
+namespace blws {
+namespace {
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+bool tune_valid(const TuneKey& k, const TuneChoice& c) {
+  if (k.v[1] == kTuneDigits) return c.a >= 1 && c.a <= 4096 && c.b == 0;
+  return (k.v[1] == kTuneF32 || k.v[1] == kTuneF64) && c.a >= 0 && c.a < 5 && c.b >= 0 && c.b <= 3;
+}
+
+// (the mutex is held)
+void tune_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = std::getenv("BLWS_TUNE_FILE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneChoice c;
+  while (std::fscanf(f, "tune %d %d %d %d %d %d %d %d %d %d\n", &k.v[0], &k.v[1], &k.v[2], &k.v[3],
+                     &k.v[4], &k.v[5], &k.v[6], &k.v[7], &c.a, &c.b) == 10)
+    if (tune_valid(k, c)) g_tune[k] = c;
+  std::fclose(f);
+}
+}  // namespace
+
+int tune_bucket(int x) {
+  if (x <= 32) return x;
+  int p = 32;
+  while (2 * p < x) p *= 2;  // p < x <= 2p
+  const int step = p / 4;
+  return ceil_div(x, step) * step;
+}
+
+bool tune_lookup(const TuneKey& k, TuneChoice* c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  auto it = g_tune.find(k);
+  if (it == g_tune.end()) return false;
+  *c = it->second;
+  return true;
+}
+
+void tune_store(const TuneKey& k, const TuneChoice& c) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  if (!g_tune.emplace(k, c).second) return;  // another context tuned it first
+  const char* path = std::getenv("BLWS_TUNE_FILE");
+  if (!path || !*path) return;
+  if (FILE* f = std::fopen(path, "a")) {
+    std::fprintf(f, "tune %d %d %d %d %d %d %d %d %d %d\n", k.v[0], k.v[1], k.v[2], k.v[3], k.v[4],
+                 k.v[5], k.v[6], k.v[7], c.a, c.b);
+    std::fclose(f);
+  }
+}
+
+size_t tune_count() {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  tune_load();
+  return g_tune.size();
+}
+
+}  // namespace blws
 
 extern "C" size_t blws_tune_count(void) { return blws::tune_count(); }

@@ -26,6 +26,7 @@
 
 #include "ops.cuh"
 #include "tc_ptx.cuh"
+#include "tune.cuh"
 
 namespace blws {
 
@@ -694,44 +695,100 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
   else BLWS_TRY(oz_planes_from_rows(ctx, s, B, ldb, N, K, OzPlanes{db, eb, npad, K, ldk}));
   const int tiles = ceil_div(M, kOzBM);
   const int kblocks = ceil_div(K, kOzBK);
-  const int sp = oz_pick_splits(ctx->sms, tiles * ngroups, kblocks);
-  const int kchunk = ceil_div(kblocks, sp) * kOzBK;
-  const int splits = ceil_div(K, kchunk);
-  float2* part = nullptr;
-  BLWS_TRY(ctx->get(BUF_TC_PART, (size_t)splits * npad * tiles * kOzBM * sizeof(float2), (void**)&part));
-  OzJobs jobs;
-  memset(&jobs, 0, sizeof(jobs));
-  OzJob& J = jobs.job[0];
-  BLWS_TRY(oz_encode(ctx, &J.a, da, M, M, K, ldk, kOzBM));
-  // op(B) columns past N: zero digits from the copy's out-of-bounds fill
-  BLWS_TRY(oz_encode(ctx, &J.b, db, N, npad, K, ldk, kOzBN));
-  J.ea = ea;
-  J.eb = eb;
-  J.part = part;
-  J.M = M;
-  J.K = K;
-  J.tiles = tiles;
-  J.ngroups = ngroups;
-  J.splits = splits;
-  J.kchunk = kchunk;
-  J.Mpad = tiles * kOzBM;
-  J.npad = npad;
-  jobs.job[1] = J;  // unused: every block belongs to job 0
   double* scal = nullptr;
   BLWS_TRY(ctx->get(BUF_SCAL, SLOT_MAX, &scal));
-  jobs.blocks0 = tiles * ngroups * splits;
-  jobs.N = N;
-  jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
   const int smem = (int)oz_smem_bytes();
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_OZ, (const void*)oz_kernel, smem));
-  oz_kernel<<<jobs.blocks0, kOzThreads, smem, s>>>(jobs);
-  BLWS_CHECK_LAUNCH(ctx);
-  const size_t tot = (size_t)M * N;
-  const int G = oz_lanes(ctx->sms, tot, splits);
-  oz_reduce<<<(int)std::min<size_t>((tot * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
-      M, N, npad, splits, J.Mpad, part, ea, eb, C, ldc, alpha, beta, sym && M == N && beta == 0.0 ? 1 : 0, G);
-  BLWS_CHECK_LAUNCH(ctx);
-  return BLWS_OK;
+  // the digit kernel over `sp` splits of K and the FP64 reduction into C
+  auto launch = [&](int sp, double* Cout, int ldo, double bet) -> blws_status {
+    const int kchunk = ceil_div(kblocks, sp) * kOzBK;
+    const int splits = ceil_div(K, kchunk);
+    float2* part = nullptr;
+    BLWS_TRY(ctx->get(BUF_TC_PART, (size_t)splits * npad * tiles * kOzBM * sizeof(float2), (void**)&part));
+    OzJobs jobs;
+    memset(&jobs, 0, sizeof(jobs));
+    OzJob& J = jobs.job[0];
+    BLWS_TRY(oz_encode(ctx, &J.a, da, M, M, K, ldk, kOzBM));
+    // op(B) columns past N: zero digits from the copy's out-of-bounds fill
+    BLWS_TRY(oz_encode(ctx, &J.b, db, N, npad, K, ldk, kOzBN));
+    J.ea = ea;
+    J.eb = eb;
+    J.part = part;
+    J.M = M;
+    J.K = K;
+    J.tiles = tiles;
+    J.ngroups = ngroups;
+    J.splits = splits;
+    J.kchunk = kchunk;
+    J.Mpad = tiles * kOzBM;
+    J.npad = npad;
+    jobs.job[1] = J;  // unused: every block belongs to job 0
+    jobs.blocks0 = tiles * ngroups * splits;
+    jobs.N = N;
+    jobs.err = reinterpret_cast<int*>(scal + SLOT_TCERR);
+    oz_kernel<<<jobs.blocks0, kOzThreads, smem, s>>>(jobs);
+    BLWS_CHECK_LAUNCH(ctx);
+    const size_t tot = (size_t)M * N;
+    const int G = oz_lanes(ctx->sms, tot, splits);
+    oz_reduce<<<(int)std::min<size_t>((tot * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
+        M, N, npad, splits, J.Mpad, part, ea, eb, Cout, ldo, alpha, bet,
+        sym && M == N && bet == 0.0 ? 1 : 0, G);
+    BLWS_CHECK_LAUNCH(ctx);
+    return BLWS_OK;
+  };
+  int sp = oz_pick_splits(ctx->sms, tiles * ngroups, kblocks);
+  if (ctx->cfg.tune) {
+    // the split count from timing: the wave model above takes a fixed cost per
+    // CTA, which the small products (b x b outputs, K in the thousands) miss
+    // most; candidates are powers of two up to one K block per split and the
+    // model's choice, each timed with its reduction into a scratch C
+    const TuneKey key{{ctx->sms, kTuneDigits, ta, tb, sym, tune_bucket(M), tune_bucket(N), tune_bucket(K)}};
+    TuneChoice c;
+    if (tune_lookup(key, &c)) {
+      sp = std::min(c.a, kblocks);
+    } else if (ctx->capturing) {
+      ctx->capture_broken = true;
+      return ctx->fail(BLWS_ECUDA, "untuned digit-plane product shape inside a graph capture");
+    } else {
+      double* Cs = nullptr;
+      BLWS_TRY(ctx->get(BUF_TUNE, (size_t)M * N, &Cs));
+      std::vector<int> cand;
+      for (int q = 1; q <= kblocks; q *= 2) cand.push_back(q);
+      cand.push_back(sp);
+      cudaEvent_t e0, e1;
+      BLWS_TRY_CUDA(ctx, cudaEventCreate(&e0));
+      if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ctx->fail(BLWS_ECUDA, "autotuner events");
+      }
+      float best_ms = -1.0f, rule_ms = -1.0f;
+      int best = sp;
+      blws_status st = BLWS_OK;
+      for (size_t i = 0; i < cand.size() && st == BLWS_OK; ++i) {
+        st = launch(cand[i], Cs, M, 0.0);  // warm-up
+        if (st != BLWS_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) st = ctx->fail(BLWS_ECUDA, "autotuner event");
+        for (int r = 0; r < 3 && st == BLWS_OK; ++r) st = launch(cand[i], Cs, M, 0.0);
+        float ms = 0.0f;
+        if (st == BLWS_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          st = ctx->fail(BLWS_ECUDA, "autotuner timing");
+        if (st != BLWS_OK) break;
+        if (cand[i] == sp) rule_ms = ms;
+        if (best_ms < 0.0f || ms < best_ms) {
+          best_ms = ms;
+          best = cand[i];
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      BLWS_TRY(st);
+      if (!(best_ms < 0.95f * rule_ms)) best = sp;  // keep the model's choice unless 5% slower
+      tune_store(key, TuneChoice{best, 0});
+      sp = best;
+    }
+  }
+  return launch(sp, C, ldc, beta);
 }
 
 }  // namespace blws

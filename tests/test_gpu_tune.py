@@ -46,11 +46,15 @@ def test_tuned_solve_matches_oracle_and_is_recorded(torch_mod, tmp_path, monkeyp
     after = blws.Context.tune_count()
     assert after > before
     if before == 0:  # this process read the file first: every choice went to it
-        lines = [l for l in path.read_text().splitlines() if l.startswith("gemm ")]
+        lines = [l for l in path.read_text().splitlines() if l.startswith("tune ")]
         assert len(lines) == after
         for l in lines:
             f = [int(x) for x in l.split()[1:]]
-            assert len(f) == 10 and 0 <= f[8] < 5 and 0 <= f[9] <= 3
+            assert len(f) == 10
+            if f[1] == 100:  # digit-plane product: its K split count
+                assert f[8] >= 1 and f[9] == 0
+            else:  # CUDA-core product: tile shape and split target
+                assert 0 <= f[8] < 5 and 0 <= f[9] <= 3
 
 
 def test_tuned_graphs_bit_identical(torch_mod):
