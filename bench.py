@@ -61,9 +61,9 @@ TENSOR_MMAS = {"fp64tc": 28, "mixed": 3}
 # DRAM bytes (read + write) of one launch of the digit-plane kernel for the
 # 2000 x 2000 product at b = 101 (2 K splits, 128 CTAs), from one ncu capture of
 # the current kernel (bench.py --profile-apply --precision fp64tc)
-OZ_TRAFFIC = {"rpca_2000x2000_r100": 120576256 + 3564544}
+OZ_TRAFFIC = {"rpca_2000x2000_r100": 120623616 + 3644672}
 OZ_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one oz_kernel launch of blws_apply "
-                     "(b=101), bench.py --profile-apply --precision fp64tc")
+                     "(b=101, the eight-drain-warp kernel), bench.py --profile-apply --precision fp64tc")
 
 
 def measured_peaks():

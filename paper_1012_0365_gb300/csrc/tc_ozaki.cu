@@ -40,7 +40,12 @@ constexpr int kOzBN = 64;        // columns per CTA (one accumulator level = 64 
 constexpr int kOzBK = 32;        // K block: 32 BF16 = one 64-byte swizzle row
 constexpr int kOzChunk = 256;    // exact FP32 sums: at most 256 K terms per level between drains
 constexpr int kOzStages = 2;
-constexpr int kOzThreads = 256;   // warp 0 TMA, warp 1 MMA, warp 2 TMEM, warps 4-7 drain/epilogue
+// drain warps: two per tensor-memory lane quarter, each draining half of the
+// 64 columns (eight warps halve the drain that separates a chunk's MMAs from
+// the next chunk's; four would need 2 x 64 accumulators per thread)
+constexpr int kOzDrainWarps = 8;
+constexpr int kOzDrainCols = kOzBN * 4 / kOzDrainWarps;
+constexpr int kOzThreads = 128 + 32 * kOzDrainWarps;  // warp 0 TMA, warp 1 MMA, warp 2 TMEM, 4.. drain
 constexpr int kOzLevels = kOzS;  // levels L = 2 .. S + 1
 constexpr int kOzPairs = kOzS * (kOzS + 1) / 2;  // pairs (t, u) with t + u <= S + 1
 
@@ -137,7 +142,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&chunk_bar, 1);
-    for (int L = 0; L < kOzLevels; ++L) mbar_init(&level_bar[L], 128);  // the four drain warps
+    for (int L = 0; L < kOzLevels; ++L) mbar_init(&level_bar[L], 32 * kOzDrainWarps);  // every drain thread
     fail_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -229,12 +234,14 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
     }
     return;
   }
-  // drain (warps 4-7; warp w reads tensor-memory lanes 32 (w - 4) ..): every
-  // chunk, levels -> double-FP32 accumulators, one row per thread
-  const int q = warp - 4;
-  float hi[kOzBN], lo[kOzBN];
+  // drain (warps 4..: warp w reads tensor-memory lanes 32 ((w - 4) mod 4) ..,
+  // columns kOzDrainCols ((w - 4) / 4) ..): every chunk, levels -> double-FP32
+  // accumulators, one row per thread
+  const int q = (warp - 4) & 3;
+  const int cb = ((warp - 4) >> 2) * kOzDrainCols;
+  float hi[kOzDrainCols], lo[kOzDrainCols];
 #pragma unroll
-  for (int j = 0; j < kOzBN; ++j) {
+  for (int j = 0; j < kOzDrainCols; ++j) {
     hi[j] = 0.0f;
     lo[j] = 0.0f;
   }
@@ -248,11 +255,11 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
 #pragma unroll 1
     for (int L = 2; L <= kOzS + 1; ++L) {
       const float scale = __uint_as_float((uint32_t)(127 - 7 * L) << 23);  // 2^(-7 L), exact
-      float v[kOzBN];
+      float v[kOzDrainCols];
 #pragma unroll
-      for (int c0 = 0; c0 < kOzBN; c0 += 16) {
+      for (int c0 = 0; c0 < kOzDrainCols; c0 += 16) {
         float w16[16];
-        tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * kOzBN + c0), w16);
+        tmem_ld16(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)((L - 2) * kOzBN + cb + c0), w16);
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[c0 + j] = w16[j];
       }
@@ -260,7 +267,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
       tc_fence_before();
       mbar_arrive(&level_bar[L - 2]);
 #pragma unroll
-      for (int j = 0; j < kOzBN; ++j) two_sum_acc(hi[j], lo[j], v[j] * scale);
+      for (int j = 0; j < kOzDrainCols; ++j) two_sum_acc(hi[j], lo[j], v[j] * scale);
     }
   }
   if (ok && !fail_sh) {
@@ -271,8 +278,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_kernel(const __grid_constant
     if (row < J.M) {
       float2* out = J.part + (size_t)split * J.npad * J.Mpad;
 #pragma unroll
-      for (int j = 0; j < kOzBN; ++j) {
-        const int col = col0 + j;
+      for (int j = 0; j < kOzDrainCols; ++j) {
+        const int col = col0 + cb + j;
         if (col < jobs.N) out[(size_t)col * J.Mpad + row] = make_float2(hi[j], lo[j]);
       }
     }
