@@ -322,7 +322,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
   Dop.ldw = ld;
   double norm_two = 0.0;
   // ||D||_2 with FP64-equivalent products where the context has them (and in
-  // the mixed mode, whose TF32 products could not resolve it to 1e-13): the
+  // the mixed mode, whose TF32 products could not resolve it to 1e-10): the
   // digit planes of D are built once for all its passes
   const bool norm_oz = ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->cfg.precision == BLWS_PREC_MIXED;
   OzPlanes Dr{}, Dc{};
@@ -334,7 +334,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
     Dop.Oc = &Dc;
     ctx->oz_tail = true;  // the block products of the norm estimate too (reset below)
   }
-  const blws_status nst = spectral_norm(ctx, s, Dop, &norm_two, norm_oz ? 1e-13 : 1e-14);
+  const blws_status nst = spectral_norm(ctx, s, Dop, &norm_two);
   ctx->oz_tail = false;
   BLWS_TRY(nst);
   info->norm_two = norm_two;
