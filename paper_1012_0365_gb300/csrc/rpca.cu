@@ -231,6 +231,20 @@ __global__ void set_scalars(double* slot, double eps, double mu, double mu_next)
 
 }  // namespace
 
+// everything of an operator the launches of a BLWS call depend on (graph keys)
+void key_operator(GraphKey& k, const Operator& op) {
+  k.u(op.m).u(op.n).u(op.sym).p(op.W).u(op.ldw).u(op.nnz).p(op.rowptr).p(op.colidx).p(op.val);
+  k.p(op.colptr).p(op.rowidx).p(op.perm).u(op.rl).p(op.Ul).p(op.sl).p(op.Vl);
+  for (const OzPlanes* o : {op.Or, op.Oc}) {
+    k.p(o);
+    if (o) k.p(o->d).p(o->e).u(o->rows).u(o->inner).u(o->ld);
+  }
+  for (const TcPlanes* t : {op.Wr, op.Wc}) {
+    k.p(t);
+    if (t) k.p(t->hi).p(t->lo).u(t->rows).u(t->inner).u(t->ld);
+  }
+}
+
 blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* out_host, double stable) {
   // block Lanczos from a seeded block, restarted from its own Ritz vectors
   // (warm start) until the leading Ritz value stops moving
@@ -257,8 +271,23 @@ blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* 
       a.ldv0 = op.n;
       a.w = r;
     }
-    BLWS_TRY(blws_run(ctx, s, op, a, U, op.m, V, op.n, sig, reinterpret_cast<int*>(scal + SLOT_COUNT)));
-    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, sig, sizeof(double), cudaMemcpyDeviceToHost, s));
+    // the passes after the first repeat the same launches: graph phases as in
+    // the solvers' outer iterations (graph.cuh)
+    GraphKey ka;
+    ka.u(0x4E524Du).u(1).u(a.r).u(a.k).u(a.w).u(a.cold).p(U).p(V).p(sig).u(ctx->cfg.seed).u(a.draw);
+    key_operator(ka, op);
+    GraphKey kb = ka;
+    kb.v[1] = 2;
+    BLWS_TRY(graph_phase(ctx, s, ka, [&](cudaStream_t q) { return blws_run_a(ctx, q, op, a); }));
+    BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
+    BLWS_TRY(graph_harvest(ctx));
+    BLWS_TRY(blws_run_mid(ctx, s, op, a));
+    BLWS_TRY(graph_phase(ctx, s, kb, [&](cudaStream_t q) -> blws_status {
+      BLWS_TRY(blws_run_b(ctx, q, op, a, U, op.m, V, op.n, sig, reinterpret_cast<int*>(scal + SLOT_COUNT),
+                          nullptr));
+      BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(ctx->host_pinned, sig, sizeof(double), cudaMemcpyDeviceToHost, q));
+      return BLWS_OK;
+    }));
     BLWS_TRY_CUDA(ctx, cudaStreamSynchronize(s));
     cur = ctx->host_pinned[0];
     if (fabs(cur - prev) <= stable * fabs(cur)) break;
