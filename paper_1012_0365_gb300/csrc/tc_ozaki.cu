@@ -365,18 +365,27 @@ __global__ void oz_fill(int n, int v, int* E) {
 // exponent without a second launch) and writes the digits of its share of
 // 0 .. ld (plane t, (r, k) at t plane_rows ld + r ld + k; zero padding past
 // inner); the first CTA of the column records the exponent E[r]
-__global__ void __launch_bounds__(256)
-oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __restrict__ A, int lda,
-               int row0, int chunks, int* E, __nv_bfloat16* planes) {
+// digit planes of `rows` columns of a column-major operand: column r is
+// A[row0 + k + r lda], k < inner, split with its own scale E[r]; `chunks` CTAs
+// share a column (each finds the column's maximum, then splits its part)
+struct ColsJob {
+  int rows, plane_rows, inner, ld;
+  const double* A;
+  int lda, row0, chunks;
+  int* E;
+  __nv_bfloat16* planes;
+};
+
+__device__ __forceinline__ void planes_cols_body(const ColsJob& J, int bid, int nblk) {
   __shared__ unsigned long long red[8];
   __shared__ int e_sh;
-  const size_t plane = (size_t)plane_rows * ld;
-  const int span = (ld + chunks - 1) / chunks;
-  for (int item = blockIdx.x; item < rows * chunks; item += gridDim.x) {
-    const int r = item / chunks, c = item % chunks;
-    const double* col = A + row0 + (size_t)r * lda;
+  const size_t plane = (size_t)J.plane_rows * J.ld;
+  const int span = (J.ld + J.chunks - 1) / J.chunks;
+  for (int item = bid; item < J.rows * J.chunks; item += nblk) {
+    const int r = item / J.chunks, c = item % J.chunks;
+    const double* col = J.A + J.row0 + (size_t)r * J.lda;
     unsigned long long mx = 0ull;
-    for (int k = threadIdx.x; k < inner; k += blockDim.x) mx = max(mx, abs_bits(col[k]));
+    for (int k = threadIdx.x; k < J.inner; k += blockDim.x) mx = max(mx, abs_bits(col[k]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
@@ -385,24 +394,37 @@ oz_planes_cols(int rows, int plane_rows, int inner, int ld, const double* __rest
       unsigned long long m2 = 0ull;
       for (int w = 0; w < (int)blockDim.x / 32; ++w) m2 = max(m2, red[w]);
       e_sh = scale_exp_bits(m2);
-      if (c == 0) E[r] = e_sh;
+      if (c == 0) J.E[r] = e_sh;
     }
     __syncthreads();
     const int er = e_sh;
-    const int kend = min(ld, (c + 1) * span);
+    const int kend = min(J.ld, (c + 1) * span);
     for (int k = c * span + threadIdx.x; k < kend; k += blockDim.x) {
       int a[kOzS];
-      if (k < inner) {
+      if (k < J.inner) {
         digits(col[k], er, a);
       } else {
 #pragma unroll
         for (int t = 0; t < kOzS; ++t) a[t] = 0;
       }
 #pragma unroll
-      for (int t = 0; t < kOzS; ++t) planes[t * plane + (size_t)r * ld + k] = __float2bfloat16_rn((float)a[t]);
+      for (int t = 0; t < kOzS; ++t)
+        J.planes[t * plane + (size_t)r * J.ld + k] = __float2bfloat16_rn((float)a[t]);
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256) oz_planes_cols(ColsJob J) {
+  planes_cols_body(J, blockIdx.x, gridDim.x);
+}
+
+// two operands' column planes in one launch: blocks [0, blocks0) for J0, the rest for J1
+__global__ void __launch_bounds__(256) oz_planes_cols2(ColsJob J0, ColsJob J1, int blocks0) {
+  if ((int)blockIdx.x < blocks0)
+    planes_cols_body(J0, blockIdx.x, blocks0);
+  else
+    planes_cols_body(J1, blockIdx.x - blocks0, gridDim.x - blocks0);
 }
 
 // transposed digit planes of the m x n column-major A: plane t, (i, j) = A[i + j lda],
@@ -583,14 +605,37 @@ blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int l
   return BLWS_OK;
 }
 
+namespace {
+// a few CTAs per column when there are too few columns to fill the GPU (each
+// rereads its column for the maximum: cheap next to the digit writes)
+ColsJob cols_job(const Ctx* ctx, const double* A, int lda, int row0, int inner, int rows, const OzPlanes& out,
+                 int* grid) {
+  const int chunks = std::max(1, std::min(8, ceil_div(2 * ctx->sms, rows)));
+  *grid = std::min(rows * chunks, ctx->sms * 16);
+  return ColsJob{rows, out.rows, inner, out.ld, A, lda, row0, chunks, out.e, out.d};
+}
+
+// the column planes of two operands, in one launch when both have columns
+blws_status planes_cols_pair(Ctx* ctx, cudaStream_t s, const double* A0, int lda0, int row00, int inner0,
+                             int rows0, const OzPlanes& out0, const double* A1, int lda1, int row01,
+                             int inner1, int rows1, const OzPlanes& out1) {
+  if (rows0 <= 0) return oz_planes_from_cols(ctx, s, A1, lda1, row01, inner1, rows1, out1);
+  if (rows1 <= 0) return oz_planes_from_cols(ctx, s, A0, lda0, row00, inner0, rows0, out0);
+  int g0 = 0, g1 = 0;
+  const ColsJob j0 = cols_job(ctx, A0, lda0, row00, inner0, rows0, out0, &g0);
+  const ColsJob j1 = cols_job(ctx, A1, lda1, row01, inner1, rows1, out1, &g1);
+  oz_planes_cols2<<<g0 + g1, 256, 0, s>>>(j0, j1, g0);
+  BLWS_CHECK_LAUNCH(ctx);
+  return BLWS_OK;
+}
+}  // namespace
+
 blws_status oz_planes_from_cols(Ctx* ctx, cudaStream_t s, const double* A, int lda, int row0, int inner,
                                 int rows, const OzPlanes& out) {
   if (rows <= 0) return BLWS_OK;
-  // a few CTAs per column when there are too few columns to fill the GPU
-  // (each rereads its column for the maximum: cheap next to the digit writes)
-  const int chunks = std::max(1, std::min(8, ceil_div(2 * ctx->sms, rows)));
-  oz_planes_cols<<<std::min(rows * chunks, ctx->sms * 16), 256, 0, s>>>(rows, out.rows, inner, out.ld, A, lda,
-                                                                        row0, chunks, out.e, out.d);
+  int grid = 0;
+  const ColsJob j = cols_job(ctx, A, lda, row0, inner, rows, out, &grid);
+  oz_planes_cols<<<grid, 256, 0, s>>>(j);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
@@ -607,8 +652,7 @@ blws_status oz_dual_apply(Ctx* ctx, cudaStream_t s, const OzPlanes& Wr, const Oz
   BLWS_TRY(ctx->get(BUF_OZ_E, (size_t)2 * npad * sizeof(int), (void**)&xe));
   OzPlanes Xu{xp, xe, npad, m, ldu};
   OzPlanes Xv{xp + (size_t)kOzS * npad * ldu, xe + npad, npad, n, ldv};
-  BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, 0, m, b, Xu));
-  BLWS_TRY(oz_planes_from_cols(ctx, s, X, ldx, m, n, b, Xv));
+  BLWS_TRY(planes_cols_pair(ctx, s, X, ldx, 0, m, b, Xu, X, ldx, m, n, b, Xv));
 
   const int Ms[2] = {m, n}, Ks[2] = {n, m};
   const int tiles[2] = {ceil_div(m, kOzBM), ceil_div(n, kOzBM)};
@@ -696,10 +740,21 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
   int* eb = ea + M;
   const OzPlanes Ap{da, ea, M, K, ldk};
   const OzPlanes Bp{db, eb, npad, K, ldk};
-  if (ta) BLWS_TRY(oz_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
-  else BLWS_TRY(oz_planes_from_rows(ctx, s, A, lda, M, K, Ap));
-  if (!tb) BLWS_TRY(oz_planes_from_cols(ctx, s, B, ldb, 0, K, N, Bp));
-  else BLWS_TRY(oz_planes_from_rows(ctx, s, B, ldb, N, K, OzPlanes{db, eb, npad, K, ldk}));
+  // A^T A (a Gram matrix): op(B)'s planes are op(A)'s, built once
+  const bool same = ta && !tb && A == B && lda == ldb && M == N;
+  if (same) {
+    BLWS_TRY(oz_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
+  } else if (ta && !tb) {  // both from columns: one launch
+    BLWS_TRY(planes_cols_pair(ctx, s, A, lda, 0, K, M, Ap, B, ldb, 0, K, N, Bp));
+  } else {
+    if (ta) BLWS_TRY(oz_planes_from_cols(ctx, s, A, lda, 0, K, M, Ap));
+    else BLWS_TRY(oz_planes_from_rows(ctx, s, A, lda, M, K, Ap));
+    if (!tb) BLWS_TRY(oz_planes_from_cols(ctx, s, B, ldb, 0, K, N, Bp));
+    else BLWS_TRY(oz_planes_from_rows(ctx, s, B, ldb, N, K, OzPlanes{db, eb, npad, K, ldk}));
+  }
+  const __nv_bfloat16* bplanes = same ? da : db;
+  const int* bexp = same ? ea : eb;
+  const int brows = same ? M : npad;  // rows between op(B)'s planes
   const int tiles = ceil_div(M, kOzBM);
   const int kblocks = ceil_div(K, kOzBK);
   double* scal = nullptr;
@@ -717,9 +772,9 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
     OzJob& J = jobs.job[0];
     BLWS_TRY(oz_encode(ctx, &J.a, da, M, M, K, ldk, kOzBM));
     // op(B) columns past N: zero digits from the copy's out-of-bounds fill
-    BLWS_TRY(oz_encode(ctx, &J.b, db, N, npad, K, ldk, kOzBN));
+    BLWS_TRY(oz_encode(ctx, &J.b, bplanes, N, brows, K, ldk, kOzBN));
     J.ea = ea;
-    J.eb = eb;
+    J.eb = bexp;
     J.part = part;
     J.M = M;
     J.K = K;
@@ -738,7 +793,7 @@ blws_status oz_gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, in
     const size_t tot = (size_t)M * N;
     const int G = oz_lanes(ctx->sms, tot, splits);
     oz_reduce<<<(int)std::min<size_t>((tot * G + 255) / 256, (size_t)ctx->sms * 8), 256, 0, s>>>(
-        M, N, npad, splits, J.Mpad, part, ea, eb, Cout, ldo, alpha, bet,
+        M, N, npad, splits, J.Mpad, part, ea, bexp, Cout, ldo, alpha, bet,
         sym && M == N && bet == 0.0 ? 1 : 0, G);
     BLWS_CHECK_LAUNCH(ctx);
     return BLWS_OK;
