@@ -348,16 +348,24 @@ __global__ void sum_final(int n, const double* __restrict__ part, double* out) {
   if (threadIdx.x == 0) *out = red[0];
 }
 
-// one warp per column
-__global__ void col_norms_kernel(int M, int N, const double* __restrict__ A, int ld, double* out) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
-  if (warp >= N) return;
-  const double* a = A + (size_t)warp * ld;
+// one CTA per column (tall columns: thousands of rows, a hundred-odd
+// columns), sums in a fixed order
+__global__ void __launch_bounds__(256) col_norms_kernel(int M, int N, const double* __restrict__ A, int ld,
+                                                        double* out) {
+  __shared__ double red[8];
+  const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+  const double* a = A + (size_t)blockIdx.x * ld;
   double acc = 0.0;
-  for (int i = lane; i < M; i += 32) acc = fma(a[i], a[i], acc);
+  for (int i = threadIdx.x; i < M; i += 256) acc = fma(a[i], a[i], acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) out[warp] = sqrt(acc);
+  if (lane == 0) red[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[blockIdx.x] = sqrt(t);
+  }
 }
 
 __global__ void max_final(int n, const double* __restrict__ v, double* out) {
@@ -452,8 +460,10 @@ blws_status sumsq(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int l
 
 blws_status col_norms(Ctx* ctx, cudaStream_t s, int M, int N, const double* A, int ld,
                       double* out, double* colmax) {
-  col_norms_kernel<<<ceil_div((long long)N * 32, 256), 256, 0, s>>>(M, N, A, ld, out);
-  BLWS_CHECK_LAUNCH(ctx);
+  if (N > 0) {
+    col_norms_kernel<<<N, 256, 0, s>>>(M, N, A, ld, out);
+    BLWS_CHECK_LAUNCH(ctx);
+  }
   if (colmax) {
     max_final<<<1, 256, 0, s>>>(N, out, colmax);
     BLWS_CHECK_LAUNCH(ctx);
