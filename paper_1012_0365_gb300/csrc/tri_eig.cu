@@ -1238,12 +1238,14 @@ tri_wy_kernel(int n, const float* __restrict__ V, const float* __restrict__ tauv
   }
 }
 
-// X(:, col) = H_0 H_1 ... H_{n-3} Y(:, col) in FP64, one warp per column; the
+// X(:, col) = H_0 H_1 ... H_{n-3} Y(:, col) in FP64, one warp per column, each
+// lane holding kBackRows rows (32 kBackRows >= n: the kernel is instantiated
+// for a few heights, so a small T_k does not carry the largest one's rows); the
 // CTA stages kBackStage WY blocks at a time in shared memory.
-constexpr int kBackRows = (kTriMaxN + 31) / 32;
 constexpr int kBackWarps = 8;
 constexpr int kBackStage = 2;
 
+template <int kBackRows>
 __global__ void __launch_bounds__(kBackWarps * 32)
 tri_back_kernel(int n, const float* __restrict__ V, const float* __restrict__ Tw, const float* __restrict__ Y,
                 double* __restrict__ X) {
@@ -1398,7 +1400,13 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
     tri_wy_kernel<<<nblk, 64, 0, s>>>(n, V, tauv, Tw);
     BLWS_CHECK_LAUNCH(ctx);
   }
-  tri_back_kernel<<<ceil_div(n, kBackWarps), kBackWarps * 32, 0, s>>>(n, V, Tw, Y, X);
+  const int bg = ceil_div(n, kBackWarps), bt = kBackWarps * 32;
+  static_assert((kTriMaxN + 31) / 32 <= 23, "heights of the back-transformation");
+  if (n <= 128) tri_back_kernel<4><<<bg, bt, 0, s>>>(n, V, Tw, Y, X);
+  else if (n <= 256) tri_back_kernel<8><<<bg, bt, 0, s>>>(n, V, Tw, Y, X);
+  else if (n <= 384) tri_back_kernel<12><<<bg, bt, 0, s>>>(n, V, Tw, Y, X);
+  else if (n <= 512) tri_back_kernel<16><<<bg, bt, 0, s>>>(n, V, Tw, Y, X);
+  else tri_back_kernel<23><<<bg, bt, 0, s>>>(n, V, Tw, Y, X);
   BLWS_CHECK_LAUNCH(ctx);
   return BLWS_OK;
 }
