@@ -337,6 +337,7 @@ __device__ __forceinline__ void digits(double v, int E, int (&a)[kOzS]) {
 // (E starts below every exponent; an all-zero row keeps that value, and its
 // digits are zero whatever E is)
 constexpr int kOzNoExp = -4000;
+constexpr int kOzStripMaxN = 1024;  // row planes of blocks with rows up to this long: one launch
 
 __global__ void oz_row_scales(int m, int n, const double* __restrict__ A, int lda, int* E) {
   __shared__ unsigned long long t[32][33];
@@ -359,12 +360,6 @@ __global__ void oz_fill(int n, int v, int* E) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) E[i] = v;
 }
 
-// digit planes of the column-major slab: plane row r (= column r of A, K along
-// A's rows row0 .. row0 + inner) is split by `chunks` CTAs, each of which finds
-// the column's maximum (all of it: every CTA of the column gets the same
-// exponent without a second launch) and writes the digits of its share of
-// 0 .. ld (plane t, (r, k) at t plane_rows ld + r ld + k; zero padding past
-// inner); the first CTA of the column records the exponent E[r]
 // digit planes of `rows` columns of a column-major operand: column r is
 // A[row0 + k + r lda], k < inner, split with its own scale E[r]; `chunks` CTAs
 // share a column (each finds the column's maximum, then splits its part)
@@ -449,6 +444,61 @@ __global__ void oz_planes_rows(int m, int n, int ld, int plane_rows, const doubl
       for (int t = 0; t < kOzS; ++t)
         planes[t * plane + (size_t)i * ld + j] = __float2bfloat16_rn((float)a[t]);
     }
+  }
+}
+
+// One launch for the row planes of a column-major m x n block with a short
+// row (n up to a thousand or so; plane row i = row i of A, K along A's
+// columns): blockIdx.x takes a strip of 32 rows, blockIdx.y one of the
+// gridDim.y shares of the planes' columns.  Every CTA of a strip first finds
+// the 32 rows' maxima over all n columns (the same exponents in every CTA, no
+// atomics, and an all-zero row keeps kOzNoExp, whose digits are zero), then
+// splits its share 32 x 32 tiles at a time and writes them transposed; the
+// first share records E.
+__global__ void __launch_bounds__(256) oz_planes_rows_strip(int m, int n, int ld, int plane_rows,
+                                                            const double* __restrict__ A, int lda, int* E,
+                                                            __nv_bfloat16* planes) {
+  __shared__ double tile[32][33];
+  __shared__ unsigned long long red[8][32];
+  __shared__ int e_sh[32];
+  const size_t plane = (size_t)plane_rows * ld;
+  const int i0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  const int i = i0 + tx;
+  unsigned long long mx = 0ull;
+  if (i < m)
+    for (int j = ty; j < n; j += 8) mx = max(mx, abs_bits(A[i + (size_t)j * lda]));
+  red[ty][tx] = mx;
+  __syncthreads();
+  if (ty == 0) {
+    unsigned long long m2 = 0ull;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m2 = max(m2, red[w][tx]);
+    const int e = m2 ? scale_exp_bits(m2) : kOzNoExp;
+    e_sh[tx] = e;
+    if (blockIdx.y == 0 && i < m) E[i] = e;
+  }
+  __syncthreads();
+  const int tiles = (ld + 31) / 32, per = (tiles + gridDim.y - 1) / gridDim.y;
+  const int tb = blockIdx.y * per, te = min(tiles, tb + per);
+  for (int tj = tb; tj < te; ++tj) {
+    const int j0 = tj * 32;
+    for (int jj = ty; jj < 32; jj += 8) {
+      const int j = j0 + jj;
+      tile[jj][tx] = (i < m && j < n) ? A[i + (size_t)j * lda] : 0.0;
+    }
+    __syncthreads();
+    for (int ii = ty; ii < 32; ii += 8) {
+      const int r = i0 + ii, j = j0 + tx;
+      if (r < m && j < ld) {
+        int a[kOzS];
+        digits(tile[tx][ii], e_sh[ii], a);
+#pragma unroll
+        for (int t = 0; t < kOzS; ++t)
+          planes[t * plane + (size_t)r * ld + j] = __float2bfloat16_rn((float)a[t]);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -595,6 +645,17 @@ blws_status oz_alloc(Ctx* ctx, int m, int n, OzPlanes* Or, OzPlanes* Oc) {
 blws_status oz_planes_from_rows(Ctx* ctx, cudaStream_t s, const double* A, int lda, int m, int n,
                                 const OzPlanes& out) {
   if (m <= 0 || n <= 0) return BLWS_OK;
+  if (n <= kOzStripMaxN) {
+    // one launch; a strip's maxima cost 32 n reads per share, so the shares
+    // stay few: enough CTAs for about two per SM, at most 8 per strip
+    const int strips = ceil_div(m, 32);
+    const int shares = std::max(1, std::min(std::min(8, ceil_div(out.ld, 32)), ceil_div(2 * ctx->sms, strips)));
+    oz_planes_rows_strip<<<dim3(strips, shares), 256, 0, s>>>(m, n, out.ld, out.rows, A, lda, out.e, out.d);
+    BLWS_CHECK_LAUNCH(ctx);
+    return BLWS_OK;
+  }
+  // long rows (the planes of W itself): the maxima by 32 x 32 tiles over the
+  // whole grid, then the split
   oz_fill<<<ceil_div(m, 256), 256, 0, s>>>(m, kOzNoExp, out.e);
   BLWS_CHECK_LAUNCH(ctx);
   oz_row_scales<<<dim3(ceil_div(m, 32), ceil_div(n, 32)), 256, 0, s>>>(m, n, A, lda, out.e);
