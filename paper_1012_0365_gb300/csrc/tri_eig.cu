@@ -33,7 +33,12 @@ namespace blws {
 namespace {
 
 constexpr int kTriThreads = 1024;
-constexpr int kQrThreads = 512;
+// threads per CTA of the group orthonormalisation: in the 2000 x 2000 solve,
+// 1024: 120.3 ms, 512: 122.0, 384: 121.6, 256: 125.6 per solve
+#ifndef BLWS_TRI_QR_THREADS
+#define BLWS_TRI_QR_THREADS 1024
+#endif
+constexpr int kQrThreads = BLWS_TRI_QR_THREADS;
 constexpr float kGroupTol = kTriGroupTol;
 constexpr float kInvPert = 1.2e-7f;  // inverse iteration: pivots kept >= this x ||T||
 constexpr int kQrSmemFloats = 56 * 1024;  // group kernel: shared-memory budget (floats)
@@ -561,8 +566,10 @@ int cl_smem_bytes(int n) {
 //       every CTA; cluster barrier.
 // Every sum has a fixed order, so the result is deterministic.
 constexpr int kRowsMaxN1 = 236, kRowsMaxN2 = 330, kRowsMaxN4 = 468, kRowsMaxN8 = 656;
+// threads per CTA of the reduction by rows: measured in the 2000 x 2000 solve
+// (4-CTA cluster at n = 303), 1024: 123.1 ms, 768: 120.7, 512: 120.9 per solve
 #ifndef BLWS_TRI_ROWS_THREADS
-#define BLWS_TRI_ROWS_THREADS 1024
+#define BLWS_TRI_ROWS_THREADS 768
 #endif
 constexpr int kTriRowsThreads = BLWS_TRI_ROWS_THREADS;  // threads per CTA (a multiple of 32, <= 1024)
 
