@@ -62,6 +62,11 @@ struct BlwsArgs {
   // cold start (a call repeated by the guard with more blocks: the local
   // recurrence loses orthogonality to converged directions as k grows)
   bool reorth = false;
+  // U0, V0 are the previous call's Ritz vectors (the solvers' own warm
+  // starts, orthonormal to rounding): the start block takes one CholeskyQR
+  // pass instead of two when it has no other columns (callers' warm starts
+  // are orthonormalised in full)
+  bool ritz_warm = false;
 };
 
 // the guard's ratio of the last stage (a) with a.guard, once s is synchronised

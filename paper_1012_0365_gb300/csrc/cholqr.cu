@@ -462,7 +462,7 @@ blws_status chol_equil(Ctx* ctx, cudaStream_t s, int b, const double* G, const d
 }  // namespace
 
 blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld, double* X,
-                     double* tmp, double* B, const double* scale, double tol, bool fp32) {
+                     double* tmp, double* B, const double* scale, double tol, bool fp32, bool one_pass) {
   // small scratch: G, S, B1, B2, work (2 b^2)
   double* sm = nullptr;
   BLWS_TRY(ctx->get(BUF_SMALL, 6ull * b * b, &sm));
@@ -477,6 +477,11 @@ blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld, 
   const double pivmin = fp32 ? kPivMinF32 : kPivMin;
   const double near_err = fp32 ? kNearIdErrF32 : kNearIdErr;
   BLWS_TRY(chol_equil(ctx, s, b, G, scale, tol, pivmin, near_err, S, B1, work));
+  if (one_pass) {
+    BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, R, ld, S, b, 0.0, X, ld, fp32));
+    BLWS_TRY_CUDA(ctx, cudaMemcpyAsync(B, B1, sizeof(double) * b * b, cudaMemcpyDeviceToDevice, s));
+    return BLWS_OK;
+  }
   BLWS_TRY(gemm(ctx, s, false, false, N, b, b, 1.0, R, ld, S, b, 0.0, tmp, ld, fp32));
   // pass 2 (columns are now unit or zero: same deflation rule against 1)
   BLWS_TRY(gemm(ctx, s, true, false, b, b, N, 1.0, tmp, ld, tmp, ld, 0.0, G, b, fp32));

@@ -171,6 +171,7 @@ blws_status mc_run(Ctx* ctx, cudaStream_t s, int m, int n, int nnz, const int* r
         a.V0 = Vw;
         a.ldv0 = n;
         a.w = w;
+        a.ritz_warm = true;
         a.k = std::max(1, std::min(k, N / std::max(sk, w)));
       }
       // the warm block is read before U, V are overwritten, so in place is safe.

@@ -82,10 +82,14 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
 // `scale` (device scalar) and `tol`: a column dies when its diagonal of B is
 // <= tol * scale.  `tmp` is an N x b scratch array (ld).
 // fp32: the four tall products (Gram matrices, X = R S) in FP32 arithmetic;
-// the b x b factorisation stays FP64.
+// the b x b factorisation stays FP64.  one_pass: R's columns are known to be
+// orthonormal to rounding already (a warm start made of the previous call's
+// Ritz vectors), so a first pass -- whose Gram matrix is then I + E with E at
+// the rounding level, factored exactly by the near-identity rule -- already
+// leaves X as orthonormal as a second one would; the second is skipped.
 blws_status chol_qr2(Ctx* ctx, cudaStream_t s, int N, int b, double* R, int ld,
                      double* X, double* tmp, double* B, const double* scale, double tol,
-                     bool fp32 = false);
+                     bool fp32 = false, bool one_pass = false);
 
 // ------------------------------------------- tensor-core products (tc_gemm)
 // A matrix as two TF32 planes (hi + lo) in FP32 containers, K-major:

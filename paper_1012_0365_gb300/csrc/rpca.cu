@@ -270,6 +270,7 @@ blws_status spectral_norm(Ctx* ctx, cudaStream_t s, const Operator& op, double* 
       a.V0 = V;
       a.ldv0 = op.n;
       a.w = r;
+      a.ritz_warm = true;
     }
     // the passes after the first repeat the same launches: graph phases as in
     // the solvers' outer iterations (graph.cuh)
@@ -442,6 +443,7 @@ blws_status rpca_run(Ctx* ctx, cudaStream_t s, const double* D, int m, int n, in
       a.V0 = Vw;
       a.ldv0 = n;
       a.w = w;
+      a.ritz_warm = true;
       a.k = std::max(1, std::min(k, N / std::max(sv, w)));
     }
     if (mixed) {
