@@ -556,14 +556,16 @@ int cl_smem_bytes(int n) {
 // rows: the trailing update and the product p = A22 v of a row are one pass
 // over it with a warp-level sum, and no column sums have to be gathered
 // across warps.  Every CTA keeps the per-index vectors (pending update
-// pv, pw and the current reflector v) in full.  Step k:
+// pv, pw, the current reflector v, and p) in full.  Step k:
 //   (1) the warp owning row k applies the pending update to it, forms the
 //       reflector and writes v (and tau) into every CTA; cluster barrier;
-//   (2) every warp updates its trailing rows and forms p_i = tau a_i . v;
-//       each CTA's sum of p_i v_i goes to every CTA; cluster barrier;
-//   (3) K = tau / 2 sum p_i v_i (the CTA sums in rank order), and the owner
-//       of row i writes the next pending pair (v_i, w_i = p_i - K v_i) into
-//       every CTA; cluster barrier.
+//   (2) every warp updates its trailing rows and forms p_i = tau a_i . v,
+//       written into every CTA; each CTA's sum of p_i v_i goes to every CTA;
+//       cluster barrier;
+//   (3) every CTA forms K = tau / 2 sum p_i v_i (the CTA sums in rank order)
+//       and the next pending pair (v_j, w_j = p_j - K v_j) of every index
+//       itself -- no third barrier; the reflectors of consecutive steps live
+//       in two slots, so the next owner can write its own meanwhile.
 // Every sum has a fixed order, so the result is deterministic.
 constexpr int kRowsMaxN1 = 236, kRowsMaxN2 = 330, kRowsMaxN4 = 468, kRowsMaxN8 = 656;
 // threads per CTA of the reduction by rows: measured in the 2000 x 2000 solve
@@ -637,20 +639,23 @@ template <int kCl>
 int rows_smem_bytes(int n) {
   const int R = rows_per_cta<kCl>(n);
   const int S = kCl > 1 ? std::min(n, kRowsSwitchM) : 0;
-  return n * (int)sizeof(float4) + std::max(R, S) * (int)sizeof(float) +
-         std::max(R * n, S * S) * (int)sizeof(float);
+  return n * (int)sizeof(float4) + n * (int)sizeof(float) + std::max(R * n, S * S) * (int)sizeof(float);
 }
 
 // One Householder step k over the rows this CTA holds, KC CTAs taking part.
 // Local row l is global row i = base + l KC + rank, stored at A + l ldA, and
 // element (i, j) of it at (A + l ldA)[j - base] (only j >= k + 1 > base is
-// touched).  sh_part has KC entries.
+// touched).  sh_part has KC entries, pv (p of every index) n.  The step's
+// reflector goes to cv[.].z on even steps and cv[.].w on odd ones, so the
+// next step's owner can write its reflector while the others still read this
+// one; two cluster barriers per step: after the reflector, after p.
 template <int KC>
 __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int base, float* A, int ldA,
-                                          float4* cv, float* pb, float* red, float* sh_part, float* sh_tau,
+                                          float4* cv, float* pv, float* red, float* sh_part, float* sh_tau,
                                           float* __restrict__ V, float* __restrict__ dv, float* __restrict__ ev,
                                           float* __restrict__ tauv) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const bool odd = (k & 1) != 0;
   // (1) row k: pending update, reflector into every CTA
   const int lk = (k - base) / KC;
   if (rank == (k - base) % KC && wid == lk % nw) {
@@ -687,11 +692,16 @@ __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int bas
     for (int j = k + 1 + lane; j < n; j += 32) {
       const float v = j == k + 1 ? 1.0f : (tau != 0.0f ? row[j] * vscale : 0.0f);
 #pragma unroll
-      for (int r = 0; r < KC; ++r) rows_remote<KC>(cv, r)[j].z = v;
+      for (int r = 0; r < KC; ++r) {
+        float4* rc = rows_remote<KC>(cv, r);
+        if (odd) rc[j].w = v;
+        else rc[j].z = v;
+      }
     }
   }
   rows_sync<KC>();
-  // (2) trailing rows: pending update and p_i = tau a_i . v, two rows per pass
+  // (2) trailing rows: pending update and p_i = tau a_i . v, two rows per pass;
+  // p_i into every CTA
   const float tau = *sh_tau;
   const int l0 = (k - base + KC - rank) / KC;  // first local row with a global index > k
   float pvw = 0.0f;                            // this warp's sum of p_i v_i
@@ -708,12 +718,13 @@ __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int bas
 #pragma unroll 2
       for (int j = k + 1 + lane; j < n; j += 32) {
         const float4 q = cv[j];
+        const float vj = odd ? q.w : q.z;
         const float a0 = r0[j] - sym_upd(q0, q);
         const float a1 = r1[j] - sym_upd(q1, q);
         r0[j] = a0;
         r1[j] = a1;
-        s0 = fmaf(a0, q.z, s0);
-        s1 = fmaf(a1, q.z, s1);
+        s0 = fmaf(a0, vj, s0);
+        s1 = fmaf(a1, vj, s1);
       }
     } else {
 #pragma unroll 2
@@ -721,7 +732,7 @@ __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int bas
         const float4 q = cv[j];
         const float a0 = r0[j] - sym_upd(q0, q);
         r0[j] = a0;
-        s0 = fmaf(a0, q.z, s0);
+        s0 = fmaf(a0, odd ? q.w : q.z, s0);
       }
     }
 #pragma unroll
@@ -730,12 +741,13 @@ __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int bas
       s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
     const float p0 = tau * s0, p1 = tau * s1;
-    if (lane == 0) {
-      pb[l] = p0;
-      if (two) pb[l + nw] = p1;
+    if (lane < KC) {
+      float* rp = rows_remote<KC>(pv, lane);
+      rp[i0] = p0;
+      if (two) rp[i1] = p1;
     }
-    pvw = fmaf(p0, q0.z, pvw);
-    if (two) pvw = fmaf(p1, q1.z, pvw);
+    pvw = fmaf(p0, odd ? q0.w : q0.z, pvw);
+    if (two) pvw = fmaf(p1, odd ? q1.w : q1.z, pvw);
   }
   if (lane == 0) red[wid] = pvw;
   __syncthreads();
@@ -746,23 +758,23 @@ __device__ __forceinline__ void rows_step(int k, int n, int rank, int R, int bas
     if (lane < KC) rows_remote<KC>(sh_part, lane)[rank] = t;
   }
   rows_sync<KC>();
-  // (3) K and the next pending pair (v_i, w_i) of the local rows, into every CTA
+  // (3) in every CTA, for every index: K and the next pending pair
+  // (v_j, w_j = p_j - K v_j) -- only the pair's two words are written, as
+  // the next step's owner may already be writing its reflector into the
+  // other slot
   float K = 0.0f;
 #pragma unroll
   for (int r = 0; r < KC; ++r) K += sh_part[r];
   K *= 0.5f * tau;
-  for (int l = l0 + tid; l < R; l += blockDim.x) {
-    const int i = base + l * KC + rank;
-    if (i >= n) break;
-    const float v = cv[i].z;
-    const float2 vw = make_float2(v, pb[l] - K * v);
-#pragma unroll
-    for (int r = 0; r < KC; ++r) *reinterpret_cast<float2*>(&rows_remote<KC>(cv, r)[i]) = vw;
+  for (int j = k + 1 + tid; j < n; j += blockDim.x) {
+    const float v = odd ? cv[j].w : cv[j].z;
+    *reinterpret_cast<float2*>(&cv[j]) = make_float2(v, pv[j] - K * v);
   }
   // reflector k out to global memory, off the serial step: CTA r writes the
   // indices i = r (mod KC) (zero above k + 1, v_{k+1} = 1)
-  for (int i = rank + KC * tid; i < n; i += KC * (int)blockDim.x) V[i + (size_t)k * n] = i > k ? cv[i].z : 0.0f;
-  rows_sync<KC>();
+  for (int i = rank + KC * tid; i < n; i += KC * (int)blockDim.x)
+    V[i + (size_t)k * n] = i > k ? (odd ? cv[i].w : cv[i].z) : 0.0f;
+  __syncthreads();  // the pairs are read by every warp of this CTA next
 }
 
 // The reduction by rows.  kCl > 1: the cluster phase runs while the trailing
@@ -785,9 +797,9 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
   if constexpr (kCl > 1) rank = (int)cg::this_cluster().block_rank();
   const int R = rows_per_cta<kCl>(n);
   const int S = kCl > 1 ? min(n, kRowsSwitchM) : 0;
-  float4* cv = smr;                                   // x, y: pending update; z: reflector
-  float* pb = reinterpret_cast<float*>(cv + n);       // p_i of the local rows
-  float* A = pb + max(R, S);                          // the rows
+  float4* cv = smr;                                   // x, y: pending update; z / w: reflector
+  float* pv = reinterpret_cast<float*>(cv + n);       // p_i of every index
+  float* A = pv + n;                                  // the rows
   // scale: largest |T_ij| over the lower triangle (every CTA finds the same)
   double mx = 0.0;
   for (int j = wid; j < n; j += nw) {
@@ -817,7 +829,7 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
   const int ks = kCl > 1 ? n - S : n;  // first step of the single-CTA phase
   int k = 0;
   for (; k + 2 < n && k < ks; ++k)
-    rows_step<kCl>(k, n, rank, R, 0, A, n, cv, pb, red, sh_part, &sh_tau, V, dv, ev, tauv);
+    rows_step<kCl>(k, n, rank, R, 0, A, n, cv, pv, red, sh_part, &sh_tau, V, dv, ev, tauv);
   int fbase = 0, fld = n;  // layout of the rows for the last 2 x 2 block
   if constexpr (kCl > 1) {
     // gather the trailing block (m0 = n - ks rows and columns) into CTA 0
@@ -835,7 +847,7 @@ tri_rows_kernel(int n, const double* __restrict__ T, float* __restrict__ V, floa
     __threadfence();
     for (int e = tid; e < m0 * m0; e += blockDim.x) A[e] = stage[e];
     __syncthreads();
-    for (; k + 2 < n; ++k) rows_step<1>(k, n, 0, m0, ks, A, m0, cv, pb, red, sh_part, &sh_tau, V, dv, ev, tauv);
+    for (; k + 2 < n; ++k) rows_step<1>(k, n, 0, m0, ks, A, m0, cv, pv, red, sh_part, &sh_tau, V, dv, ev, tauv);
     fbase = ks;
     fld = m0;
   }
