@@ -23,16 +23,17 @@ namespace blws {
 
 namespace {
 
-// 1 / sqrt(p) for a pivot p in (1e-30, 1e30): an FP32 estimate and two
-// Newton-Raphson steps y <- y (3 - p y^2) / 2 in FP64 (each step squares the
-// relative error: ~1e-7 -> 1e-14 -> rounding).  On this GPU an FP64 divide or
-// square root is a long dependent chain of FP64 operations; this is six, and
-// it gives both the pivot sqrt(p) = p y and its reciprocal y.
-__device__ __forceinline__ double rsqrt_newton(double p) {
-  double y = (double)rsqrtf((float)p);
-  y = y * fma(-0.5 * p * y, y, 1.5);
-  y = y * fma(-0.5 * p * y, y, 1.5);
-  return y;
+// 1 / sqrt(p) for a pivot p in (1e-30, 1e30): an FP32 estimate y0 and one
+// third-order correction in FP64.  With e = 1 - p y0^2,
+// 1/sqrt(p) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3e^2/8 + ...); the estimate
+// leaves |e| ~ 2^-22, so the dropped terms (~e^3) are below FP64 rounding.
+// On this GPU an FP64 divide or square root is a long dependent chain of
+// FP64 operations; this is four (two Newton steps would be six), and it gives
+// both the pivot sqrt(p) = p y and its reciprocal y.
+__device__ __forceinline__ double rsqrt_cubic(double p) {
+  const double y0 = (double)rsqrtf((float)p);
+  const double e = fma(-(p * y0), y0, 1.0);
+  return fma(y0 * e, fma(e, 0.375, 0.5), y0);
 }
 
 constexpr double kPivMin = 1e-10;
@@ -140,7 +141,7 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
       bool dj = dead[j] != 0 || !(p > pivmin);
       double y = 1.0;
       if (!dj) {
-        y = rsqrt_newton(p);
+        y = rsqrt_cubic(p);
         if (!(d[j] * (p * y) > thr)) dj = true;
       }
       dead[j] = dj ? 1 : 0;
@@ -289,6 +290,8 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
     dead[j] = dz ? 1 : 0;
     d[j] = dz ? 1.0 : dj;
     dinv[j] = dz ? 1.0 : 1.0 / dj;
+    const double t = thr / (dz ? 1.0 : dj);
+    dl[j] = t * t;  // the pivot threshold until the factor is complete
   }
   __syncthreads();
   // every CTA takes the same decision from the same data; none has touched
@@ -324,12 +327,9 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
         const int j = jt * kCT + c;
         if (tid == 0) {
           const double p = T[c + kCT * c];
-          bool dj = dead[j] != 0 || !(p > pivmin);
-          double y = 1.0;
-          if (!dj) {
-            y = rsqrt_newton(p);
-            if (!(d[j] * (p * y) > thr)) dj = true;
-          }
+          // deflation d_j sqrt(p) <= thr tested as p <= (thr / d_j)^2, off the chain
+          const bool dj = dead[j] != 0 || !(p > pivmin) || !(p > dl[j]);
+          const double y = dj ? 1.0 : rsqrt_cubic(p);
           dead[j] = dj ? 1 : 0;
           piv_sh = dj ? 1.0 : p * y;
           rpiv_sh = dj ? 1.0 : y;
