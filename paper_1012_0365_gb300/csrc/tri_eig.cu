@@ -43,6 +43,7 @@ constexpr float kGroupTol = kTriGroupTol;
 constexpr float kInvPert = 1.2e-7f;  // inverse iteration: pivots kept >= this x ||T||
 constexpr int kQrSmemFloats = 56 * 1024;  // group kernel: shared-memory budget (floats)
 constexpr int kQrMaxGroup = 192;          // group kernel: widest group (2 c^2 <= the budget)
+constexpr int kQrTileThreads = 64;        // group kernel: Gram tiles from which a thread takes a tile
 constexpr float kPivMin = 1e-30f;    // Sturm counts: pivots kept away from zero by this (T scaled to <= 1)
 
 // packed lower triangle, column-major: element (i, j), i >= j
@@ -1096,7 +1097,8 @@ tri_solve_kernel(int n, const float* __restrict__ dv, const float* __restrict__ 
 // (the CTA of the group's first column; the others return at once).  The
 // block and its Gram matrix are staged in shared memory (sm_floats), the
 // block with an odd leading dimension so that warps reading down a column
-// and threads walking a row both hit distinct banks.  A group too wide for
+// and threads walking a row both hit distinct banks, the Gram matrix with
+// rows padded to a multiple of four floats (the solve reads L four at a time).  A group too wide for
 // that sets *fail (the matrix then goes to Jacobi).
 // The Cholesky factor is built column by column with one barrier per column:
 // every thread reads the pivot itself, and column k of L goes to the unused
@@ -1109,7 +1111,7 @@ constexpr float kNearId = 3e-4f;
 
 __global__ void __launch_bounds__(kQrThreads)
 tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __restrict__ Y, int* fail) {
-  extern __shared__ float smq[];
+  extern __shared__ __align__(16) float smq[];
   __shared__ float dg[kQrMaxGroup];
   __shared__ int near_sh;
   const int i = blockIdx.x, tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -1118,31 +1120,44 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
   while (j < n && grp[j] == i) ++j;
   const int c = j - i;
   const int lds = c | 1;
-  if ((long long)n * lds + (long long)c * c > sm_floats || c > kQrMaxGroup) {
+  const int ldg = (c + 3) & ~3;           // Gram rows 16-byte aligned
+  const int goff = (n * lds + 3) & ~3;
+  if ((long long)goff + (long long)c * ldg > sm_floats || c > kQrMaxGroup) {
     // too wide to stage: the caller falls back to Jacobi for this matrix
     if (tid == 0) *fail = 1;
     return;
   }
   float* Yb = smq;  // block element (r, a) at Yb[r * lds + a]
-  float* G = smq + (size_t)n * lds;
+  float* G = smq + goff;  // G(a, b) at G[a + b * ldg]
   const int ldb = lds;
   for (int r = wid; r < n; r += nw)
     for (int a = lane; a < c; a += 32) Yb[r * ldb + a] = Y[(size_t)r * n + i + a];
   if (tid == 0) near_sh = 1;
   __syncthreads();
   for (int pass = 0; pass < 2; ++pass) {
-    // Gram matrix in 4 x 4 tiles (upper triangle of tiles), a warp per tile,
-    // lanes over rows; mirrored
+    // Gram matrix in 4 x 4 tiles (upper triangle of tiles), mirrored.  Few
+    // tiles: a warp per tile, lanes over rows, summed by shuffles.  Many: a
+    // thread per tile summing over every S-th row (S = 4, 2 or 1, as many
+    // row slices as the threads allow), the slices of a tile in adjacent
+    // lanes, combined by shuffles
     const int t4 = (c + 3) / 4, ntile = t4 * (t4 + 1) / 2;
-    for (int e = wid; e < ntile; e += nw) {
-      int ta = 0, rem = e;  // unrank e -> (ta, tb), ta <= tb
-      while (rem >= t4 - ta) {
-        rem -= t4 - ta;
-        ++ta;
-      }
-      const int tb = ta + rem;
-      float acc[4][4] = {};
-      for (int r = lane; r < n; r += 32) {
+    auto put_tile = [&](int ta, int tb, const float(&acc)[4][4]) {
+      bool near = true;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int a = 4 * ta + u, b = 4 * tb + q;
+          if (a < c && b < c) {
+            G[a + b * ldg] = acc[u][q];
+            G[b + a * ldg] = acc[u][q];
+            near = near && fabsf(acc[u][q] - (a == b ? 1.0f : 0.0f)) <= kNearId;
+          }
+        }
+      if (!near) near_sh = 0;
+    };
+    auto tile_sum = [&](int ta, int tb, int r0, int step, float(&acc)[4][4]) {
+      for (int r = r0; r < n; r += step) {
         const float* yr = Yb + (size_t)r * ldb;
         float ya[4], yb[4];
 #pragma unroll
@@ -1155,26 +1170,46 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[u][q] = fmaf(ya[u], yb[q], acc[u][q]);
       }
+    };
+    auto unrank = [&](int e, int& ta, int& tb) {  // e -> (ta, tb), ta <= tb
+      int rem = e;
+      ta = 0;
+      while (rem >= t4 - ta) {
+        rem -= t4 - ta;
+        ++ta;
+      }
+      tb = ta + rem;
+    };
+    if (ntile < kQrTileThreads) {
+      for (int e = wid; e < ntile; e += nw) {
+        int ta, tb;
+        unrank(e, ta, tb);
+        float acc[4][4] = {};
+        tile_sum(ta, tb, lane, 32, acc);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
-      if (lane == 0) {
-        bool near = true;
+            for (int q = 0; q < 4; ++q) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
+        if (lane == 0) put_tile(ta, tb, acc);
+      }
+    } else {
+      const int S = ntile * 4 <= nt ? 4 : (ntile * 2 <= nt ? 2 : 1);
+      for (int base = 0; base < ntile; base += nt / S) {
+        const int e = base + tid / S, sl = tid % S;
+        int ta = 0, tb = 0;
+        float acc[4][4] = {};
+        if (e < ntile) {
+          unrank(e, ta, tb);
+          tile_sum(ta, tb, sl, S, acc);
+        }
+        for (int o = 1; o < S; o <<= 1)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+          for (int u = 0; u < 4; ++u)
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int a = 4 * ta + u, b = 4 * tb + q;
-            if (a < c && b < c) {
-              G[a + b * c] = acc[u][q];
-              G[b + a * c] = acc[u][q];
-              near = near && fabsf(acc[u][q] - (a == b ? 1.0f : 0.0f)) <= kNearId;
-            }
-          }
-        if (!near) near_sh = 0;
+            for (int q = 0; q < 4; ++q) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
+        if (e < ntile && sl == 0) put_tile(ta, tb, acc);
       }
     }
     __syncthreads();
@@ -1182,23 +1217,23 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
       // G = I + E with |E| <= kNearId: L = I + tril(E) to within |E|^2 ~ 1e-7
       // (the FP32 level), which is G itself below the diagonal and its mirror
       // above (where the solve reads it), with the square-rooted diagonal
-      for (int a = tid; a < c; a += nt) dg[a] = sqrtf(G[a + a * c]);
+      for (int a = tid; a < c; a += nt) dg[a] = sqrtf(G[a + a * ldg]);
       __syncthreads();
     } else {
       // G = L L^T: column kk of L into the upper triangle and dg, one barrier per column
       for (int kk = 0; kk < c; ++kk) {
-        float p = G[kk + kk * c];
+        float p = G[kk + kk * ldg];
         if (!(p > 1e-8f)) {  // too ill-conditioned for CholeskyQR2 in FP32
           if (tid == 0) *fail = 1;
           p = 1.0f;
         }
         const float ri = rsqrtf(p);
         if (tid == 0) dg[kk] = p * ri;  // sqrt(p)
-        for (int a = kk + 1 + tid; a < c; a += nt) G[kk + a * c] = G[a + kk * c] * ri;
+        for (int a = kk + 1 + tid; a < c; a += nt) G[kk + a * ldg] = G[a + kk * ldg] * ri;
         // trailing update of the lower triangle: a warp per column, lanes over rows
         for (int b = kk + 1 + wid; b < c; b += nw) {
-          const float gb = G[b + kk * c] * ri * ri;
-          for (int a = b + lane; a < c; a += 32) G[a + b * c] = fmaf(-G[a + kk * c], gb, G[a + b * c]);
+          const float gb = G[b + kk * ldg] * ri * ri;
+          for (int a = b + lane; a < c; a += 32) G[a + b * ldg] = fmaf(-G[a + kk * ldg], gb, G[a + b * ldg]);
         }
         __syncthreads();
       }
@@ -1209,7 +1244,16 @@ tri_group_qr_kernel(int n, int sm_floats, const int* __restrict__ grp, float* __
       float* yr = Yb + (size_t)r * ldb;
       for (int a = 0; a < c; ++a) {
         float acc = yr[a];
-        for (int b = 0; b < a; ++b) acc = fmaf(-yr[b], G[b + a * c], acc);
+        const float* La = G + (size_t)a * ldg;  // L(a, b) at La[b], four at a time
+        int b = 0;
+        for (; b + 4 <= a; b += 4) {
+          const float4 l = *reinterpret_cast<const float4*>(La + b);
+          acc = fmaf(-yr[b], l.x, acc);
+          acc = fmaf(-yr[b + 1], l.y, acc);
+          acc = fmaf(-yr[b + 2], l.z, acc);
+          acc = fmaf(-yr[b + 3], l.w, acc);
+        }
+        for (; b < a; ++b) acc = fmaf(-yr[b], La[b], acc);
         yr[a] = acc / dg[a];
       }
     }
@@ -1384,7 +1428,7 @@ blws_status tri_stage(Ctx* ctx, cudaStream_t s, int n, const double* T, double* 
     BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI, (const void*)tri_reduce_kernel, smem));
   }
   // the group kernel's shared memory: the largest staged block n x (c|1) plus c x c, capped
-  const int qr_floats = std::min((int)(((size_t)n * (n | 1) + nn)), kQrSmemFloats);
+  const int qr_floats = std::min((int)(((size_t)n * (n | 1) + (size_t)n * ((n + 3) & ~3) + 4)), kQrSmemFloats);
   const int gsmem = qr_floats * (int)sizeof(float);
   BLWS_TRY(ctx->smem_limit(Ctx::ATTR_TRI_INV, (const void*)tri_group_qr_kernel, gsmem));
   const int ssmem = n * ((int)sizeof(float4) + 4 * (int)sizeof(float));
