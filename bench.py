@@ -50,7 +50,8 @@ APPLY_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the
 MODE_DTYPE = {
     "fp64": "f64 throughout (DFMA products)",
     "mixed": "tf32x3 tensor-core products (hi+lo split, f32 sums of <= 256 terms, f64 beyond), f64 "
-             "Cholesky/eigen/count; fp64-equivalent digit-plane products once the residual < 1e-5",
+             "Cholesky/eigen/count (the eigen refinement's products as fp64-equivalent digit planes); "
+             "fp64-equivalent digit-plane products for everything once the residual < 1e-5",
     "fp64tc": "fp64-equivalent products: 7 bf16 digit planes per operand on tcgen05 (exact f32 sums of "
               "256 terms, ~1e-14 relative); Cholesky, eigen stage and count f64",
 }

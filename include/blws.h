@@ -53,9 +53,12 @@ typedef int blws_status;
  * operands (hi + lo, three products, FP32 accumulation over at most 256
  * terms, FP64 sums beyond); the other block products (Gram matrices, block
  * coefficients, residuals, Ritz lift) and the RPCA reconstruction in FP32
- * arithmetic with FP64 sums.  Block widths above 256 and sparse operators
- * keep FP64 products.  rpca_solve returns to FP64 products once its
- * residual falls below rpca_params.mixed_tol (the refinement tail). */
+ * arithmetic with FP64 sums.  Products that need FP64 accuracy (the eigen
+ * stage's refinement, block widths above 256, and every block product of
+ * the refinement tail: rpca_solve returns to FP64-level products once its
+ * residual falls below rpca_params.mixed_tol) run as in BLWS_PREC_FP64_TC:
+ * BF16 digit-plane products from 8e6 multiply-adds, FP64 below.  Sparse
+ * operators keep FP64 products. */
 #define BLWS_PREC_MIXED 1
 /* FP64-equivalent products on the tensor cores (dense W only): every row of W
  * and every column of X is written as 7 balanced base-128 digits under one

@@ -394,6 +394,10 @@ __global__ void scale_kernel(int M, int N, double beta, double* C, int ldc) {
 
 namespace {
 
+bool oz_mode(const Ctx* ctx) {
+  return ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->cfg.precision == BLWS_PREC_MIXED || ctx->oz_tail;
+}
+
 blws_status gemm_any(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K, double alpha,
                      const double* A, int lda, const double* B, int ldb, double beta, double* C,
                      int ldc, bool fp32, bool sym) {
@@ -424,8 +428,10 @@ blws_status gemm(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int M, int N, int K
   }
   // A^T A (the Gram matrices): symmetric, so one triangle of tiles is computed
   const bool sym = ta && !tb && A == B && lda == ldb && M == N && beta == 0.0;
-  if (!fp32 && (ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->oz_tail) && (double)M * N * K >= kOzGemmMin &&
-      std::min(M, N) >= 16 && K >= 64)
+  // FP64-level products of the tensor-core modes (in the mixed mode: the
+  // eigen stage's refinement, blocks too wide for the TF32 accumulator, the
+  // refinement tail) as digit-plane products once they are large enough
+  if (!fp32 && oz_mode(ctx) && (double)M * N * K >= kOzGemmMin && std::min(M, N) >= 16 && K >= 64)
     return oz_gemm(ctx, s, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sym);
   // mixed precision: the FP32-level block products on the tensor cores (TF32 hi + lo)
   if (fp32 && ctx->cfg.precision == BLWS_PREC_MIXED && (double)M * N * K >= kTcGemmMin &&
@@ -438,8 +444,7 @@ blws_status gemm_sym(Ctx* ctx, cudaStream_t s, bool ta, bool tb, int n, int K, d
                      const double* A, int lda, const double* B, int ldb, double* C, int ldc, bool fp32) {
   if (n <= 0) return BLWS_OK;
   if (K <= 0) return gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, fp32);
-  if (!fp32 && (ctx->cfg.precision == BLWS_PREC_FP64_TC || ctx->oz_tail) && (double)n * n * K >= kOzGemmMin && n >= 16 &&
-      K >= 64)
+  if (!fp32 && oz_mode(ctx) && (double)n * n * K >= kOzGemmMin && n >= 16 && K >= 64)
     return oz_gemm(ctx, s, ta, tb, n, n, K, alpha, A, lda, B, ldb, 0.0, C, ldc, true);
   if (fp32 && ctx->cfg.precision == BLWS_PREC_MIXED && (double)n * n * K >= kTcGemmMin && n >= 16 &&
       K >= 32 && n <= 256)

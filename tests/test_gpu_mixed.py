@@ -98,7 +98,8 @@ def test_mixed_gram_is_exactly_symmetric(ctxs, torch_mod):
 
 
 def test_mixed_apply_wide_block_keeps_fp64(ctxs, torch_mod):
-    # b > 256 exceeds one accumulator: the product stays FP64
+    # b > 256 exceeds one accumulator: the product stays at the FP64 level
+    # (digit planes from 8e6 multiply-adds, as in the FP64-equivalent mode)
     torch = torch_mod
     c64, cmx = ctxs
     W = torch.randn(300, 400, dtype=torch.float64, device="cuda").t()

@@ -5,7 +5,8 @@ byte of the GPU, a plugin host that forbids its own allocations, code that
 must not trigger the synchronisation an allocation can cause); this entry
 point serves them with its scratch in a static device array.  The test checks
 its output against the allocating blws_apply on two calls in a row, within
-the relative tolerance of the GPU parity tests, and that it rejects a product
+the relative tolerance of the GPU parity tests, and against an FP64 product
+formed outside the library, and that it rejects a product
 whose scratch need exceeds the array.  It runs last (file name) and needs no
 state from other tests.
 """
@@ -62,6 +63,11 @@ def test_noalloc_matches_allocating_apply_two_calls(env):
     for call, (W, X, P, ref) in enumerate(cases):
         err = float(torch.linalg.norm(P - ref) / torch.linalg.norm(ref))
         assert err < TOL, (call, err)
+        # and against an FP64 product formed outside the library (torch, cuBLAS)
+        m = W.shape[0]
+        ind = torch.cat([W @ X[m:], W.t() @ X[:m]])
+        err = float(torch.linalg.norm(P - ind) / torch.linalg.norm(ind))
+        assert err < 1e-13, (call, err)
 
 
 SCRATCH_DOUBLES = 2 << 20  # the header's stated maximum (16 MiB)
