@@ -189,8 +189,9 @@ blws_status blws_run_a(Ctx* ctx, cudaStream_t s, const Operator& op, const BlwsA
   const bool f32 = a.mixed;
   const double defl = f32 ? kDeflTolMixed : kDeflTol;
   // a warm start of the previous call's Ritz vectors alone (mixed start, no
-  // drawn or given columns) is orthonormal to rounding: one CholeskyQR pass
-  const bool one_pass = a.ritz_warm && !a.cold && !a.standard && !f32 && g == 0 && w == b;
+  // drawn or given columns) is orthonormal to the working precision's
+  // rounding: one CholeskyQR pass
+  const bool one_pass = a.ritz_warm && !a.cold && !a.standard && g == 0 && w == b;
   BLWS_TRY(chol_qr2(ctx, s, N, b, P, N, Q, P2, Bblk, scal + SLOT_AUX, defl, f32, one_pass));
 
   for (int l = 0; l < k; ++l) {
