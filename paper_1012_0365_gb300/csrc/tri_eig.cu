@@ -1301,7 +1301,8 @@ tri_wy_kernel(int n, const float* __restrict__ V, const float* __restrict__ tauv
   }
 }
 
-// X(:, col) = H_0 H_1 ... H_{n-3} Y(:, col) in FP64, one warp per column, each
+// X(:, col) = H_0 H_1 ... H_{n-3} Y(:, col) in FP32 arithmetic (the FP32 stage's
+// accuracy; the FP64 refinement follows), written as FP64; one warp per column, each
 // lane holding kBackRows rows (32 kBackRows >= n: the kernel is instantiated
 // for a few heights, so a small T_k does not carry the largest one's rows); the
 // CTA stages kBackStage WY blocks at a time in shared memory.
