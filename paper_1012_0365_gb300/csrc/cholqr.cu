@@ -51,22 +51,24 @@ constexpr double kNearIdErrF32 = 1e-10;  // the same with FP32 Gram matrices (re
 // a live column whose scale is within a factor 1 + 1e-6 of the deflation
 // threshold takes the full path, so both paths deflate the same columns.
 // The test reads the lower triangle only, like the factorisation, and a
-// non-finite entry sends the matrix to the full path.  Every thread of the
-// block calls it (it ends in a block-wide vote).
-__device__ bool near_identity(int b, const double* __restrict__ G, const double* d,
-                              const double* dinv, const int* dead, double thr, double err) {
+// non-finite entry sends the matrix to the full path.  It is split into
+// `parts` shares by columns (column j in share j mod parts, a warp per
+// column, lanes over its rows); every thread of the block calls it for the
+// block's share `part`, and it returns 1 (a block-wide vote) when that share
+// rules the shortcut out.
+__device__ int near_identity_slow(int b, const double* __restrict__ G, const double* d,
+                                  const double* dinv, const int* dead, double thr, double err,
+                                  int part, int parts) {
   const double eb = sqrt(err / b);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   int slow = 0;
-  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
-    const int i = e % b, j = e / b;
-    if (i < j) continue;
-    if (i == j) {
-      if (!dead[j] && !(d[j] > thr * (1.0 + 1e-6))) slow = 1;
-    } else if (!dead[i] && !dead[j] && !(fabs(G[e]) * dinv[i] * dinv[j] <= eb)) {
-      slow = 1;
-    }
+  for (int j = part + parts * (int)(threadIdx.x >> 5); j < b; j += parts * nw) {
+    if (dead[j]) continue;
+    if (lane == 0 && !(d[j] > thr * (1.0 + 1e-6))) slow = 1;
+    for (int i = j + 1 + lane; i < b; i += 32)
+      if (!dead[i] && !(fabs(G[i + (size_t)j * b]) * dinv[i] * dinv[j] <= eb)) slow = 1;
   }
-  return __syncthreads_or(slow) == 0;
+  return __syncthreads_or(slow);
 }
 
 // S(c, j) = L^-1(j, c) / d_c and B(c, j) = L(j, c) d_j from the shortcut,
@@ -119,7 +121,7 @@ chol_equil_kernel(int b, const double* __restrict__ G, const double* __restrict_
     dinv[j] = dz ? 1.0 : 1.0 / dj;
   }
   __syncthreads();
-  if (near_identity(b, G, d, dinv, dead, thr, near_err)) {
+  if (!near_identity_slow(b, G, d, dinv, dead, thr, near_err, 0, 1)) {
     near_identity_write(b, G, d, dinv, dead, S, Bout, tid, nt);
     return;
   }
@@ -274,6 +276,10 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
   int* dead = reinterpret_cast<int*>(smem + lay.off_dead);
   __shared__ double piv_sh, rpiv_sh;
   __shared__ double rdg[kCT];  // reciprocals of the diagonal of the step's tile
+  __shared__ int votes_sh[kCC];  // the CTAs' near-identity votes
+  // arrive at a cluster barrier now and wait for it before the first access
+  // to another CTA's shared memory (the votes below): by then every CTA runs
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   const int nt = lay.nt;
   const double thr = tol * (*scale_ptr);
   auto owner = [](int it, int jt) { return (it * (it + 1) / 2 + jt) % kCC; };
@@ -294,11 +300,24 @@ chol_cluster_kernel(int b, const double* __restrict__ G, const double* __restric
     dl[j] = t * t;  // the pivot threshold until the factor is complete
   }
   __syncthreads();
-  // every CTA takes the same decision from the same data; none has touched
-  // another's shared memory yet, so all may leave here
-  if (near_identity(b, G, d, dinv, dead, thr, near_err)) {
-    near_identity_write(b, G, d, dinv, dead, S, Bout, rank * kCThreads + tid, kCC * kCThreads);
-    return;
+  // the near-identity test, an eighth of the columns per CTA: every CTA
+  // writes its vote into every CTA (once all have started), and after the
+  // barrier all decide alike from their own copies; nothing is read from
+  // another CTA's shared memory, so all may leave here
+  {
+    const int slow = near_identity_slow(b, G, d, dinv, dead, thr, near_err, rank, kCC);
+    // every CTA of the cluster has started (the arrival at the top) before
+    // any writes into another's shared memory
+    asm volatile("barrier.cluster.wait.aligned;" ::: "memory");
+    if (tid < kCC) cl.map_shared_rank(votes_sh, tid)[rank] = slow;
+    cl.sync();
+    int any = 0;
+#pragma unroll
+    for (int r = 0; r < kCC; ++r) any |= votes_sh[r];
+    if (!any) {
+      near_identity_write(b, G, d, dinv, dead, S, Bout, rank * kCThreads + tid, kCC * kCThreads);
+      return;
+    }
   }
   // my tiles of the equilibrated lower triangle; padding rows and columns
   // (index >= b) are identity, dead columns unit vectors
