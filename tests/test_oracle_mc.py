@@ -1,6 +1,6 @@
 """Pins for the oracle's matrix-completion hosts: Table 2's pattern for SVT,
-full observation (closed form), and one proximal step with full observation
-equal to a plain SVT (Eq. 4)."""
+transpose equivariance, full observation (closed form), and one proximal step
+with full observation equal to a plain SVT (Eq. 4)."""
 import json
 import os
 
@@ -40,15 +40,21 @@ def test_svt_table2_pattern(small_mc):
     assert 60 <= out["iters"] <= 1.3 * max(r["iters"] for r in rows)
 
 
-def test_svt_iterate_is_supported_on_omega(small_mc):
-    # The SVT dual iterate Y stays on Omega, so X = T_tau(Y) depends on the
-    # observed entries only: re-running with the unobserved entries of M
-    # changed changes nothing.
-    P, out = small_mc
-    vals = P["vals"]
-    out2 = oracle.mc_svt_full(300, 300, P["rows"], P["cols"], vals, max_iter=5)
-    out3 = oracle.mc_svt_full(300, 300, P["rows"], P["cols"], vals.copy(), max_iter=5)
-    np.testing.assert_allclose(out2["th"], out3["th"])
+def test_svt_is_transpose_equivariant():
+    # SVT on the transposed problem (rows and columns of Omega swapped, m and
+    # n swapped) is the transposed iteration: the same singular values and
+    # X' = X^T.  A non-square problem, so an m/n mix-up or a transposed
+    # operand in the oracle shows.
+    m, n, r = 240, 300, 6
+    P = syn.mc_problem(m, n, r, 6 * r * (m + n - r) / (m * n), seed=4)
+    a = oracle.mc_svt_full(m, n, P["rows"], P["cols"], P["vals"], max_iter=8)
+    t = oracle.mc_svt_full(n, m, P["cols"], P["rows"], P["vals"], max_iter=8)
+    assert a["iters"] == t["iters"] and a["rank"] == t["rank"]
+    np.testing.assert_allclose(t["th"], a["th"], rtol=1e-10)
+    Xa = (a["U"] * a["th"]) @ a["V"].T
+    Xt = (t["U"] * t["th"]) @ t["V"].T
+    assert Xa.shape == (m, n) and Xt.shape == (n, m)
+    assert np.linalg.norm(Xt.T - Xa) <= 1e-10 * np.linalg.norm(Xa)
 
 
 def test_svt_full_observation_recovers_m():
